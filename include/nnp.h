@@ -1,0 +1,173 @@
+/*
+ * nnp.h -- C ABI of the B300 (sm_103a) Behler-Parrinello neural-network
+ * potential hot path (arXiv 2002.00054, "Implementing a neural network
+ * interatomic model with performance portability ...").
+ *
+ * Conventions for every call below
+ *   - Units: Angstrom, eV, amu, fs.  Boxes are orthorhombic and periodic with
+ *     the origin at 0; positions need not lie inside the box.
+ *   - "device" pointers are CUDA device memory on the handle's device, owned by
+ *     the caller, contiguous, naturally aligned (float arrays 4-byte, double
+ *     8-byte).  "host" pointers are ordinary host memory read during the call.
+ *   - The library owns only its scratch (cell lists, neighbour lists, per-pair
+ *     force buffer, descriptor buffers) and its copy of the model parameters.
+ *   - 'stream' is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     All device work of a call is enqueued on it.  Calls that return a status
+ *     from the device (nnp_compute, nnp_descriptors, nnp_step, the gradient
+ *     calls) synchronise that stream once at their end to read the library's
+ *     error word; no other synchronisation is done.
+ *   - Every call returns an nnp_status (0 = NNP_OK).  After an error,
+ *     nnp_last_error(h) describes it.  No call traps, asserts on the device or
+ *     spins: overflowing capacities and non-finite values are reported through
+ *     the status.
+ *   - A handle is not thread-safe: serialise calls on one handle.
+ */
+#ifndef NNP_B300_H
+#define NNP_B300_H
+
+#if defined(__GNUC__)
+#define NNP_API __attribute__((visibility("default")))
+#else
+#define NNP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum nnp_status {
+    NNP_OK = 0,
+    NNP_EINVAL = 1,           /* bad argument or parameter set                      */
+    NNP_ENOMEM = 2,           /* device or host allocation failed                   */
+    NNP_ENEIGH_OVERFLOW = 3,  /* an atom has more neighbours than max_neighbors,     */
+                              /* or a cell holds more atoms than the cell capacity   */
+    NNP_ENONFINITE = 4,       /* non-finite input/output, or two atoms closer than   */
+                              /* 1e-4 A                                               */
+    NNP_EBOX = 5,             /* box edge below (cutoff + skin) / 2, or box not > 0  */
+    NNP_ECUDA = 6,            /* a CUDA runtime call failed                          */
+    NNP_EUNSUPPORTED = 7      /* valid model outside what the kernels implement     */
+};
+
+/* --------------------------------------------------------- model definition */
+/* Descriptor kinds.  Radial: Fig. 1b step 1 of the paper,
+ *   G2_i = sum_j exp(-eta (r_ij - r_s)^2) f_c(r_ij),  f_c(r) = (cos(pi r / r_c) + 1) / 2.
+ * Angular ("one extra loop over neighbours of neighbours", Sec. 3.1; the paper
+ * does not print the formula, these are Behler's standard forms):
+ *   narrow: 2^(1-zeta) sum_{j<k} (1 + lambda cos t_ijk)^zeta
+ *                exp(-eta (r_ij^2 + r_ik^2 + r_jk^2)) f_c(r_ij) f_c(r_ik) f_c(r_jk)
+ *   wide:   the same without r_jk^2 in the exponent and without f_c(r_jk). */
+enum nnp_sf_type { NNP_SF_RADIAL = 2, NNP_SF_ANG_NARROW = 3, NNP_SF_ANG_WIDE = 4 };
+
+/* Network precision: FP32 everywhere, or BF16 operands with FP32 accumulation
+ * for the network layers (descriptors and forces stay FP32). */
+enum nnp_precision { NNP_FP32 = 0, NNP_BF16 = 1 };
+
+typedef struct {
+    int type;      /* nnp_sf_type                                                  */
+    int elem_a;    /* radial: neighbour element, -1 = any.                          */
+                   /* angular: with elem_b the unordered neighbour element pair,    */
+                   /* -1/-1 = any pair (the only angular filter implemented)        */
+    int elem_b;
+    double eta;    /* A^-2, >= 0                                                    */
+    double rs;     /* A, radial only (angular: must be 0)                           */
+    double zeta;   /* angular: 1, 2, 4, 8 or 16                                     */
+    double lambda; /* angular: +1 or -1                                             */
+} nnp_sf_desc;
+
+typedef struct {
+    int n_elements;              /* 1..8                                              */
+    const double* masses_amu;    /* host [n_elements]                                 */
+    double cutoff;               /* r_c, A                                            */
+    double skin;                 /* neighbour-list skin, A (>= 0); lists are rebuilt  */
+                                 /* when an atom moved more than skin/2               */
+    const int* n_sf;             /* host [n_elements]; all equal to widths[0]         */
+    const nnp_sf_desc* sf;       /* host, element 0's n_sf[0] descriptors, then       */
+                                 /* element 1's, ...; at most 64 per element, at most */
+                                 /* 4 distinct angular eta per element, one angular  */
+                                 /* kind per element                                  */
+    const double* sf_shift;      /* host, packed like sf: mu of G~ = (G - mu) / s     */
+    const double* sf_scale;      /* host, packed like sf: s (> 0)                     */
+    int n_layers;                /* weight layers, 2..6 (e.g. 3 for n_G-25-25-1)       */
+    const int* widths;           /* host [n_layers + 1]; widths[0] = n_G (<= 64),      */
+                                 /* hidden widths <= 32, widths[n_layers] = 1          */
+    const double* weights;       /* host, per element: for each layer l the matrix    */
+                                 /* W_l [widths[l+1]][widths[l]] row-major then the   */
+                                 /* bias b_l [widths[l+1]]; elements back to back     */
+    int mlp_precision;           /* nnp_precision                                     */
+    int max_neighbors;           /* capacity of one atom's neighbour-list row (entries */
+                                 /* within cutoff + skin), 32..1024                   */
+} nnp_params;
+
+typedef struct nnp_handle nnp_handle;
+
+/* Creates a handle on CUDA device 'device': validates and copies the parameters
+ * (host memory may be freed afterwards).  *out is NULL on failure.  Parameter
+ * validation happens before any CUDA call.  Scratch grows on demand later. */
+NNP_API int nnp_create(const nnp_params* params, int device, nnp_handle** out);
+
+/* Frees the handle and its device memory (waits for its pending work).  NULL is a no-op. */
+NNP_API int nnp_destroy(nnp_handle* h);
+
+/* Message of the last failed call on h (never NULL; "" if none).  Valid until the
+ * next call on h.  nnp_last_error(NULL) gives the message of the last failed
+ * nnp_create on this thread. */
+NNP_API const char* nnp_last_error(const nnp_handle* h);
+
+/* Static name of a status code. */
+NNP_API const char* nnp_status_string(int status);
+
+/* Number of network parameters over all elements (packed layout of nnp_params.weights). */
+NNP_API int nnp_num_params(const nnp_handle* h);
+
+/* Replaces the network parameters from a device buffer of nnp_num_params(h) floats in
+ * the packed layout (used by training).  Ordered on 'stream'; no synchronisation. */
+NNP_API int nnp_set_weights(nnp_handle* h, const float* weights_dev, void* stream);
+
+/* Energy and forces of one periodic system: Fig. 1b of the paper, steps 1-3.
+ *   n_atoms      >= 0 (0: energy = 0, virial = 0, nothing else written)
+ *   pos          device float [n_atoms][3]
+ *   types        device int [n_atoms], 0 <= type < n_elements
+ *   box          host double [3], edges > 0 and >= (cutoff + skin) / 2
+ *   cutoff       <= 0 or equal to the model cutoff (anything else: NNP_EINVAL)
+ *   energy       device double [1]: E = sum_i E_i, summed in FP64 (nullable)
+ *   atom_energy  device float [n_atoms]: E_i (nullable)
+ *   forces       device float [n_atoms][3]: F = -dE/dr (nullable)
+ *   virial       device double [9] row-major: W_ab = -sum_{i, j in nb(i)} d_ij^a dE_i/dd_ij^b,
+ *                d_ij = r_j - r_i for each neighbour image (nullable)
+ * The neighbour list is kept in the handle and rebuilt when n_atoms or the box
+ * changed or an atom moved more than skin/2 since the last build. */
+NNP_API int nnp_compute(nnp_handle* h, int n_atoms, const float* pos, const int* types, const double* box,
+                double cutoff, double* energy, float* atom_energy, float* forces, double* virial,
+                void* stream);
+
+/* Raw descriptors G (Fig. 1b step 1) and dE_i/dG_i (the network's input gradient
+ * used by step 3) of one system; arguments as nnp_compute.
+ *   G, dEdG      device float [n_atoms][n_G] (each nullable). */
+NNP_API int nnp_descriptors(nnp_handle* h, int n_atoms, const float* pos, const int* types, const double* box,
+                    float* G, float* dEdG, void* stream);
+
+/* n_steps velocity-Verlet NVE steps (Sec. 4.2 energy conservation):
+ *   v += dt/2 F/m;  x += dt v;  F = F(x);  v += dt/2 F/m
+ * pos, vel: device float [n_atoms][3], updated in place (positions are not wrapped).
+ * vel in A/fs; dt_fs > 0; n_steps >= 0.  pe_ke_log: device double [n_steps + 1][2]
+ * of (potential, kinetic) energy in eV before the first and after every step
+ * (nullable).  Forces at the start are computed by the call. */
+NNP_API int nnp_step(nnp_handle* h, int n_atoms, float* pos, float* vel, const int* types, const double* box,
+             double dt_fs, int n_steps, double* pe_ke_log, void* stream);
+
+/* Neighbour and work counters of the last compute (synchronises the handle's device). */
+typedef struct {
+    long long n_atoms;
+    long long list_entries;    /* neighbour-list entries within cutoff + skin      */
+    long long cutoff_entries;  /* entries within the cutoff                        */
+    long long pairs;           /* neighbour pairs j < k examined by the angular loop */
+    long long triplets;        /* pairs that contribute (narrow: r_jk < r_c)       */
+    long long rebuilds;        /* neighbour-list builds since creation             */
+} nnp_stats;
+NNP_API int nnp_get_stats(nnp_handle* h, nnp_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NNP_B300_H */

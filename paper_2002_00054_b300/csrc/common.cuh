@@ -1,0 +1,139 @@
+// common.cuh -- device-side model plan, error bits and small helpers shared by
+// the kernels of the NNP hot path (one translation unit: nnp_capi.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define NNP_MAXE 8      // elements
+#define NNP_MAXG 64     // descriptors per element
+#define NNP_MAXRAD 64   // radial descriptors per element
+#define NNP_MAXETA 4    // distinct angular eta per element
+#define NNP_KMAX 4      // angular zeta = 2^k, k <= NNP_KMAX
+#define NNP_MAXL 6      // weight layers
+#define NNP_MAXH 32     // hidden width
+
+#define WARP 32
+#define FULL 0xffffffffu
+
+// error word bits (flags[FLAG_ERR])
+#define ERR_NEIGH_OVERFLOW 1
+#define ERR_CELL_OVERFLOW 2
+#define ERR_NONFINITE 4
+#define ERR_CLOSE 8
+#define ERR_REV 16
+#define ERR_RC_OVERFLOW 32
+
+#define FLAG_ERR 0
+#define FLAG_REBUILD 1
+
+// work counters (counters[])
+#define CNT_LIST 0
+#define CNT_RC 1
+#define CNT_PAIRS 2
+#define CNT_TRIPLETS 3
+#define CNT_REBUILDS 4
+#define CNT_N 8
+
+#define LOG2E 1.4426950408889634f
+
+// Per-element descriptor plan.  Angular functions of one element share one kind
+// and are grouped by eta: ang_out[q][l][k] is the descriptor index of
+// (eta_q, lambda = (l == 0 ? +1 : -1), zeta = 2^k), or -1.
+struct ElemPlan {
+    int n_g;
+    int n_rad;
+    float rad_eta[NNP_MAXRAD];
+    float rad_rs[NNP_MAXRAD];
+    int rad_elem[NNP_MAXRAD];
+    int rad_out[NNP_MAXRAD];
+    int n_eta;
+    float ang_eta[NNP_MAXETA];
+    int ang_out[NNP_MAXETA][2][NNP_KMAX + 1];
+    float mu[NNP_MAXG];
+    float inv_s[NNP_MAXG];
+};
+
+struct Plan {
+    int n_elem;
+    int ang_kind;        // 0 none, 3 narrow, 4 wide (same for every element)
+    int n_eta_max;
+    float rc, rc2, hpi_rc;   // cutoff, cutoff^2, pi / (2 rc)
+    float rcut2;             // (cutoff + skin)^2
+    float half_skin2;        // (skin / 2)^2
+    float acc_over_m[NNP_MAXE];  // (1 eV/(A amu) in A/fs^2) / mass
+    float mass[NNP_MAXE];
+    // network: per layer, offsets into one element's block in the shared-memory
+    // weight image (row stride ld[l] = in | 1 so both access patterns are
+    // bank-conflict free)
+    int n_layers;
+    int width[NNP_MAXL + 1];
+    int ld[NNP_MAXL];
+    int s_woff[NNP_MAXL], s_boff[NNP_MAXL];
+    int s_elem;              // floats per element in the shared-memory image
+    int p_woff[NNP_MAXL], p_boff[NNP_MAXL];  // packed (caller) layout offsets
+    int n_params_elem;
+    int gs;                  // row stride of G / dEdG buffers
+    ElemPlan e[NNP_MAXE];
+};
+
+// f_c(r) = (cos(pi r / rc) + 1) / 2 = cos^2(pi r / (2 rc)); written as a square to
+// avoid the cancellation of cos + 1 near r = rc.  Derivative -2 k sin cos, k = pi/(2 rc).
+__device__ __forceinline__ void cutoff_fn(float r, float hpi_rc, float& fc, float& dfc)
+{
+    float s, c;
+    __sincosf(r * hpi_rc, &s, &c);
+    fc = c * c;
+    dfc = -2.0f * hpi_rc * s * c;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// neighbour entry: bits 0..23 atom index, bits 24..31 image code
+// code = (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2), s in [-2, 2]
+#define NB_INDEX_MASK 0x00ffffffu
+__device__ __forceinline__ uint32_t nb_pack(int j, int sx, int sy, int sz)
+{
+    return (uint32_t)j | ((uint32_t)((sx + 2) * 25 + (sy + 2) * 5 + (sz + 2)) << 24);
+}
+__device__ __forceinline__ void nb_shift(uint32_t e, float Lx, float Ly, float Lz, float& ox, float& oy, float& oz)
+{
+    int code = (int)(e >> 24);
+    int sx = code / 25 - 2;
+    int sy = (code / 5) % 5 - 2;
+    int sz = code % 5 - 2;
+    ox = (float)sx * Lx;
+    oy = (float)sy * Ly;
+    oz = (float)sz * Lz;
+}
+// the same image seen from the other atom: code -> 124 - code
+__device__ __forceinline__ uint32_t nb_reverse(uint32_t e, int i)
+{
+    return (uint32_t)i | ((124u - (e >> 24)) << 24);
+}
+
+struct Box { float L[3]; };
+
+// d = (pj - pi) + shift, with the rounding error of pj - pi restored by Knuth's
+// TwoSum (the error of a float sum is exactly representable).  For periodic
+// images pj - pi is close to -shift, so t + shift is exact (Sterbenz) and d is
+// correct to one rounding even in boxes hundreds of A wide.  Exactly
+// antisymmetric: swapping i and j and negating the shift negates d.
+__device__ __forceinline__ float pair_disp(float pj, float pi, float shift)
+{
+    const float t = pj - pi;
+    const float bb = t - pj;
+    const float e = (pj - (t - bb)) + (-pi - bb);
+    return (t + shift) + e;
+}

@@ -1,0 +1,277 @@
+// k_neighbors.cuh -- neighbour-list maintenance.
+//
+// The paper keeps a Cabana neighbour list (Sec. 3.2) and notes that random
+// neighbour access dominates (Sec. 4.3).  Here: a full (both directions) Verlet
+// list within cutoff + skin, one fixed-stride row per atom, entries packing the
+// neighbour index and its periodic image, plus a reverse index rev[e] = slot of
+// the mirrored entry so forces can be gathered without atomics.
+//
+// Positions inside the library are pos4 = pos - off, where off is a multiple of
+// the box fixed at the last rebuild (atoms are never wrapped in the caller's
+// buffer).  Every kernel of a rebuild returns at once unless flags[FLAG_REBUILD]
+// is set, so the whole sequence is enqueued without a host round trip.
+#pragma once
+#include "common.cuh"
+
+// pos4 = pos - off (old offsets); flags a rebuild if any atom moved more than skin/2.
+__global__ void k_check_disp(int n, const float* __restrict__ pos, const int* __restrict__ types, int n_elem,
+                             const float4* __restrict__ off, const float4* __restrict__ ref,
+                             float4* __restrict__ pos4, float half_skin2, int* __restrict__ flags)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 o = off[i];
+    float x = pos[3 * i] - o.x, y = pos[3 * i + 1] - o.y, z = pos[3 * i + 2] - o.z;
+    int t = types[i];
+    if (t < 0 || t >= n_elem) {   // invalid element: reported, and never used as an index
+        atomicOr(&flags[FLAG_ERR], ERR_NONFINITE);
+        t = 0;
+    }
+    pos4[i] = make_float4(x, y, z, __int_as_float(t));
+    float4 r = ref[i];
+    float dx = x - r.x, dy = y - r.y, dz = z - r.z;
+    float d2 = dx * dx + dy * dy + dz * dz;
+    if (!(d2 <= half_skin2)) flags[FLAG_REBUILD] = 1;   // also catches NaN
+}
+
+// On rebuild: new offsets off = floor(pos / L) L, pos4 = pos - off in [0, L), ref = pos4.
+__global__ void k_rebuild_pos(int n, const float* __restrict__ pos, const int* __restrict__ types, Box box,
+                              int n_elem, float4* __restrict__ off, float4* __restrict__ pos4,
+                              float4* __restrict__ ref, int* __restrict__ flags,
+                              unsigned long long* __restrict__ counters)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) counters[CNT_REBUILDS] += 1ull;
+    if (i >= n) return;
+    float x = pos[3 * i], y = pos[3 * i + 1], z = pos[3 * i + 2];
+    int t = types[i];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
+        atomicOr(&flags[FLAG_ERR], ERR_NONFINITE);
+        x = y = z = 0.0f;
+    }
+    if (t < 0 || t >= n_elem) {
+        atomicOr(&flags[FLAG_ERR], ERR_NONFINITE);
+        t = 0;
+    }
+    float ox = floorf(x / box.L[0]) * box.L[0];
+    float oy = floorf(y / box.L[1]) * box.L[1];
+    float oz = floorf(z / box.L[2]) * box.L[2];
+    off[i] = make_float4(ox, oy, oz, 0.0f);
+    float4 p = make_float4(x - ox, y - oy, z - oz, __int_as_float(t));
+    pos4[i] = p;
+    ref[i] = p;
+}
+
+__device__ __forceinline__ int cell_coord(float x, float L, int nc)
+{
+    int c = (int)floorf(x / L * (float)nc);
+    return c < 0 ? 0 : (c >= nc ? nc - 1 : c);
+}
+
+__global__ void k_cell_count(int n, const float4* __restrict__ pos4, Box box, int ncx, int ncy, int ncz,
+                             int* __restrict__ cell_of, int* __restrict__ cell_count, const int* __restrict__ flags)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 p = pos4[i];
+    int c = (cell_coord(p.z, box.L[2], ncz) * ncy + cell_coord(p.y, box.L[1], ncy)) * ncx + cell_coord(p.x, box.L[0], ncx);
+    cell_of[i] = c;
+    atomicAdd(&cell_count[c], 1);
+}
+
+// Exclusive scan of the cell counts by one block; cell_start[ncell] = n.  cursor = start.
+__global__ void k_cell_scan(int ncell, const int* __restrict__ cell_count, int* __restrict__ cell_start,
+                            int* __restrict__ cursor, const int* __restrict__ flags)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    __shared__ int part[1024];
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int per = (ncell + nt - 1) / nt;
+    const int lo = t * per, hi = min(lo + per, ncell);
+    int s = 0;
+    for (int c = lo; c < hi; ++c) s += cell_count[c];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < nt; o <<= 1) {   // Hillis-Steele inclusive scan of the partial sums
+        int v = (t >= o) ? part[t - o] : 0;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    int run = (t > 0) ? part[t - 1] : 0;
+    for (int c = lo; c < hi; ++c) {
+        cell_start[c] = run;
+        cursor[c] = run;
+        run += cell_count[c];
+    }
+    if (t == nt - 1) cell_start[ncell] = part[nt - 1];
+}
+
+__global__ void k_cell_fill(int n, const int* __restrict__ cell_of, int* __restrict__ cursor,
+                            int* __restrict__ cell_atoms, const int* __restrict__ flags)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int slot = atomicAdd(&cursor[cell_of[i]], 1);
+    cell_atoms[slot] = i;
+}
+
+// Deterministic order inside each cell (ascending atom index): warp per cell, rank sort.
+#define CELL_CAP 256
+__global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start, int* __restrict__ cell_atoms,
+                            int* __restrict__ flags)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    __shared__ int buf[8][CELL_CAP];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int c = blockIdx.x * (blockDim.x >> 5) + w; c < ncell; c += nw) {
+        const int s0 = cell_start[c], cnt = cell_start[c + 1] - s0;
+        if (cnt > CELL_CAP) {
+            if (lane == 0) atomicOr(&flags[FLAG_ERR], ERR_CELL_OVERFLOW);
+            continue;
+        }
+        for (int k = lane; k < cnt; k += 32) buf[w][k] = cell_atoms[s0 + k];
+        __syncwarp();
+        for (int k = lane; k < cnt; k += 32) {
+            int v = buf[w][k], rank = 0;
+            for (int q = 0; q < cnt; ++q) rank += (buf[w][q] < v);
+            cell_atoms[s0 + rank] = v;
+        }
+        __syncwarp();
+    }
+}
+
+// Row of atom i from the 27-cell stencil (cells of edge >= cutoff + skin, >= 3 per side).
+// Entry order: stencil order (z, y, x from -1 to 1), then ascending atom index.
+__global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int ncx, int ncy, int ncz,
+                            const int* __restrict__ cell_start, const int* __restrict__ cell_atoms,
+                            float rcut2, int stride, uint32_t* __restrict__ nbr, int* __restrict__ ncount,
+                            int* __restrict__ flags)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+        const float4 pi = pos4[i];
+        const int cx = cell_coord(pi.x, box.L[0], ncx), cy = cell_coord(pi.y, box.L[1], ncy),
+                  cz = cell_coord(pi.z, box.L[2], ncz);
+        int cnt = 0;
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int x = cx + dx, y = cy + dy, z = cz + dz, sx = 0, sy = 0, sz = 0;
+                    if (x < 0) { x += ncx; sx = -1; } else if (x >= ncx) { x -= ncx; sx = 1; }
+                    if (y < 0) { y += ncy; sy = -1; } else if (y >= ncy) { y -= ncy; sy = 1; }
+                    if (z < 0) { z += ncz; sz = -1; } else if (z >= ncz) { z -= ncz; sz = 1; }
+                    const int c = (z * ncy + y) * ncx + x;
+                    const float ox = (float)sx * box.L[0], oy = (float)sy * box.L[1], oz = (float)sz * box.L[2];
+                    const int b0 = cell_start[c], b1 = cell_start[c + 1];
+                    for (int base = b0; base < b1; base += 32) {
+                        const int p = base + lane;
+                        bool keep = false;
+                        int j = 0;
+                        if (p < b1) {
+                            j = cell_atoms[p];
+                            const float4 pj = pos4[j];
+                            const float ddx = pair_disp(pj.x, pi.x, ox), ddy = pair_disp(pj.y, pi.y, oy),
+                                        ddz = pair_disp(pj.z, pi.z, oz);
+                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                            keep = (r2 < rcut2) && !(j == i && sx == 0 && sy == 0 && sz == 0);
+                        }
+                        const unsigned m = __ballot_sync(FULL, keep);
+                        const int at = cnt + __popc(m & ((1u << lane) - 1u));
+                        if (keep && at < stride) nbr[(size_t)i * stride + at] = nb_pack(j, sx, sy, sz);
+                        cnt += __popc(m);
+                    }
+                }
+        if (lane == 0) {
+            if (cnt > stride) atomicOr(&flags[FLAG_ERR], ERR_NEIGH_OVERFLOW);
+            ncount[i] = min(cnt, stride);
+        }
+    }
+}
+
+// Row of atom i by brute force over the atoms of its system and the images
+// s in [-nimg, nimg]^3 (small boxes, several images of one atom possible).
+// Entry order: 32-atom chunks in index order, then image, then atom index.
+__global__ void k_rows_brute(int n, const float4* __restrict__ pos4, const int* __restrict__ sys_of,
+                             const int* __restrict__ sys_start, const float4* __restrict__ sys_box,
+                             float rcut2, int stride, uint32_t* __restrict__ nbr, int* __restrict__ ncount,
+                             int* __restrict__ flags)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+        const int s = sys_of ? sys_of[i] : 0;
+        const int j0 = sys_of ? sys_start[s] : 0, j1 = sys_of ? sys_start[s + 1] : n;
+        const float4 bx = sys_box[s];   // x, y, z edges; w = image range (as float)
+        const int nim = (int)bx.w;
+        const float4 pi = pos4[i];
+        int cnt = 0;
+        for (int base = j0; base < j1; base += 32) {
+            const int j = base + lane;
+            const bool vj = j < j1;
+            const float4 pj = vj ? pos4[j] : pi;
+            for (int sx = -nim; sx <= nim; ++sx)
+                for (int sy = -nim; sy <= nim; ++sy)
+                    for (int sz = -nim; sz <= nim; ++sz) {
+                        const float ddx = pair_disp(pj.x, pi.x, (float)sx * bx.x),
+                                    ddy = pair_disp(pj.y, pi.y, (float)sy * bx.y),
+                                    ddz = pair_disp(pj.z, pi.z, (float)sz * bx.z);
+                        const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                        const bool keep = vj && (r2 < rcut2) && !(j == i && sx == 0 && sy == 0 && sz == 0);
+                        const unsigned m = __ballot_sync(FULL, keep);
+                        const int at = cnt + __popc(m & ((1u << lane) - 1u));
+                        if (keep && at < stride) nbr[(size_t)i * stride + at] = nb_pack(j, sx, sy, sz);
+                        cnt += __popc(m);
+                    }
+        }
+        if (lane == 0) {
+            if (cnt > stride) atomicOr(&flags[FLAG_ERR], ERR_NEIGH_OVERFLOW);
+            ncount[i] = min(cnt, stride);
+        }
+    }
+}
+
+// rev[i, s] = slot of the mirrored entry (i seen from j with the opposite image).
+__global__ void k_rev(int n, const uint32_t* __restrict__ nbr, const int* __restrict__ ncount, int stride,
+                      int* __restrict__ rev, int* __restrict__ flags)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+        const int cnt = ncount[i];
+        const uint32_t* row = nbr + (size_t)i * stride;
+        for (int s0 = 0; s0 < cnt; s0 += 32) {
+            // each lane takes one entry of this chunk; the warp then searches row by row
+            const int my = s0 + lane;
+            const uint32_t e = (my < cnt) ? row[my] : 0u;
+            int found = -1;
+            const int m = min(32, cnt - s0);
+            for (int q = 0; q < m; ++q) {
+                const uint32_t eq = __shfl_sync(FULL, e, q);
+                const int j = (int)(eq & NB_INDEX_MASK);
+                const uint32_t target = nb_reverse(eq, i);
+                const int cj = ncount[j];
+                const uint32_t* rj = nbr + (size_t)j * stride;
+                int f = -1;
+                for (int b = 0; b < cj && f < 0; b += 32) {
+                    const int t = b + lane;
+                    const unsigned hit = __ballot_sync(FULL, t < cj && rj[t] == target);
+                    if (hit) f = b + __ffs(hit) - 1;
+                }
+                if (lane == q) found = f;
+            }
+            if (my < cnt) {
+                if (found < 0) atomicOr(&flags[FLAG_ERR], ERR_REV);
+                rev[(size_t)i * stride + my] = found < 0 ? 0 : found;
+            }
+        }
+    }
+}

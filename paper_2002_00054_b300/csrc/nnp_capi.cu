@@ -1,0 +1,678 @@
+// nnp_capi.cu -- host side of the C ABI declared in include/nnp.h: parameter
+// validation, the device plan, scratch management and the launch sequence of
+// one energy+force evaluation (Fig. 1b steps 1-3 of arXiv 2002.00054) and of
+// velocity-Verlet NVE.  All kernels live in this translation unit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/nnp.h"
+#include "common.cuh"
+#include "k_descriptors.cuh"
+#include "k_md.cuh"
+#include "k_mlp.cuh"
+#include "k_neighbors.cuh"
+
+namespace {
+
+const double kAcc = 9.64853321233100e-3;   // 1 eV/(A amu) in A/fs^2
+
+}  // namespace
+
+struct nnp_handle {
+    int device = 0;
+    Plan plan;
+    Plan* d_plan = nullptr;
+    int n_params = 0;
+    float* d_w = nullptr;
+    double cutoff = 0, skin = 0;
+    int stride = 0;
+    int precision = NNP_FP32;
+    std::string err;
+
+    // per-atom scratch (capacity cap_n)
+    int cap_n = 0;
+    float4 *off = nullptr, *ref = nullptr, *pos4 = nullptr, *Fown = nullptr;
+    float *G = nullptr, *dEdG = nullptr, *Ei = nullptr, *F = nullptr;
+    uint32_t* nbr = nullptr;
+    int *ncount = nullptr, *rev = nullptr, *cell_of = nullptr, *cell_atoms = nullptr;
+    float4* gbuf = nullptr;
+    // cells
+    int cap_cells = 0;
+    int *cell_count = nullptr, *cell_start = nullptr, *cursor = nullptr;
+    // reductions
+    int cap_epart = 0, cap_vpart = 0;
+    double *epart = nullptr, *vpart = nullptr, *d_energy = nullptr, *d_log = nullptr;
+    int cap_log = 0;
+    // flags, counters, boxes
+    int* flags = nullptr;
+    int* h_flags = nullptr;   // pinned
+    unsigned long long* counters = nullptr;
+    float4* sys_box = nullptr;
+
+    // list state
+    bool list_valid = false;
+    int list_n = -1;
+    double list_box[3] = {0, 0, 0};
+    bool cell_path = false;
+    int nc[3] = {0, 0, 0};
+
+    // launch configuration
+    int num_sms = 148;
+    int wpb_sf = 8, wpb_force = 8;
+    size_t smem_sf = 0, smem_force = 0, smem_mlp = 0;
+    int grid_sf = 0, grid_force = 0, grid_mlp = 0;
+    int cap_rc = 0;
+};
+
+static thread_local std::string g_create_err;
+
+static int set_err(nnp_handle* h, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+static int set_err(nnp_handle* h, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_create_err = buf;
+    return code;
+}
+
+#define CK(h, call)                                                                                  \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return set_err(h, e_ == cudaErrorMemoryAllocation ? NNP_ENOMEM : NNP_ECUDA, "%s: %s (%s:%d)", \
+                           #call, cudaGetErrorString(e_), __FILE__, __LINE__);                     \
+    } while (0)
+
+// ------------------------------------------------------------ validation / plan
+static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& why)
+{
+    char buf[256];
+    auto fail = [&](const char* m) { why = m; return NNP_EINVAL; };
+    if (!p) return fail("params is NULL");
+    if (p->n_elements < 1 || p->n_elements > NNP_MAXE) return fail("n_elements must be in 1..8");
+    if (!p->masses_amu || !p->n_sf || !p->sf || !p->sf_shift || !p->sf_scale || !p->widths || !p->weights)
+        return fail("a required params pointer is NULL");
+    if (!(p->cutoff > 0.0) || !std::isfinite(p->cutoff)) return fail("cutoff must be > 0");
+    if (!(p->skin >= 0.0) || !std::isfinite(p->skin)) return fail("skin must be >= 0");
+    if (p->n_layers < 2 || p->n_layers > NNP_MAXL) return fail("n_layers must be in 2..6");
+    if (p->mlp_precision != NNP_FP32 && p->mlp_precision != NNP_BF16) return fail("mlp_precision must be NNP_FP32 or NNP_BF16");
+    if (p->max_neighbors < 32 || p->max_neighbors > 1024) return fail("max_neighbors must be in 32..1024");
+    memset(&P, 0, sizeof P);
+    P.n_elem = p->n_elements;
+    P.rc = (float)p->cutoff;
+    P.rc2 = (float)(p->cutoff * p->cutoff);
+    P.hpi_rc = (float)(M_PI / (2.0 * p->cutoff));
+    const double rcut = p->cutoff + p->skin;
+    P.rcut2 = (float)(rcut * rcut);
+    P.half_skin2 = (float)(0.25 * p->skin * p->skin);
+    for (int e = 0; e < p->n_elements; ++e) {
+        if (!(p->masses_amu[e] > 0.0)) return fail("masses must be > 0");
+        P.mass[e] = (float)p->masses_amu[e];
+        P.acc_over_m[e] = (float)(kAcc / p->masses_amu[e]);
+    }
+    // network shape
+    const int ng = p->widths[0];
+    if (ng < 1 || ng > NNP_MAXG) return fail("widths[0] (n_G) must be in 1..64");
+    if (p->widths[p->n_layers] != 1) return fail("the last width must be 1");
+    for (int l = 1; l < p->n_layers; ++l)
+        if (p->widths[l] < 1 || p->widths[l] > NNP_MAXH) return fail("hidden widths must be in 1..32");
+    P.n_layers = p->n_layers;
+    int soff = 0, poff = 0;
+    for (int l = 0; l <= p->n_layers; ++l) P.width[l] = p->widths[l];
+    for (int l = 0; l < p->n_layers; ++l) {
+        const int in = p->widths[l], out = p->widths[l + 1];
+        P.ld[l] = in | 1;
+        P.s_woff[l] = soff;
+        soff += out * P.ld[l];
+        P.s_boff[l] = soff;
+        soff += out;
+        P.p_woff[l] = poff;
+        poff += out * in;
+        P.p_boff[l] = poff;
+        poff += out;
+    }
+    P.s_elem = (soff + 3) & ~3;
+    P.n_params_elem = poff;
+    n_params = poff * p->n_elements;
+    for (int i = 0; i < n_params; ++i)
+        if (!std::isfinite(p->weights[i])) return fail("weights must be finite");
+    // descriptors
+    int off = 0, kind = 0, neta_max = 0;
+    for (int e = 0; e < p->n_elements; ++e) {
+        ElemPlan& E = P.e[e];
+        const int ns = p->n_sf[e];
+        if (ns != ng) return fail("n_sf[e] must equal widths[0] for every element");
+        E.n_g = ns;
+        for (int q = 0; q < NNP_MAXETA; ++q)
+            for (int l = 0; l < 2; ++l)
+                for (int k = 0; k <= NNP_KMAX; ++k) E.ang_out[q][l][k] = -1;
+        std::vector<double> etas;
+        for (int s = 0; s < ns; ++s) {
+            const nnp_sf_desc& d = p->sf[off + s];
+            const double mu = p->sf_shift[off + s], sc = p->sf_scale[off + s];
+            if (!(sc > 0.0) || !std::isfinite(sc) || !std::isfinite(mu)) return fail("sf_scale must be > 0 and finite, sf_shift finite");
+            E.mu[s] = (float)mu;
+            E.inv_s[s] = (float)(1.0 / sc);
+            if (!(d.eta >= 0.0) || !std::isfinite(d.eta)) return fail("eta must be >= 0");
+            if (d.type == NNP_SF_RADIAL) {
+                if (d.elem_a < -1 || d.elem_a >= p->n_elements) return fail("radial elem_a out of range");
+                if (!std::isfinite(d.rs)) return fail("rs must be finite");
+                if (E.n_rad >= NNP_MAXRAD) return fail("too many radial descriptors");
+                E.rad_eta[E.n_rad] = (float)d.eta;
+                E.rad_rs[E.n_rad] = (float)d.rs;
+                E.rad_elem[E.n_rad] = d.elem_a;
+                E.rad_out[E.n_rad] = s;
+                E.n_rad++;
+            } else if (d.type == NNP_SF_ANG_NARROW || d.type == NNP_SF_ANG_WIDE) {
+                if (d.elem_a != -1 || d.elem_b != -1) { why = "element-resolved angular descriptors are not implemented"; return NNP_EUNSUPPORTED; }
+                if (d.rs != 0.0) return fail("angular rs must be 0");
+                if (kind == 0) kind = d.type;
+                else if (kind != d.type) { why = "narrow and wide angular descriptors in one model are not implemented"; return NNP_EUNSUPPORTED; }
+                int q = -1;
+                for (size_t t = 0; t < etas.size(); ++t) if (etas[t] == d.eta) q = (int)t;
+                if (q < 0) {
+                    if ((int)etas.size() >= NNP_MAXETA) { why = "more than 4 distinct angular eta per element"; return NNP_EUNSUPPORTED; }
+                    etas.push_back(d.eta);
+                    q = (int)etas.size() - 1;
+                    E.ang_eta[q] = (float)d.eta;
+                }
+                int l;
+                if (d.lambda == 1.0) l = 0;
+                else if (d.lambda == -1.0) l = 1;
+                else return fail("lambda must be +1 or -1");
+                int k = -1;
+                for (int t = 0; t <= NNP_KMAX; ++t) if (d.zeta == (double)(1 << t)) k = t;
+                if (k < 0) { why = "angular zeta must be 1, 2, 4, 8 or 16"; return NNP_EUNSUPPORTED; }
+                if (E.ang_out[q][l][k] >= 0) return fail("duplicate angular descriptor");
+                E.ang_out[q][l][k] = s;
+            } else {
+                snprintf(buf, sizeof buf, "unknown descriptor type %d", d.type);
+                why = buf;
+                return NNP_EINVAL;
+            }
+        }
+        E.n_eta = (int)etas.size();
+        neta_max = std::max(neta_max, E.n_eta);
+        off += ns;
+    }
+    P.ang_kind = kind;
+    P.n_eta_max = neta_max;
+    P.gs = (ng + 3) & ~3;
+    return NNP_OK;
+}
+
+// --------------------------------------------------------------- dispatch
+typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, float*, float*, int*, unsigned long long*);
+typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
+                            double*, int*);
+
+template <int NETA, bool NARROW>
+static void pick(SfKernel& s, ForceKernel& f)
+{
+    s = k_sf<NETA, NARROW>;
+    f = k_force<NETA, NARROW>;
+}
+
+static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
+{
+    const bool nar = (P.ang_kind == NNP_SF_ANG_NARROW);
+    switch (P.n_eta_max) {
+    case 0: pick<0, false>(s, f); break;
+    case 1: if (nar) pick<1, true>(s, f); else pick<1, false>(s, f); break;
+    case 2: if (nar) pick<2, true>(s, f); else pick<2, false>(s, f); break;
+    case 3: if (nar) pick<3, true>(s, f); else pick<3, false>(s, f); break;
+    default: if (nar) pick<4, true>(s, f); else pick<4, false>(s, f); break;
+    }
+}
+
+static size_t sf_smem_per_warp(int cap) { return (size_t)cap * (16 + 16 + 8) + NNP_MAXG * 8; }
+static size_t force_smem_per_warp(int cap, int stride)
+{
+    return (size_t)cap * (16 + 16 + 16 + 8 + 12) + (size_t)stride * 4 + NNP_MAXG * 4;
+}
+
+// ------------------------------------------------------------------ scratch
+template <typename T>
+static cudaError_t regrow(T*& p, size_t count)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    return cudaMalloc((void**)&p, std::max<size_t>(count, 1) * sizeof(T));
+}
+
+static int ensure_atoms(nnp_handle* h, int n)
+{
+    if (n <= h->cap_n) return NNP_OK;
+    const int cap = std::max(n, h->cap_n + h->cap_n / 8);
+    const size_t rows = (size_t)cap * h->stride;
+    CK(h, regrow(h->off, cap));
+    CK(h, regrow(h->ref, cap));
+    CK(h, regrow(h->pos4, cap));
+    CK(h, regrow(h->Fown, cap));
+    CK(h, regrow(h->G, (size_t)cap * h->plan.gs));
+    CK(h, regrow(h->dEdG, (size_t)cap * h->plan.gs));
+    CK(h, regrow(h->Ei, cap));
+    CK(h, regrow(h->F, (size_t)cap * 3));
+    CK(h, regrow(h->nbr, rows));
+    CK(h, regrow(h->ncount, cap));
+    CK(h, regrow(h->rev, rows));
+    CK(h, regrow(h->gbuf, rows));
+    CK(h, regrow(h->cell_of, cap));
+    CK(h, regrow(h->cell_atoms, cap));
+    h->cap_n = cap;
+    h->list_valid = false;
+    return NNP_OK;
+}
+
+static int ensure_cells(nnp_handle* h, int ncell)
+{
+    if (ncell <= h->cap_cells) return NNP_OK;
+    CK(h, regrow(h->cell_count, ncell + 1));
+    CK(h, regrow(h->cell_start, ncell + 1));
+    CK(h, regrow(h->cursor, ncell + 1));
+    h->cap_cells = ncell;
+    return NNP_OK;
+}
+
+static int ensure_red(nnp_handle* h, int ne, int nv)
+{
+    if (ne > h->cap_epart) {
+        CK(h, regrow(h->epart, ne));
+        h->cap_epart = ne;
+    }
+    if (nv > h->cap_vpart) {
+        CK(h, regrow(h->vpart, (size_t)nv * 9));
+        h->cap_vpart = nv;
+    }
+    return NNP_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d)
+    {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static int check_box(nnp_handle* h, const double* box)
+{
+    if (!box) return set_err(h, NNP_EINVAL, "box is NULL");
+    const double rcut = h->cutoff + h->skin;
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0.0) || !std::isfinite(box[a])) return set_err(h, NNP_EBOX, "box edges must be finite and > 0");
+        if (box[a] < 0.5 * rcut)
+            return set_err(h, NNP_EBOX, "box edge %g is below (cutoff + skin) / 2 = %g", box[a], 0.5 * rcut);
+    }
+    return NNP_OK;
+}
+
+static int read_status(nnp_handle* h, cudaStream_t st)
+{
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(h->h_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    const int f = h->h_flags[0];
+    if (f) {
+        // errors leave the neighbour list in an unknown state
+        h->list_valid = false;
+        if (f & (ERR_NEIGH_OVERFLOW | ERR_RC_OVERFLOW))
+            return set_err(h, NNP_ENEIGH_OVERFLOW, "an atom has more than max_neighbors = %d neighbours", h->stride);
+        if (f & ERR_CELL_OVERFLOW) return set_err(h, NNP_ENEIGH_OVERFLOW, "a cell holds more than %d atoms", CELL_CAP);
+        if (f & ERR_CLOSE) return set_err(h, NNP_ENONFINITE, "two atoms are closer than 1e-4 A");
+        if (f & ERR_NONFINITE) return set_err(h, NNP_ENONFINITE, "non-finite position/energy/force or invalid element type");
+        if (f & ERR_REV) return set_err(h, NNP_ECUDA, "internal error: neighbour list not symmetric");
+        return set_err(h, NNP_ECUDA, "device error word 0x%x", f);
+    }
+    return NNP_OK;
+}
+
+static int blocks_for(int n, int t) { return (n + t - 1) / t; }
+
+// Neighbour maintenance + descriptors + network + forces for one system.
+// Outputs (device, each nullable): energy[1], Ei_out[n], F_out[n*3], vir_out[9], G_out, dEdG_out [n][n_G].
+// stop_after: 0 full, 1 after descriptors, 2 after network.
+static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, const double* box, cudaStream_t st,
+                    double* energy, float* Ei_out, float* F_out, double* vir_out, float* G_out, float* dEdG_out,
+                    int stop_after)
+{
+    int rc = ensure_atoms(h, n);
+    if (rc) return rc;
+    const Plan& P = h->plan;
+    const double rcut = h->cutoff + h->skin;
+    // path and rebuild decision
+    bool same_box = h->list_valid && h->list_n == n;
+    for (int a = 0; a < 3; ++a) same_box = same_box && (h->list_box[a] == box[a]);
+    int nc[3];
+    bool cell = true;
+    for (int a = 0; a < 3; ++a) {
+        nc[a] = (int)std::floor(box[a] / rcut);
+        if (nc[a] < 3) cell = false;
+    }
+    int nim = 0;
+    for (int a = 0; a < 3; ++a) nim = std::max(nim, (int)std::ceil(rcut / box[a]));
+    if (!cell && nim > 2) return set_err(h, NNP_EBOX, "box too small for the image range");
+    Box bx;
+    for (int a = 0; a < 3; ++a) bx.L[a] = (float)box[a];
+    const int T = 256;
+    CK(h, cudaMemsetAsync(h->flags + FLAG_ERR, 0, sizeof(int), st));
+    if (!same_box) {
+        CK(h, cudaMemsetAsync(h->flags + FLAG_REBUILD, 1, sizeof(int), st));   // any non-zero value
+        h->cell_path = cell;
+        for (int a = 0; a < 3; ++a) h->nc[a] = nc[a];
+        const float4 sb = make_float4(bx.L[0], bx.L[1], bx.L[2], (float)nim);
+        CK(h, cudaMemcpyAsync(h->sys_box, &sb, sizeof(float4), cudaMemcpyHostToDevice, st));
+    } else {
+        CK(h, cudaMemsetAsync(h->flags + FLAG_REBUILD, 0, sizeof(int), st));
+        k_check_disp<<<blocks_for(n, T), T, 0, st>>>(n, pos, types, P.n_elem, h->off, h->ref, h->pos4, P.half_skin2, h->flags);
+    }
+    k_rebuild_pos<<<blocks_for(n, T), T, 0, st>>>(n, pos, types, bx, P.n_elem, h->off, h->pos4, h->ref, h->flags,
+                                                  h->counters);
+    const int rows_grid = std::min(blocks_for(n, 8), h->num_sms * 8);
+    if (h->cell_path) {
+        const int ncell = h->nc[0] * h->nc[1] * h->nc[2];
+        rc = ensure_cells(h, ncell);
+        if (rc) return rc;
+        CK(h, cudaMemsetAsync(h->cell_count, 0, sizeof(int) * (size_t)ncell, st));
+        k_cell_count<<<blocks_for(n, T), T, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_of,
+                                                     h->cell_count, h->flags);
+        k_cell_scan<<<1, 1024, 0, st>>>(ncell, h->cell_count, h->cell_start, h->cursor, h->flags);
+        k_cell_fill<<<blocks_for(n, T), T, 0, st>>>(n, h->cell_of, h->cursor, h->cell_atoms, h->flags);
+        k_cell_sort<<<std::min(blocks_for(ncell, 8), h->num_sms * 8), 256, 0, st>>>(ncell, h->cell_start,
+                                                                                    h->cell_atoms, h->flags);
+        k_rows_cell<<<rows_grid, 256, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_start,
+                                               h->cell_atoms, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
+    } else {
+        k_rows_brute<<<rows_grid, 256, 0, st>>>(n, h->pos4, nullptr, nullptr, h->sys_box, P.rcut2, h->stride, h->nbr,
+                                                h->ncount, h->flags);
+    }
+    k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
+    h->list_valid = true;
+    h->list_n = n;
+    for (int a = 0; a < 3; ++a) h->list_box[a] = box[a];
+
+    NbView nv{h->nbr, h->ncount, h->stride};
+    SfKernel ksf;
+    ForceKernel kf;
+    pick_kernels(P, ksf, kf);
+    CK(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CNT_REBUILDS, st));
+    const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
+    ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->G, G_out, h->flags,
+                                                 h->counters);
+    if (stop_after == 1 && !dEdG_out) return read_status(h, st);
+    const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
+    k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, h->pos4, h->d_plan, h->d_w, h->G, h->Ei, h->dEdG);
+    if (dEdG_out) CK(h, cudaMemcpy2DAsync(dEdG_out, sizeof(float) * P.width[0], h->dEdG, sizeof(float) * P.gs,
+                                          sizeof(float) * P.width[0], n, cudaMemcpyDeviceToDevice, st));
+    if (stop_after >= 1) return read_status(h, st);
+    const int gf = std::min(blocks_for(n, h->wpb_force), h->grid_force);
+    const int nvp = gf * h->wpb_force;
+    const int gred = std::min(blocks_for(n, T), 4 * h->num_sms);
+    rc = ensure_red(h, gred, nvp);
+    if (rc) return rc;
+    kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf,
+                                                     h->Fown, h->vpart, h->flags);
+    k_gather<<<rows_grid, 256, 0, st>>>(n, nv, h->rev, h->gbuf, h->Fown, F_out ? F_out : h->F, h->flags);
+    k_sum_partial<<<gred, T, 0, st>>>(n, h->Ei, h->epart, h->flags);
+    k_finalize<<<1, 256, 0, st>>>(gred, h->epart, energy ? energy : h->d_energy, nvp, h->vpart, vir_out);
+    if (Ei_out) CK(h, cudaMemcpyAsync(Ei_out, h->Ei, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    return NNP_OK;
+}
+
+// ---------------------------------------------------------------- public API
+extern "C" {
+
+const char* nnp_status_string(int s)
+{
+    switch (s) {
+    case NNP_OK: return "NNP_OK";
+    case NNP_EINVAL: return "NNP_EINVAL";
+    case NNP_ENOMEM: return "NNP_ENOMEM";
+    case NNP_ENEIGH_OVERFLOW: return "NNP_ENEIGH_OVERFLOW";
+    case NNP_ENONFINITE: return "NNP_ENONFINITE";
+    case NNP_EBOX: return "NNP_EBOX";
+    case NNP_ECUDA: return "NNP_ECUDA";
+    case NNP_EUNSUPPORTED: return "NNP_EUNSUPPORTED";
+    default: return "NNP_UNKNOWN";
+    }
+}
+
+const char* nnp_last_error(const nnp_handle* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int nnp_num_params(const nnp_handle* h) { return h ? h->n_params : 0; }
+
+int nnp_create(const nnp_params* params, int device, nnp_handle** out)
+{
+    if (!out) return set_err(nullptr, NNP_EINVAL, "out is NULL");
+    *out = nullptr;
+    g_create_err.clear();
+    Plan P;
+    int n_params = 0;
+    std::string why;
+    int rc = build_plan(params, P, n_params, why);
+    if (rc) return set_err(nullptr, rc, "%s", why.c_str());
+    if (params->mlp_precision == NNP_BF16)
+        return set_err(nullptr, NNP_EUNSUPPORTED, "the BF16 network path is not built in this library version");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return set_err(nullptr, NNP_ECUDA, "CUDA device %d not available", device);
+    nnp_handle* h = new nnp_handle();
+    h->device = device;
+    h->plan = P;
+    h->n_params = n_params;
+    h->cutoff = params->cutoff;
+    h->skin = params->skin;
+    h->stride = (params->max_neighbors + 3) & ~3;   // multiple of 4 keeps per-warp shared arrays 16-byte aligned
+    h->precision = params->mlp_precision;
+    h->cap_rc = h->stride;
+    DeviceGuard g(device);
+    auto fail = [&](int code) {
+        g_create_err = h->err;
+        nnp_destroy(h);
+        return code;
+    };
+#define CKC(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            set_err(h, e_ == cudaErrorMemoryAllocation ? NNP_ENOMEM : NNP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+            return fail(e_ == cudaErrorMemoryAllocation ? NNP_ENOMEM : NNP_ECUDA);                 \
+        }                                                                                          \
+    } while (0)
+    CKC(cudaMalloc((void**)&h->d_plan, sizeof(Plan)));
+    CKC(cudaMemcpy(h->d_plan, &P, sizeof(Plan), cudaMemcpyHostToDevice));
+    std::vector<float> w(n_params);
+    for (int i = 0; i < n_params; ++i) w[i] = (float)params->weights[i];
+    CKC(cudaMalloc((void**)&h->d_w, sizeof(float) * (size_t)n_params));
+    CKC(cudaMemcpy(h->d_w, w.data(), sizeof(float) * (size_t)n_params, cudaMemcpyHostToDevice));
+    CKC(cudaMalloc((void**)&h->flags, sizeof(int) * 4));
+    CKC(cudaMemset(h->flags, 0, sizeof(int) * 4));
+    CKC(cudaMallocHost((void**)&h->h_flags, sizeof(int) * 4));
+    CKC(cudaMalloc((void**)&h->counters, sizeof(unsigned long long) * CNT_N));
+    CKC(cudaMemset(h->counters, 0, sizeof(unsigned long long) * CNT_N));
+    CKC(cudaMalloc((void**)&h->sys_box, sizeof(float4) * 4));
+    CKC(cudaMalloc((void**)&h->d_energy, sizeof(double) * 4));
+    CKC(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device));
+    int max_smem = 0;
+    CKC(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    SfKernel ksf;
+    ForceKernel kf;
+    pick_kernels(P, ksf, kf);
+    // warps per block limited by shared memory
+    const size_t ps = sf_smem_per_warp(h->cap_rc), pf = force_smem_per_warp(h->cap_rc, h->stride);
+    h->wpb_sf = (int)std::min<size_t>(8, (size_t)max_smem / ps);
+    h->wpb_force = (int)std::min<size_t>(8, (size_t)max_smem / pf);
+    if (h->wpb_sf < 1 || h->wpb_force < 1) {
+        set_err(h, NNP_EINVAL, "max_neighbors = %d needs more shared memory than one block has", h->stride);
+        return fail(NNP_EINVAL);
+    }
+    h->smem_sf = ps * h->wpb_sf;
+    h->smem_force = pf * h->wpb_force;
+    h->smem_mlp = sizeof(float) * (size_t)P.s_elem * P.n_elem;
+    if (h->smem_mlp > (size_t)max_smem) {
+        set_err(h, NNP_EUNSUPPORTED, "network weights do not fit in shared memory");
+        return fail(NNP_EUNSUPPORTED);
+    }
+    CKC(cudaFuncSetAttribute((const void*)ksf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_sf));
+    CKC(cudaFuncSetAttribute((const void*)kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_force));
+    CKC(cudaFuncSetAttribute((const void*)k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_mlp));
+    int bs = 0;
+    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)ksf, 32 * h->wpb_sf, h->smem_sf));
+    h->grid_sf = std::max(1, bs) * h->num_sms;
+    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)kf, 32 * h->wpb_force, h->smem_force));
+    h->grid_force = std::max(1, bs) * h->num_sms;
+    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)k_mlp_fp32, 256, h->smem_mlp));
+    h->grid_mlp = std::max(1, bs) * h->num_sms;
+#undef CKC
+    *out = h;
+    return NNP_OK;
+}
+
+int nnp_destroy(nnp_handle* h)
+{
+    if (!h) return NNP_OK;
+    DeviceGuard g(h->device);
+    cudaDeviceSynchronize();
+    void* dev[] = {h->d_plan, h->d_w, h->off, h->ref, h->pos4, h->Fown, h->G, h->dEdG, h->Ei, h->F, h->nbr,
+                   h->ncount, h->rev, h->cell_of, h->cell_atoms, h->gbuf, h->cell_count, h->cell_start, h->cursor,
+                   h->epart, h->vpart, h->d_energy, h->d_log, h->flags, h->counters, h->sys_box};
+    for (void* p : dev)
+        if (p) cudaFree(p);
+    if (h->h_flags) cudaFreeHost(h->h_flags);
+    delete h;
+    return NNP_OK;
+}
+
+int nnp_set_weights(nnp_handle* h, const float* w, void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    if (!w) return set_err(h, NNP_EINVAL, "weights pointer is NULL");
+    DeviceGuard g(h->device);
+    CK(h, cudaMemcpyAsync(h->d_w, w, sizeof(float) * (size_t)h->n_params, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return NNP_OK;
+}
+
+static int common_args(nnp_handle* h, int n, const float* pos, const int* types, const double* box)
+{
+    if (n < 0) return set_err(h, NNP_EINVAL, "n_atoms must be >= 0");
+    if (n > (int)NB_INDEX_MASK) return set_err(h, NNP_EINVAL, "n_atoms must be < 2^24");
+    if (n > 0 && (!pos || !types)) return set_err(h, NNP_EINVAL, "pos and types must not be NULL");
+    return check_box(h, box);
+}
+
+int nnp_compute(nnp_handle* h, int n, const float* pos, const int* types, const double* box, double cutoff,
+                double* energy, float* atom_energy, float* forces, double* virial, void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    h->err.clear();
+    int rc = common_args(h, n, pos, types, box);
+    if (rc) return rc;
+    if (cutoff > 0.0 && std::fabs(cutoff - h->cutoff) > 1e-12 * h->cutoff)
+        return set_err(h, NNP_EINVAL, "cutoff %g differs from the model cutoff %g", cutoff, h->cutoff);
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        if (energy) CK(h, cudaMemsetAsync(energy, 0, sizeof(double), st));
+        if (virial) CK(h, cudaMemsetAsync(virial, 0, 9 * sizeof(double), st));
+        CK(h, cudaStreamSynchronize(st));
+        return NNP_OK;
+    }
+    rc = run_eval(h, n, pos, types, box, st, energy, atom_energy, forces, virial, nullptr, nullptr, 0);
+    if (rc) return rc;
+    return read_status(h, st);
+}
+
+int nnp_descriptors(nnp_handle* h, int n, const float* pos, const int* types, const double* box, float* G,
+                    float* dEdG, void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    h->err.clear();
+    int rc = common_args(h, n, pos, types, box);
+    if (rc) return rc;
+    if (n == 0) return NNP_OK;
+    DeviceGuard g(h->device);
+    return run_eval(h, n, pos, types, box, (cudaStream_t)stream, nullptr, nullptr, nullptr, nullptr, G, dEdG,
+                    dEdG ? 2 : 1);
+}
+
+int nnp_step(nnp_handle* h, int n, float* pos, float* vel, const int* types, const double* box, double dt_fs,
+             int n_steps, double* log, void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    h->err.clear();
+    int rc = common_args(h, n, pos, types, box);
+    if (rc) return rc;
+    if (n > 0 && !vel) return set_err(h, NNP_EINVAL, "vel must not be NULL");
+    if (!(dt_fs > 0.0) || !std::isfinite(dt_fs)) return set_err(h, NNP_EINVAL, "dt_fs must be > 0");
+    if (n_steps < 0) return set_err(h, NNP_EINVAL, "n_steps must be >= 0");
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        if (log) CK(h, cudaMemsetAsync(log, 0, sizeof(double) * 2 * ((size_t)n_steps + 1), st));
+        CK(h, cudaStreamSynchronize(st));
+        return NNP_OK;
+    }
+    if (!log) {
+        if (h->cap_log < n_steps + 1) {
+            CK(h, regrow(h->d_log, 2 * ((size_t)n_steps + 1)));
+            h->cap_log = n_steps + 1;
+        }
+        log = h->d_log;
+    }
+    const int T = 256;
+    const int gke = std::min(blocks_for(n, T), 4 * h->num_sms);
+    rc = ensure_red(h, gke, 0);
+    if (rc) return rc;
+    const float dt = (float)dt_fs;
+    rc = run_eval(h, n, pos, types, box, st, log, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+    if (rc) return rc;
+    // run_eval sized epart for its own reduction; the kinetic-energy partials reuse it
+    rc = ensure_red(h, gke, 0);
+    if (rc) return rc;
+    k_kick_ke<<<gke, T, 0, st>>>(n, h->d_plan, types, h->F, vel, 0.f, h->epart);
+    k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, log, 1);
+    for (int k = 1; k <= n_steps; ++k) {
+        k_kick_drift<<<blocks_for(n, T), T, 0, st>>>(n, h->d_plan, types, h->F, vel, pos, dt);
+        rc = run_eval(h, n, pos, types, box, st, log + 2 * k, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+        if (rc) return rc;
+        k_kick_ke<<<gke, T, 0, st>>>(n, h->d_plan, types, h->F, vel, dt, h->epart);
+        k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, log, 2 * k + 1);
+    }
+    return read_status(h, st);
+}
+
+int nnp_get_stats(nnp_handle* h, nnp_stats* out)
+{
+    if (!h || !out) return NNP_EINVAL;
+    DeviceGuard g(h->device);
+    unsigned long long c[CNT_N];
+    CK(h, cudaDeviceSynchronize());
+    CK(h, cudaMemcpy(c, h->counters, sizeof c, cudaMemcpyDeviceToHost));
+    out->n_atoms = h->list_n;
+    out->list_entries = (long long)c[CNT_LIST];
+    out->cutoff_entries = (long long)c[CNT_RC];
+    out->pairs = (long long)c[CNT_PAIRS];
+    out->triplets = (long long)c[CNT_TRIPLETS];
+    out->rebuilds = (long long)c[CNT_REBUILDS];
+    return NNP_OK;
+}
+
+}  // extern "C"

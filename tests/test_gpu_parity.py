@@ -1,0 +1,187 @@
+"""CUDA path (FP32) against the FP64 oracle on the same seeded inputs: descriptors,
+network input gradient, per-atom energies, forces, virial and energy, over the
+brute-force (small box, several images) and cell-list neighbour paths, the
+narrow (water) and wide (FCC) angular kinds, ragged sizes and edge cases."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from tests.gpuhelp import E_REL, F_ABS, check, energy_err, f32, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def water_nnp():
+    from paper_2002_00054_b300 import NNP
+    return NNP(workloads.water_model())
+
+
+@pytest.fixture(scope="module")
+def fcc_nnp():
+    from paper_2002_00054_b300 import NNP
+    return NNP(workloads.fcc_model())
+
+
+def _case(nnp, model, pos, types, box):
+    pos, box = f32(pos), f32(box)
+    ref = oracle.compute(model, pos, types, box)
+    p, t = to_dev(pos, types)
+    out = nnp.compute(p, t, box)
+    return ref, out, p, t, box
+
+
+def test_water_tiny_descriptors(water_nnp):
+    m = workloads.water_model()
+    pos, types, box = workloads.water_random()
+    pos, box = f32(pos), f32(box)
+    ref = oracle.compute(m, pos, types, box)
+    p, t = to_dev(pos, types)
+    G, dEdG = water_nnp.descriptors(p, t, box)
+    G = G.double().cpu().numpy()
+    np.testing.assert_allclose(G, ref["G"][:, :30], rtol=2e-6, atol=2e-6 * np.abs(ref["G"]).max(0))
+    dE = dEdG.double().cpu().numpy()
+    np.testing.assert_allclose(dE, ref["dEdG"][:, :30], rtol=1e-4, atol=1e-5 * np.abs(ref["dEdG"]).max())
+
+
+def test_water_tiny_energy_forces(water_nnp):
+    m = workloads.water_model()
+    ref, out, *_ = _case(water_nnp, m, *workloads.water_random())
+    check(out, ref, what="water 192")
+
+
+def test_water_lattice_cell_path(water_nnp):
+    m = workloads.water_model()
+    ref, out, *_ = _case(water_nnp, m, *workloads.water_lattice((2, 2, 2), seed=5))
+    assert water_nnp.stats()["n_atoms"] == 1536
+    check(out, ref, what="water 1536")
+
+
+@pytest.mark.parametrize("n_mol", [21, 22, 37])
+def test_water_ragged_small_boxes(water_nnp, n_mol):
+    """63-111 atoms at liquid density: box < 2 (rc + skin), several images per atom."""
+    m = workloads.water_model()
+    L = (3 * n_mol / workloads.WATER_DENSITY_ATOMS) ** (1 / 3)
+    ref, out, *_ = _case(water_nnp, m, *workloads.water_random(n_mol, L, seed=100 + n_mol))
+    check(out, ref, what="water %d" % (3 * n_mol))
+
+
+def test_fcc_4000_cell_path(fcc_nnp):
+    m = workloads.fcc_model()
+    ref, out, *_ = _case(fcc_nnp, m, *workloads.fcc((10, 10, 10)))
+    check(out, ref, what="fcc 4000")
+
+
+def test_fcc_small_box_images(fcc_nnp):
+    m = workloads.fcc_model()
+    ref, out, *_ = _case(fcc_nnp, m, *workloads.fcc((2, 2, 2), sigma=0.1, seed=4))
+    check(out, ref, what="fcc 32")
+
+
+def test_single_atom_sees_only_itself(fcc_nnp):
+    m = workloads.fcc_model()
+    ref, out, *_ = _case(fcc_nnp, m, np.array([[0.4, 1.1, 2.0]]), np.array([0], np.int32), np.array([4.0, 4.0, 4.0]))
+    check(out, ref, what="one atom")
+    assert np.abs(out["F"].cpu().numpy()).max() < 1e-5
+
+
+def test_empty_system(water_nnp):
+    p = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    t = torch.zeros((0,), dtype=torch.int32, device="cuda")
+    out = water_nnp.compute(p, t, [20.0, 20.0, 20.0])
+    assert out["energy"].item() == 0.0
+    assert out["F"].shape == (0, 3)
+
+
+def test_bitwise_repeatable(water_nnp):
+    pos, types, box = workloads.water_lattice((2, 2, 2), seed=6)
+    p, t = to_dev(f32(pos), types)
+    a = water_nnp.compute(p, t, f32(box))
+    water_nnp.compute(p + 0.3, t, f32(box))   # forces a rebuild in between
+    b = water_nnp.compute(p, t, f32(box))
+    assert torch.equal(a["F"], b["F"]) and torch.equal(a["Ei"], b["Ei"])
+    assert a["energy"].item() == b["energy"].item()
+
+
+def test_list_reuse_within_skin(water_nnp):
+    m = workloads.water_model()
+    pos, types, box = workloads.water_lattice((2, 2, 2), seed=7)
+    pos, box = f32(pos), f32(box)
+    p, t = to_dev(pos, types)
+    water_nnp.compute(p, t, box)
+    r0 = water_nnp.stats()["rebuilds"]
+    rng = np.random.default_rng(0)
+    moved = f32(pos + rng.uniform(-0.2, 0.2, pos.shape))   # |d| < 0.35 < skin / 2
+    pm, _ = to_dev(moved, types)
+    out = water_nnp.compute(pm, t, box)
+    assert water_nnp.stats()["rebuilds"] == r0
+    check(out, oracle.compute(m, moved, types, box), what="reused list")
+    far = f32(pos + rng.uniform(-0.8, 0.8, pos.shape))
+    pf, _ = to_dev(far, types)
+    out = water_nnp.compute(pf, t, box)
+    assert water_nnp.stats()["rebuilds"] == r0 + 1
+    check(out, oracle.compute(m, far, types, box), what="rebuilt list")
+
+
+def test_positions_outside_box(water_nnp):
+    """Unwrapped coordinates (atoms shifted by whole boxes) give the same result."""
+    m = workloads.water_model()
+    pos, types, box = workloads.water_random()
+    pos, box = f32(pos), f32(box)
+    shift = np.zeros_like(pos)
+    shift[::3, 0] = box[0]
+    shift[1::5, 2] = -box[2]
+    pos2 = f32(pos + shift)
+    ref = oracle.compute(m, pos, types, box)
+    p, t = to_dev(pos2, types)
+    out = water_nnp.compute(p, t, box)
+    check(out, ref, e_rel=E_REL, f_abs=F_ABS, what="unwrapped")
+
+
+def test_stats_counts(water_nnp):
+    pos, types, box = workloads.water_random()
+    p, t = to_dev(f32(pos), types)
+    water_nnp.compute(p, t, f32(box))
+    s = water_nnp.stats()
+    nb = oracle.neighbors(f32(pos), f32(box), 6.0)
+    assert s["cutoff_entries"] == sum(len(x[0]) for x in nb)
+    assert s["pairs"] == sum(len(x[0]) * (len(x[0]) - 1) // 2 for x in nb)
+    assert 0 < s["triplets"] < s["pairs"]
+
+
+# ------------------------------------------------------------- errors
+def test_overflow_is_reported():
+    from paper_2002_00054_b300 import NNP, NNPError
+    nnp = NNP(workloads.water_model(), max_neighbors=32)
+    pos, types, box = workloads.water_random()
+    p, t = to_dev(f32(pos), types)
+    with pytest.raises(NNPError) as e:
+        nnp.compute(p, t, f32(box))
+    assert e.value.status == 3
+    nnp.close()
+
+
+def test_nonfinite_and_bad_type_are_reported(water_nnp):
+    from paper_2002_00054_b300 import NNPError
+    pos, types, box = workloads.water_random()
+    p, t = to_dev(f32(pos), types)
+    q = p.clone(); q[5, 1] = float("nan")
+    with pytest.raises(NNPError) as e:
+        water_nnp.compute(q, t, f32(box))
+    assert e.value.status == 4
+    t2 = t.clone(); t2[3] = 7
+    with pytest.raises(NNPError) as e:
+        water_nnp.compute(p, t2, f32(box))
+    assert e.value.status == 4
+    out = water_nnp.compute(p, t, f32(box))   # handle still usable
+    assert np.isfinite(out["energy"].item())
+
+
+def test_box_too_small(water_nnp):
+    from paper_2002_00054_b300 import NNPError
+    p, t = to_dev(np.zeros((1, 3)), np.zeros(1, np.int32))
+    with pytest.raises(NNPError) as e:
+        water_nnp.compute(p, t, [3.0, 3.0, 3.0])
+    assert e.value.status == 5
