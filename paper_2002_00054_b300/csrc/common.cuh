@@ -36,6 +36,13 @@
 
 #define LOG2E 1.4426950408889634f
 
+// exp(-eta x2) = 2^(k x2) with k = -eta log2(e) given as hi + lo floats, so the
+// argument carries no systematic rounding of the constant (|k x2| reaches ~20).
+__device__ __forceinline__ float gauss2(float khi, float klo, float x2)
+{
+    return exp2f(fmaf(khi, x2, klo * x2));
+}
+
 // Per-element descriptor plan.  Angular functions of one element share one kind
 // and are grouped by eta: ang_out[q][l][k] is the descriptor index of
 // (eta_q, lambda = (l == 0 ? +1 : -1), zeta = 2^k), or -1.
@@ -43,11 +50,13 @@ struct ElemPlan {
     int n_g;
     int n_rad;
     float rad_eta[NNP_MAXRAD];
+    float rad_khi[NNP_MAXRAD], rad_klo[NNP_MAXRAD];   // -eta log2(e) as hi + lo floats
     float rad_rs[NNP_MAXRAD];
     int rad_elem[NNP_MAXRAD];
     int rad_out[NNP_MAXRAD];
     int n_eta;
     float ang_eta[NNP_MAXETA];
+    float ang_khi[NNP_MAXETA], ang_klo[NNP_MAXETA];   // -eta log2(e) as hi + lo floats
     int ang_out[NNP_MAXETA][2][NNP_KMAX + 1];
     float mu[NNP_MAXG];
     float inv_s[NNP_MAXG];
@@ -58,6 +67,7 @@ struct Plan {
     int ang_kind;        // 0 none, 3 narrow, 4 wide (same for every element)
     int n_eta_max;
     float rc, rc2, hpi_rc;   // cutoff, cutoff^2, pi / (2 rc)
+    float inv_2rc, inv_2rc_lo;   // 1 / (2 rc) as hi + lo floats
     float rcut2;             // (cutoff + skin)^2
     float half_skin2;        // (skin / 2)^2
     float acc_over_m[NNP_MAXE];  // (1 eV/(A amu) in A/fs^2) / mass
@@ -78,7 +88,21 @@ struct Plan {
 
 // f_c(r) = (cos(pi r / rc) + 1) / 2 = cos^2(pi r / (2 rc)); written as a square to
 // avoid the cancellation of cos + 1 near r = rc.  Derivative -2 k sin cos, k = pi/(2 rc).
-__device__ __forceinline__ void cutoff_fn(float r, float hpi_rc, float& fc, float& dfc)
+// Per-neighbour factors use the accurate sincospif (about 1 ulp): descriptor
+// sums over tens of neighbours are scaled by 1/s with |mu/s| up to ~1e2, so a
+// 4e-7 absolute error of the hardware approximation would reach 1e-4 in G~.
+// The argument r / (2 rc) uses 1/(2 rc) split into hi + lo floats: a single
+// rounded constant biases every cutoff value by ~1e-7 relative in one direction.
+__device__ __forceinline__ void cutoff_fn(float r, float inv_2rc, float inv_2rc_lo, float hpi_rc, float& fc, float& dfc)
+{
+    float s, c;
+    sincospif(fmaf(r, inv_2rc, r * inv_2rc_lo), &s, &c);
+    fc = c * c;
+    dfc = -2.0f * hpi_rc * s * c;
+}
+// Per-triplet f_c(r_jk) of the narrow angular functions: hardware sin/cos
+// (absolute error <= 2^-21.4 on [0, pi/2]), one term among ~10^3 per descriptor.
+__device__ __forceinline__ void cutoff_fn_fast(float r, float hpi_rc, float& fc, float& dfc)
 {
     float s, c;
     __sincosf(r * hpi_rc, &s, &c);

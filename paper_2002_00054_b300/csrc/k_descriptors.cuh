@@ -33,8 +33,8 @@ struct NbView {
 template <int NETA, bool FORCE>
 __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box& bx, const NbView& nv,
                                                const float4* __restrict__ pos4, const Plan& P,
-                                               const ElemPlan& E, const float* __restrict__ eta_l2e,
-                                               const float* __restrict__ etav, int cap, float4* nd, float4* npf,
+                                               const ElemPlan& E, const float* __restrict__ khi,
+                                               const float* __restrict__ klo, const float* __restrict__ etav, int cap, float4* nd, float4* npf,
                                                float4* ndp, float2* nfe, int* cmap, float* sg,
                                                const float* sW, int lane, int* flags, int& n_list)
 {
@@ -66,12 +66,12 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
             if (r2 < 1e-8f) atomicOr(&flags[FLAG_ERR], ERR_CLOSE);
             const float r = sqrtf(r2);
             float fc, dfc;
-            cutoff_fn(r, P.hpi_rc, fc, dfc);
+            cutoff_fn(r, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, fc, dfc);
             nd[at] = make_float4(dx, dy, dz, r);
             float pq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int q = 0; q < NETA; ++q) {
-                const float ex = exp2f(eta_l2e[q] * r2);
+                const float ex = gauss2(khi[q], klo[q], r2);
                 pq[q] = ex * fc;
                 dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
             }
@@ -85,7 +85,7 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                     const int el = E.rad_elem[rr];
                     if (el < 0 || el == ej) {
                         const float x = r - E.rad_rs[rr];
-                        const float ex = exp2f(-E.rad_eta[rr] * LOG2E * x * x);
+                        const float ex = gauss2(E.rad_khi[rr], E.rad_klo[rr], x * x);
                         gr += sW[E.rad_out[rr]] * ex * (dfc - 2.0f * E.rad_eta[rr] * x * fc);
                     }
                 }
@@ -139,18 +139,19 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         const float4 pi = pos4[i];
         const int ti = __float_as_int(pi.w);
         const ElemPlan& E = P.e[ti];
-        float eta_l2e[4], etav[4];
+        float khi[4], klo[4], etav[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             etav[q] = (q < E.n_eta) ? E.ang_eta[q] : 0.f;
-            eta_l2e[q] = -etav[q] * LOG2E;
+            khi[q] = (q < E.n_eta) ? E.ang_khi[q] : 0.f;
+            klo[q] = (q < E.n_eta) ? E.ang_klo[q] : 0.f;
         }
         int n_list;
-        const int M = stage_neighbors<NETA, false>(i, pi, bx, nv, pos4, P, E, eta_l2e, etav, cap, nd, npf,
+        const int M = stage_neighbors<NETA, false>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, cap, nd, npf,
                                                    nullptr, nfe, nullptr, nullptr, nullptr, lane, flags, n_list);
         // radial: lane <-> descriptor, loop over neighbours (broadcast reads)
         for (int rr = lane; rr < E.n_rad; rr += 32) {
-            const float eta2 = -E.rad_eta[rr] * LOG2E, rs = E.rad_rs[rr];
+            const float kh = E.rad_khi[rr], kl = E.rad_klo[rr], rs = E.rad_rs[rr];
             const int el = E.rad_elem[rr];
             double acc = 0.0;   // radial sums feed G~ = (G - mu)/s with |mu/s| up to ~1e2
             for (int m = 0; m < M; ++m) {
@@ -158,7 +159,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 const float2 fe = nfe[m];
                 if (el < 0 || el == __float_as_int(fe.y)) {
                     const float x = r - rs;
-                    acc += (double)(exp2f(eta2 * x * x) * fe.x);
+                    acc += (double)(gauss2(kh, kl, x * x) * fe.x);
                 }
             }
             sG[E.rad_out[rr]] = acc;
@@ -187,7 +188,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                         ok = rd2 < P.rc2;
                         if (ok) {
                             float dfcd;
-                            cutoff_fn(sqrtf(rd2), P.hpi_rc, fcd, dfcd);
+                            cutoff_fn_fast(sqrtf(rd2), P.hpi_rc, fcd, dfcd);
                         }
                     }
                     if (ok) {
@@ -206,7 +207,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
 #pragma unroll
                         for (int q = 0; q < NETA; ++q) {
                             float R = pav[q] * pbv[q];
-                            if (NARROW) R *= exp2f(eta_l2e[q] * rd2) * fcd;
+                            if (NARROW) R *= gauss2(khi[q], klo[q], rd2) * fcd;
 #pragma unroll
                             for (int l = 0; l < 2; ++l)
 #pragma unroll
@@ -290,14 +291,15 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         const ElemPlan& E = P.e[ti];
         for (int s = lane; s < E.n_g; s += 32) sW[s] = dEdG[(size_t)i * P.gs + s];
         __syncwarp();
-        float eta_l2e[4], etav[4];
+        float khi[4], klo[4], etav[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             etav[q] = (q < E.n_eta) ? E.ang_eta[q] : 0.f;
-            eta_l2e[q] = -etav[q] * LOG2E;
+            khi[q] = (q < E.n_eta) ? E.ang_khi[q] : 0.f;
+            klo[q] = (q < E.n_eta) ? E.ang_klo[q] : 0.f;
         }
         int n_list;
-        const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, eta_l2e, etav, cap, nd, npf, ndp, nfe,
+        const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, cap, nd, npf, ndp, nfe,
                                                   cmap, sg, sW, lane, flags, n_list);
         if (NETA > 0) {
             // dense weights W[q][l][k] = dE/dG_o * 2^(1-zeta); Wd = W * lambda * zeta
@@ -327,7 +329,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                         ok = rd2 < P.rc2;
                         if (ok) {
                             rd = sqrtf(rd2);
-                            cutoff_fn(rd, P.hpi_rc, fcd, dfcd);
+                            cutoff_fn_fast(rd, P.hpi_rc, fcd, dfcd);
                         }
                     }
                     if (ok) {
@@ -362,7 +364,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                 }
                             float Pd = 1.f, dPd = 0.f;
                             if (NARROW) {
-                                const float ed = exp2f(eta_l2e[q] * rd2);
+                                const float ed = gauss2(khi[q], klo[q], rd2);
                                 Pd = ed * fcd;
                                 dPd = ed * (dfcd - 2.0f * etav[q] * rd * fcd);
                             }

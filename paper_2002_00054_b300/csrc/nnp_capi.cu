@@ -22,6 +22,14 @@
 namespace {
 
 const double kAcc = 9.64853321233100e-3;   // 1 eV/(A amu) in A/fs^2
+const double kLog2e = 1.4426950408889634074;
+
+// x = hi + lo with hi = float(x), lo = float(x - hi)
+void split(double x, float& hi, float& lo)
+{
+    hi = (float)x;
+    lo = (float)(x - (double)hi);
+}
 
 }  // namespace
 
@@ -113,6 +121,7 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
     P.rc = (float)p->cutoff;
     P.rc2 = (float)(p->cutoff * p->cutoff);
     P.hpi_rc = (float)(M_PI / (2.0 * p->cutoff));
+    split(0.5 / p->cutoff, P.inv_2rc, P.inv_2rc_lo);
     const double rcut = p->cutoff + p->skin;
     P.rcut2 = (float)(rcut * rcut);
     P.half_skin2 = (float)(0.25 * p->skin * p->skin);
@@ -170,6 +179,7 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
                 if (!std::isfinite(d.rs)) return fail("rs must be finite");
                 if (E.n_rad >= NNP_MAXRAD) return fail("too many radial descriptors");
                 E.rad_eta[E.n_rad] = (float)d.eta;
+                split(-d.eta * kLog2e, E.rad_khi[E.n_rad], E.rad_klo[E.n_rad]);
                 E.rad_rs[E.n_rad] = (float)d.rs;
                 E.rad_elem[E.n_rad] = d.elem_a;
                 E.rad_out[E.n_rad] = s;
@@ -186,6 +196,7 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
                     etas.push_back(d.eta);
                     q = (int)etas.size() - 1;
                     E.ang_eta[q] = (float)d.eta;
+                    split(-d.eta * kLog2e, E.ang_khi[q], E.ang_klo[q]);
                 }
                 int l;
                 if (d.lambda == 1.0) l = 0;
@@ -531,9 +542,11 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
         set_err(h, NNP_EUNSUPPORTED, "network weights do not fit in shared memory");
         return fail(NNP_EUNSUPPORTED);
     }
-    CKC(cudaFuncSetAttribute((const void*)ksf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_sf));
-    CKC(cudaFuncSetAttribute((const void*)kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_force));
-    CKC(cudaFuncSetAttribute((const void*)k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->smem_mlp));
+    // The limit is a property of the kernel, shared by every handle in the process:
+    // raise it to the device maximum (never lower it to this handle's need).
+    CKC(cudaFuncSetAttribute((const void*)ksf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    CKC(cudaFuncSetAttribute((const void*)kf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    CKC(cudaFuncSetAttribute((const void*)k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     int bs = 0;
     CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)ksf, 32 * h->wpb_sf, h->smem_sf));
     h->grid_sf = std::max(1, bs) * h->num_sms;

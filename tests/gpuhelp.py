@@ -5,10 +5,19 @@ import torch
 
 import oracle
 
-# FP32 path tolerances: per-atom energy |dE_i| <= 1e-5 * max(|E_i|, rms(E)),
-# forces <= 1e-4 eV/A max-abs (against the FP64 oracle).
+# FP32 path tolerances against the FP64 oracle:
+#   forces: <= 1e-4 eV/A max-abs;
+#   per-atom energy: |dE_i| <= max(1e-5 * max(|E_i|, rms(E)),  KAPPA * u * sum_s |dE_i/dG_s * G_s|).
+# The second term is the floor that float32 descriptors impose: every descriptor
+# is a sum of positive terms, each rounded to u = 2^-24 relative, so E_i cannot be
+# known better than u times its condition number sum_s |dE_i/dG_s G_s|.  For the
+# water model that floor is ~1e-6 of |E_i| and the 1e-5 bound decides; for the FCC
+# model (per-atom energies ~0.1 eV, |mu/s| up to 18) it is ~3e-5 of |E_i|.
+# KAPPA = 4 allows the few ulp of exp/cos/sqrt in each term.
 E_REL = 1e-5
 F_ABS = 1e-4
+KAPPA = 4.0
+U32 = 2.0 ** -24
 
 
 def f32(x):
@@ -26,15 +35,25 @@ def energy_err(Ei, ref_Ei):
     return np.max(np.abs(Ei - ref_Ei) / scale)
 
 
+def energy_tol(ref, e_rel=E_REL):
+    """Per-atom energy tolerance (see the module comment)."""
+    Ei = ref["Ei"]
+    scale = np.maximum(np.abs(Ei), np.sqrt(np.mean(Ei ** 2)))
+    cond = np.abs(ref["dEdG"] * ref["G"]).sum(1)
+    return np.maximum(e_rel * scale, KAPPA * U32 * cond)
+
+
 def check(out, ref, e_rel=E_REL, f_abs=F_ABS, what=""):
     Ei = out["Ei"].double().cpu().numpy()
     F = out["F"].double().cpu().numpy()
     ee = energy_err(Ei, ref["Ei"])
     fe = np.abs(F - ref["F"]).max() if len(F) else 0.0
-    assert ee <= e_rel, "%s per-atom energy rel err %.3g" % (what, ee)
+    tol = energy_tol(ref, e_rel)
+    worst = np.max(np.abs(Ei - ref["Ei"]) / tol) if len(Ei) else 0.0
+    assert worst <= 1.0, "%s per-atom energy err %.3g of tolerance (rel err %.3g)" % (what, worst, ee)
     assert fe <= f_abs, "%s force max-abs err %.3g" % (what, fe)
     E = out["energy"].item()
-    tol_e = e_rel * np.abs(ref["Ei"]).sum() + 1e-12
+    tol_e = tol.sum() + 1e-12
     assert abs(E - ref["energy"]) <= tol_e, "%s total energy %r vs %r" % (what, E, ref["energy"])
     if out.get("virial") is not None and "virial" in ref:
         W = out["virial"].cpu().numpy()
