@@ -1,0 +1,317 @@
+"""Benchmark of the NNP hot path on B300: atom-steps/s of velocity-Verlet MD with
+energy and forces every step, on the 2,064,384-atom water-like workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload water_2m|water_110k|water_1m|fcc_1m] [--no-cpu-baseline]
+
+Prints one JSON line (rank 0).  The timed region is one nnp_step call of K steps
+(device-resident inputs; neighbour-list maintenance included), bracketed by a
+barrier and device synchronisation on both sides, max over ranks.  Each rank
+runs its own copy of the workload (weak scaling, no collective on the data
+path).  --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "atom-steps/sec (E+F) at 1 B300, FP32 vs BF16-MLP at stated force error; % roofline"
+UNIT = "atom-steps/s"
+DT_FS = 0.5
+WORKLOADS = {
+    "water_2m": ("water_lattice", (16, 24, 28), "2,064,384-atom water-like box (lattice + sigma 0.1 A noise), "
+                 "FP32, cutoff 6.0 A, skin 1.0 A, n_G 30, network 30-25-25-1", 200),
+    "water_110k": ("water_lattice", (8, 8, 9), "110,592-atom water-like box, FP32", 200),
+    "water_1m": ("water_lattice", (13, 20, 21), "1,048,320-atom water-like box, FP32", 200),
+    "fcc_1m": ("fcc", (64, 64, 64), "1,048,576-atom FCC metal-like crystal, a 3.52 A, sigma 0.05 A, "
+               "cutoff 5.5 A, n_G 40, network 40-30-30-1, FP32", 160),
+}
+# FP32 peak from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flops x 2032 MHz.
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2032e6 / 1e12
+MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
+# DRAM traffic per atom-evaluation of each kernel group from the ncu capture
+# summarised in profiles/ (filled in with the source hash it was taken at).
+TRAFFIC = {}
+TRAFFIC_SRC_SHA = None
+
+
+def src_sha():
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2002_00054_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def make_workload(name):
+    kind, arg, desc, max_nb = WORKLOADS[name]
+    if kind == "water_lattice":
+        pos, types, box = workloads.water_lattice(arg)
+        model = workloads.water_model()
+    else:
+        pos, types, box = workloads.fcc(arg)
+        model = workloads.fcc_model()
+    box = np.asarray(box, np.float32).astype(np.float64)
+    return model, np.asarray(pos, np.float32), np.asarray(types, np.int32), box, desc, max_nb
+
+
+def sample_clocks_start(index):
+    f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+    try:
+        p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                              "-lms", "200"], stdout=f, stderr=subprocess.DEVNULL)
+    except OSError:
+        p = None
+    return p, f.name
+
+
+def sample_clocks_stop(p, path):
+    if p is not None:
+        p.terminate()
+        try:
+            p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            p.kill()
+    sm, mx, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        with open(path) as f:
+            for line in f:
+                c = [x.strip() for x in line.split(",")]
+                if len(c) < 9:
+                    continue
+                try:
+                    sm.append(float(c[1]))
+                    mx.append(float(c[2]))
+                except ValueError:
+                    continue
+                for k, nm in enumerate(names):
+                    if c[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(path)
+    except OSError:
+        pass
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(model_name, budget_s=12.0):
+    """The FP64 oracle, as it stands, on a 1,536-atom sample of the same workload
+    recipe (2x2x2 replica cells of the water lattice, or a 6x6x8 FCC box):
+    neighbour search + energy + forces per evaluation, repeated for ~budget_s."""
+    import oracle
+    if model_name == "water":
+        pos, types, box = workloads.water_lattice((2, 2, 2))
+        model = workloads.water_model()
+        sample = "1,536-atom water-like box (2x2x2 replicas of the same lattice recipe), E+F per evaluation"
+    else:
+        pos, types, box = workloads.fcc((6, 6, 8))
+        model = workloads.fcc_model()
+        sample = "1,152-atom FCC box (same recipe), E+F per evaluation"
+    cores = oracle.set_threads(0)
+    m = oracle.Model(model)
+    oracle.compute(m, pos, types, box)
+    n_eval, t0 = 0, time.perf_counter()
+    while True:
+        oracle.compute(m, pos, types, box)
+        n_eval += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return {"value": len(pos) * n_eval / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%s; %d evaluations in %.1f s on %d threads" % (sample, n_eval, el, cores)}
+
+
+def reference_arm(args, rank):
+    """FP64 CPU oracle MD on a bounded sample of the workload (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    name = WORKLOADS[args.workload][0]
+    if name == "water_lattice":
+        pos, types, box = workloads.water_lattice((2, 2, 2))
+        model = workloads.water_model()
+        sample = "1,536-atom water-like box (2x2x2 replicas of the workload's lattice recipe)"
+    else:
+        pos, types, box = workloads.fcc((6, 6, 8))
+        model = workloads.fcc_model()
+        sample = "1,152-atom FCC box (the workload's recipe)"
+    vel = workloads.maxwell_boltzmann(types, model["masses"])
+    cores = oracle.set_threads(0)
+    m = oracle.Model(model)
+    p, v, _ = oracle.md(m, pos, vel, types, box, DT_FS, args.warmup)
+    t0 = time.perf_counter()
+    oracle.md(m, p, v, types, box, DT_FS, args.steps)
+    el = time.perf_counter() - t0
+    # oracle.md evaluates forces once at its start and once per step
+    value = len(pos) * args.steps / el
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / max(1, args.steps),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water_2m", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2002_00054_b300 import NNP, opcount
+
+    model, pos_h, types_h, box, desc, max_nb = make_workload(args.workload)
+    n = len(pos_h)
+    vel_h = workloads.maxwell_boltzmann(types_h, model["masses"]).astype(np.float32)
+    nnp = NNP(model, device=local, max_neighbors=max_nb)
+    pos = torch.from_numpy(pos_h).to(dev)
+    vel = torch.from_numpy(vel_h).to(dev)
+    types = torch.from_numpy(types_h).to(dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up steps (list build, caches); the timed call continues from their final state
+    nnp.step(pos, vel, types, box, DT_FS, args.warmup)
+    nnp.profile(True)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    smi, smi_path = sample_clocks_start(local)
+    barrier()
+    e0.record(stream)
+    log = nnp.step(pos, vel, types, box, DT_FS, args.steps)
+    e1.record(stream)
+    barrier()
+    clocks = sample_clocks_stop(smi, smi_path)
+    ms = e0.elapsed_time(e1)
+    st = nnp.stats()
+    ktimes = nnp.kernel_times()
+    nnp.profile(False)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = n * args.steps * world / (t_max * 1e-3)
+    logn = log.cpu().numpy()
+    drift = float(abs(logn[-1].sum() - logn[0].sum()) / n)
+
+    # ---- end to end: host buffers in, energy + forces out, every step
+    pos_pin = torch.from_numpy(pos.cpu().numpy()).pin_memory()
+    types_pin = torch.from_numpy(types_h).pin_memory()
+    f_pin = torch.empty((n, 3), dtype=torch.float32).pin_memory()
+    e_pin = torch.empty(1, dtype=torch.float64).pin_memory()
+    pos_d = torch.empty_like(pos)
+    types_d = torch.empty_like(types)
+    f_d = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    e_d = torch.empty(1, dtype=torch.float64, device=dev)
+    for _ in range(2):
+        pos_d.copy_(pos_pin, non_blocking=True)
+        types_d.copy_(types_pin, non_blocking=True)
+        nnp.compute_into(pos_d, types_d, box, e_d, F=f_d)
+    barrier()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.e2e_steps):
+        pos_d.copy_(pos_pin, non_blocking=True)
+        types_d.copy_(types_pin, non_blocking=True)
+        nnp.compute_into(pos_d, types_d, box, e_d, F=f_d)
+        f_pin.copy_(f_d, non_blocking=True)
+        e_pin.copy_(e_d, non_blocking=True)
+    a1.record(stream)
+    barrier()
+    e2e_ms = a0.elapsed_time(a1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": n * args.e2e_steps * world / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": n * 12 + n * 4, "d2h_bytes_per_step": n * 12 + 8,
+           "call": "nnp_compute per step with host pinned positions/types in and forces/energy out"}
+
+    # ---- roofline of the dominant kernel group (FP32 ALU bound)
+    units = (st["list_entries"], st["cutoff_entries"], st["pairs"], st["triplets"])
+    ops = {"descriptors": opcount.descriptor_ops(model, *units), "force": opcount.force_ops(model, *units),
+           "network": opcount.network_ops(model, n * args.steps)}
+    timed = {k: v for k, v in ktimes.items() if v[1] > 0}
+    dom = max(("descriptors", "force"), key=lambda k: timed.get(k, (0, 0))[0])
+    dom_ms, dom_launch = timed[dom]
+    fl, mu = ops[dom]
+    achieved = fl / (dom_ms * 1e-3) / 1e12
+    sha = src_sha()
+    traffic = None
+    if TRAFFIC_SRC_SHA == sha and dom in TRAFFIC:
+        traffic = TRAFFIC[dom] * n
+    roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+            "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (unit counts and max clock)",
+            "mufu_gops": mu / (dom_ms * 1e-3) / 1e9, "mufu_peak_gops": MUFU_PEAK_GOPS,
+            "avg_launch_ms": dom_ms / dom_launch, "launches": dom_launch}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": args.workload, "description": desc, "atoms_per_gpu": n, "dt_fs": DT_FS,
+                      "parallelism": "replicas" if world > 1 else "single",
+                      "l2": "inputs larger than L2: neighbour list, reverse index and pair-force buffer are "
+                            "%.1f GB per GPU" % (n * max_nb * 24 / 1e9),
+                      "mlp_precision": "fp32"},
+           "e2e": e2e, "gpu_launches": st["kernel_launches"], "roofline": roof, "clocks": clocks,
+           "kernels_ms": {k: round(v[0], 3) for k, v in timed.items()},
+           "work": {"list_entries": units[0], "cutoff_entries": units[1], "pairs": units[2], "triplets": units[3],
+                    "rebuilds_total": st["rebuilds"]},
+           "nve_drift_ev_per_atom": drift}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(model["name"])
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -152,11 +152,15 @@ NNP_API int nnp_descriptors(nnp_handle* h, int n_atoms, const float* pos, const 
  * pos, vel: device float [n_atoms][3], updated in place (positions are not wrapped).
  * vel in A/fs; dt_fs > 0; n_steps >= 0.  pe_ke_log: device double [n_steps + 1][2]
  * of (potential, kinetic) energy in eV before the first and after every step
- * (nullable).  Forces at the start are computed by the call. */
+ * (nullable).  Forces at the start are computed by the call, unless the previous
+ * call on h was nnp_step on the same pos/types buffers, n_atoms and box and the
+ * positions and types are bitwise unchanged since it returned (checked on the
+ * device); then that call's final forces and energy are reused. */
 NNP_API int nnp_step(nnp_handle* h, int n_atoms, float* pos, float* vel, const int* types, const double* box,
              double dt_fs, int n_steps, double* pe_ke_log, void* stream);
 
-/* Neighbour and work counters of the last compute (synchronises the handle's device). */
+/* Work counters summed over the last nnp_compute / nnp_descriptors / nnp_step
+ * call (rebuilds: since creation).  Synchronises the handle's device. */
 typedef struct {
     long long n_atoms;
     long long list_entries;    /* neighbour-list entries within cutoff + skin      */
@@ -164,8 +168,21 @@ typedef struct {
     long long pairs;           /* neighbour pairs j < k examined by the angular loop */
     long long triplets;        /* pairs that contribute (narrow: r_jk < r_c)       */
     long long rebuilds;        /* neighbour-list builds since creation             */
+    long long kernel_launches; /* CUDA kernels launched by the last call           */
 } nnp_stats;
 NNP_API int nnp_get_stats(nnp_handle* h, nnp_stats* out);
+
+/* ------------------------------------------------------- kernel timing */
+/* Per-kernel device time, measured with CUDA events recorded on the call's
+ * stream around every kernel group of a call (no extra synchronisation; the
+ * events are read at the call's final synchronisation).
+ *   nnp_profile(h, 1) clears the totals and starts recording; nnp_profile(h, 0) stops.
+ *   nnp_kernel_times fills total_ms[k] and launches[k] for kernel groups
+ *   k < min(max_groups, nnp_num_kernel_groups()); returns the count written. */
+NNP_API int nnp_profile(nnp_handle* h, int enable);
+NNP_API int nnp_num_kernel_groups(void);
+NNP_API const char* nnp_kernel_group_name(int k);
+NNP_API int nnp_kernel_times(nnp_handle* h, int max_groups, double* total_ms, long long* launches);
 
 #ifdef __cplusplus
 }

@@ -35,7 +35,8 @@ class Params(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_longlong), ("list_entries", ctypes.c_longlong),
                 ("cutoff_entries", ctypes.c_longlong), ("pairs", ctypes.c_longlong),
-                ("triplets", ctypes.c_longlong), ("rebuilds", ctypes.c_longlong)]
+                ("triplets", ctypes.c_longlong), ("rebuilds", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/nnp.h
@@ -53,6 +54,10 @@ SIGNATURES = {
     "nnp_descriptors": (I, [V, I, V, V, c_double_p, V, V, V]),
     "nnp_step": (I, [V, I, V, V, V, c_double_p, D, I, V, V]),
     "nnp_get_stats": (I, [V, ctypes.POINTER(Stats)]),
+    "nnp_profile": (I, [V, I]),
+    "nnp_num_kernel_groups": (I, []),
+    "nnp_kernel_group_name": (ctypes.c_char_p, [I]),
+    "nnp_kernel_times": (I, [V, I, c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
 }
 
 _lib = None

@@ -71,6 +71,24 @@ struct nnp_handle {
     bool cell_path = false;
     int nc[3] = {0, 0, 0};
 
+    // nnp_step continuation: final state of the last nnp_step call
+    bool step_valid = false;
+    const float* step_pos = nullptr;
+    const int* step_types = nullptr;
+    int step_n = -1;
+    double step_box[3] = {0, 0, 0};
+    float* pos_cache = nullptr;
+    int* types_cache = nullptr;
+
+    // kernel-group timing (CUDA events on the call's stream)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct Pending { int id; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    double prof_ms[8] = {0};
+    long long prof_n[8] = {0};
+    long long launches = 0;   // kernels launched by the current / last call
+
     // launch configuration
     int num_sms = 148;
     int wpb_sf = 8, wpb_force = 8;
@@ -281,8 +299,11 @@ static int ensure_atoms(nnp_handle* h, int n)
     CK(h, regrow(h->gbuf, rows));
     CK(h, regrow(h->cell_of, cap));
     CK(h, regrow(h->cell_atoms, cap));
+    CK(h, regrow(h->pos_cache, (size_t)cap * 3));
+    CK(h, regrow(h->types_cache, cap));
     h->cap_n = cap;
     h->list_valid = false;
+    h->step_valid = false;
     return NNP_OK;
 }
 
@@ -324,6 +345,60 @@ struct DeviceGuard {
     }
 };
 
+enum { KG_NEIGH = 0, KG_SF, KG_MLP, KG_FORCE, KG_GATHER, KG_REDUCE, KG_INTEGRATE, KG_N };
+static const char* kKgName[KG_N] = {"neighbor_maintenance", "descriptors", "network", "force", "gather",
+                                    "reductions", "integrate"};
+
+static cudaEvent_t ev_get(nnp_handle* h)
+{
+    cudaEvent_t e = nullptr;
+    if (!h->ev_pool.empty()) {
+        e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+// Times the kernels launched in its lifetime (when profiling is on) and counts launches.
+struct KScope {
+    nnp_handle* h;
+    int id;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    int n_kernels;
+    KScope(nnp_handle* h_, int id_, cudaStream_t st_, int n_kernels_ = 1) : h(h_), id(id_), st(st_), n_kernels(n_kernels_)
+    {
+        h->launches += n_kernels;
+        if (h->prof_on && (a = ev_get(h))) cudaEventRecord(a, st);
+    }
+    ~KScope()
+    {
+        if (!h->prof_on || !a) return;
+        cudaEvent_t b = ev_get(h);
+        if (!b) return;
+        cudaEventRecord(b, st);
+        h->pending.push_back({id, a, b});
+    }
+};
+
+// Accumulates finished event pairs (call after the stream has been synchronised).
+static void prof_flush(nnp_handle* h)
+{
+    for (auto& p : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            h->prof_ms[p.id] += ms;
+            h->prof_n[p.id] += 1;
+        }
+        h->ev_pool.push_back(p.a);
+        h->ev_pool.push_back(p.b);
+    }
+    h->pending.clear();
+    cudaGetLastError();
+}
+
 static int check_box(nnp_handle* h, const double* box)
 {
     if (!box) return set_err(h, NNP_EINVAL, "box is NULL");
@@ -341,10 +416,12 @@ static int read_status(nnp_handle* h, cudaStream_t st)
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(h->h_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
+    prof_flush(h);
     const int f = h->h_flags[0];
     if (f) {
-        // errors leave the neighbour list in an unknown state
+        // errors leave the neighbour list and the step state unknown
         h->list_valid = false;
+        h->step_valid = false;
         if (f & (ERR_NEIGH_OVERFLOW | ERR_RC_OVERFLOW))
             return set_err(h, NNP_ENEIGH_OVERFLOW, "an atom has more than max_neighbors = %d neighbours", h->stride);
         if (f & ERR_CELL_OVERFLOW) return set_err(h, NNP_ENEIGH_OVERFLOW, "a cell holds more than %d atoms", CELL_CAP);
@@ -385,37 +462,46 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     for (int a = 0; a < 3; ++a) bx.L[a] = (float)box[a];
     const int T = 256;
     CK(h, cudaMemsetAsync(h->flags + FLAG_ERR, 0, sizeof(int), st));
-    if (!same_box) {
-        CK(h, cudaMemsetAsync(h->flags + FLAG_REBUILD, 1, sizeof(int), st));   // any non-zero value
-        h->cell_path = cell;
-        for (int a = 0; a < 3; ++a) h->nc[a] = nc[a];
-        const float4 sb = make_float4(bx.L[0], bx.L[1], bx.L[2], (float)nim);
-        CK(h, cudaMemcpyAsync(h->sys_box, &sb, sizeof(float4), cudaMemcpyHostToDevice, st));
-    } else {
-        CK(h, cudaMemsetAsync(h->flags + FLAG_REBUILD, 0, sizeof(int), st));
-        k_check_disp<<<blocks_for(n, T), T, 0, st>>>(n, pos, types, P.n_elem, h->off, h->ref, h->pos4, P.half_skin2, h->flags);
-    }
-    k_rebuild_pos<<<blocks_for(n, T), T, 0, st>>>(n, pos, types, bx, P.n_elem, h->off, h->pos4, h->ref, h->flags,
-                                                  h->counters);
     const int rows_grid = std::min(blocks_for(n, 8), h->num_sms * 8);
-    if (h->cell_path) {
-        const int ncell = h->nc[0] * h->nc[1] * h->nc[2];
-        rc = ensure_cells(h, ncell);
-        if (rc) return rc;
-        CK(h, cudaMemsetAsync(h->cell_count, 0, sizeof(int) * (size_t)ncell, st));
-        k_cell_count<<<blocks_for(n, T), T, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_of,
-                                                     h->cell_count, h->flags);
-        k_cell_scan<<<1, 1024, 0, st>>>(ncell, h->cell_count, h->cell_start, h->cursor, h->flags);
-        k_cell_fill<<<blocks_for(n, T), T, 0, st>>>(n, h->cell_of, h->cursor, h->cell_atoms, h->flags);
-        k_cell_sort<<<std::min(blocks_for(ncell, 8), h->num_sms * 8), 256, 0, st>>>(ncell, h->cell_start,
-                                                                                    h->cell_atoms, h->flags);
-        k_rows_cell<<<rows_grid, 256, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_start,
-                                               h->cell_atoms, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
-    } else {
-        k_rows_brute<<<rows_grid, 256, 0, st>>>(n, h->pos4, nullptr, nullptr, h->sys_box, P.rcut2, h->stride, h->nbr,
-                                                h->ncount, h->flags);
+    {
+        KScope ks(h, KG_NEIGH, st, 0);
+        if (!same_box) {
+            CK(h, cudaMemsetAsync(h->flags + FLAG_REBUILD, 1, sizeof(int), st));   // any non-zero value
+            h->cell_path = cell;
+            for (int a = 0; a < 3; ++a) h->nc[a] = nc[a];
+            const float4 sb = make_float4(bx.L[0], bx.L[1], bx.L[2], (float)nim);
+            CK(h, cudaMemcpyAsync(h->sys_box, &sb, sizeof(float4), cudaMemcpyHostToDevice, st));
+        } else {
+            CK(h, cudaMemsetAsync(h->flags + FLAG_REBUILD, 0, sizeof(int), st));
+            k_check_disp<<<blocks_for(n, T), T, 0, st>>>(n, pos, types, P.n_elem, h->off, h->ref, h->pos4,
+                                                         P.half_skin2, h->flags);
+            h->launches++;
+        }
+        k_rebuild_pos<<<blocks_for(n, T), T, 0, st>>>(n, pos, types, bx, P.n_elem, h->off, h->pos4, h->ref, h->flags,
+                                                      h->counters);
+        h->launches++;
+        if (h->cell_path) {
+            const int ncell = h->nc[0] * h->nc[1] * h->nc[2];
+            rc = ensure_cells(h, ncell);
+            if (rc) return rc;
+            CK(h, cudaMemsetAsync(h->cell_count, 0, sizeof(int) * (size_t)ncell, st));
+            k_cell_count<<<blocks_for(n, T), T, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_of,
+                                                         h->cell_count, h->flags);
+            k_cell_scan<<<1, 1024, 0, st>>>(ncell, h->cell_count, h->cell_start, h->cursor, h->flags);
+            k_cell_fill<<<blocks_for(n, T), T, 0, st>>>(n, h->cell_of, h->cursor, h->cell_atoms, h->flags);
+            k_cell_sort<<<std::min(blocks_for(ncell, 8), h->num_sms * 8), 256, 0, st>>>(ncell, h->cell_start,
+                                                                                        h->cell_atoms, h->flags);
+            k_rows_cell<<<rows_grid, 256, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_start,
+                                                   h->cell_atoms, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
+            h->launches += 5;
+        } else {
+            k_rows_brute<<<rows_grid, 256, 0, st>>>(n, h->pos4, nullptr, nullptr, h->sys_box, P.rcut2, h->stride,
+                                                    h->nbr, h->ncount, h->flags);
+            h->launches++;
+        }
+        k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
+        h->launches++;
     }
-    k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
     h->list_valid = true;
     h->list_n = n;
     for (int a = 0; a < 3; ++a) h->list_box[a] = box[a];
@@ -424,13 +510,18 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     SfKernel ksf;
     ForceKernel kf;
     pick_kernels(P, ksf, kf);
-    CK(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CNT_REBUILDS, st));
-    const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
-    ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->G, G_out, h->flags,
-                                                 h->counters);
+    {
+        KScope ks(h, KG_SF, st);
+        const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
+        ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->G, G_out, h->flags,
+                                                     h->counters);
+    }
     if (stop_after == 1 && !dEdG_out) return read_status(h, st);
-    const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
-    k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, h->pos4, h->d_plan, h->d_w, h->G, h->Ei, h->dEdG);
+    {
+        KScope ks(h, KG_MLP, st);
+        const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
+        k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, h->pos4, h->d_plan, h->d_w, h->G, h->Ei, h->dEdG);
+    }
     if (dEdG_out) CK(h, cudaMemcpy2DAsync(dEdG_out, sizeof(float) * P.width[0], h->dEdG, sizeof(float) * P.gs,
                                           sizeof(float) * P.width[0], n, cudaMemcpyDeviceToDevice, st));
     if (stop_after >= 1) return read_status(h, st);
@@ -439,13 +530,42 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     const int gred = std::min(blocks_for(n, T), 4 * h->num_sms);
     rc = ensure_red(h, gred, nvp);
     if (rc) return rc;
-    kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf,
-                                                     h->Fown, h->vpart, h->flags);
-    k_gather<<<rows_grid, 256, 0, st>>>(n, nv, h->rev, h->gbuf, h->Fown, F_out ? F_out : h->F, h->flags);
-    k_sum_partial<<<gred, T, 0, st>>>(n, h->Ei, h->epart, h->flags);
-    k_finalize<<<1, 256, 0, st>>>(gred, h->epart, energy ? energy : h->d_energy, nvp, h->vpart, vir_out);
+    {
+        KScope ks(h, KG_FORCE, st);
+        kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf,
+                                                         h->Fown, h->vpart, h->flags);
+    }
+    {
+        KScope ks(h, KG_GATHER, st);
+        k_gather<<<rows_grid, 256, 0, st>>>(n, nv, h->rev, h->gbuf, h->Fown, F_out ? F_out : h->F, h->flags);
+    }
+    {
+        KScope ks(h, KG_REDUCE, st, 2);
+        k_sum_partial<<<gred, T, 0, st>>>(n, h->Ei, h->epart, h->flags);
+        k_finalize<<<1, 256, 0, st>>>(gred, h->epart, energy ? energy : h->d_energy, nvp, h->vpart, vir_out);
+    }
     if (Ei_out) CK(h, cudaMemcpyAsync(Ei_out, h->Ei, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     return NNP_OK;
+}
+
+// Called at the start of every evaluating API call: clears work counters.
+static int begin_call(nnp_handle* h, cudaStream_t st)
+{
+    h->launches = 0;
+    CK(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CNT_REBUILDS, st));
+    return NNP_OK;
+}
+
+// all positions and types equal to the cached final state of the last nnp_step?
+__global__ void k_same(int n, const float* __restrict__ pos, const float* __restrict__ pc, const int* __restrict__ t,
+                       const int* __restrict__ tc, int* __restrict__ diff)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const bool d = (__float_as_int(pos[3 * i]) != __float_as_int(pc[3 * i])) ||
+                   (__float_as_int(pos[3 * i + 1]) != __float_as_int(pc[3 * i + 1])) ||
+                   (__float_as_int(pos[3 * i + 2]) != __float_as_int(pc[3 * i + 2])) || (t[i] != tc[i]);
+    if (d) *diff = 1;
 }
 
 // ---------------------------------------------------------------- public API
@@ -569,6 +689,13 @@ int nnp_destroy(nnp_handle* h)
                    h->epart, h->vpart, h->d_energy, h->d_log, h->flags, h->counters, h->sys_box};
     for (void* p : dev)
         if (p) cudaFree(p);
+    if (h->pos_cache) cudaFree(h->pos_cache);
+    if (h->types_cache) cudaFree(h->types_cache);
+    for (auto& p : h->pending) {
+        h->ev_pool.push_back(p.a);
+        h->ev_pool.push_back(p.b);
+    }
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->h_flags) cudaFreeHost(h->h_flags);
     delete h;
     return NNP_OK;
@@ -608,6 +735,9 @@ int nnp_compute(nnp_handle* h, int n, const float* pos, const int* types, const 
         CK(h, cudaStreamSynchronize(st));
         return NNP_OK;
     }
+    h->step_valid = false;
+    rc = begin_call(h, st);
+    if (rc) return rc;
     rc = run_eval(h, n, pos, types, box, st, energy, atom_energy, forces, virial, nullptr, nullptr, 0);
     if (rc) return rc;
     return read_status(h, st);
@@ -622,6 +752,9 @@ int nnp_descriptors(nnp_handle* h, int n, const float* pos, const int* types, co
     if (rc) return rc;
     if (n == 0) return NNP_OK;
     DeviceGuard g(h->device);
+    h->step_valid = false;
+    rc = begin_call(h, (cudaStream_t)stream);
+    if (rc) return rc;
     return run_eval(h, n, pos, types, box, (cudaStream_t)stream, nullptr, nullptr, nullptr, nullptr, G, dEdG,
                     dEdG ? 2 : 1);
 }
@@ -655,21 +788,91 @@ int nnp_step(nnp_handle* h, int n, float* pos, float* vel, const int* types, con
     rc = ensure_red(h, gke, 0);
     if (rc) return rc;
     const float dt = (float)dt_fs;
-    rc = run_eval(h, n, pos, types, box, st, log, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+    rc = begin_call(h, st);
     if (rc) return rc;
-    // run_eval sized epart for its own reduction; the kinetic-energy partials reuse it
+    // continue from the previous nnp_step if its final state is bitwise unchanged
+    bool cont = h->step_valid && h->step_n == n && h->step_pos == pos && h->step_types == types;
+    for (int a = 0; a < 3; ++a) cont = cont && (h->step_box[a] == box[a]);
+    if (cont) {
+        CK(h, cudaMemsetAsync(h->flags + 2, 0, sizeof(int), st));
+        k_same<<<blocks_for(n, T), T, 0, st>>>(n, pos, h->pos_cache, types, h->types_cache, h->flags + 2);
+        h->launches++;
+        CK(h, cudaMemcpyAsync(h->h_flags + 2, h->flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(h, cudaStreamSynchronize(st));
+        cont = (h->h_flags[2] == 0);
+    }
+    h->step_valid = false;
+    if (cont) {
+        CK(h, cudaMemcpyAsync(log, h->d_energy, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    } else {
+        rc = run_eval(h, n, pos, types, box, st, log, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+        if (rc) return rc;
+    }
+    // the kinetic-energy partials reuse the energy partial buffer (same block count)
     rc = ensure_red(h, gke, 0);
     if (rc) return rc;
-    k_kick_ke<<<gke, T, 0, st>>>(n, h->d_plan, types, h->F, vel, 0.f, h->epart);
-    k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, log, 1);
+    {
+        KScope ks(h, KG_INTEGRATE, st, 2);
+        k_kick_ke<<<gke, T, 0, st>>>(n, h->d_plan, types, h->F, vel, 0.f, h->epart);
+        k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, log, 1);
+    }
     for (int k = 1; k <= n_steps; ++k) {
-        k_kick_drift<<<blocks_for(n, T), T, 0, st>>>(n, h->d_plan, types, h->F, vel, pos, dt);
+        {
+            KScope ks(h, KG_INTEGRATE, st);
+            k_kick_drift<<<blocks_for(n, T), T, 0, st>>>(n, h->d_plan, types, h->F, vel, pos, dt);
+        }
         rc = run_eval(h, n, pos, types, box, st, log + 2 * k, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
         if (rc) return rc;
-        k_kick_ke<<<gke, T, 0, st>>>(n, h->d_plan, types, h->F, vel, dt, h->epart);
-        k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, log, 2 * k + 1);
+        {
+            KScope ks(h, KG_INTEGRATE, st, 2);
+            k_kick_ke<<<gke, T, 0, st>>>(n, h->d_plan, types, h->F, vel, dt, h->epart);
+            k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, log, 2 * k + 1);
+        }
     }
-    return read_status(h, st);
+    // remember the final state for a continuing call
+    CK(h, cudaMemcpyAsync(h->pos_cache, pos, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    CK(h, cudaMemcpyAsync(h->types_cache, types, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+    CK(h, cudaMemcpyAsync(h->d_energy, log + 2 * (size_t)n_steps, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    rc = read_status(h, st);
+    if (rc) return rc;
+    h->step_valid = true;
+    h->step_n = n;
+    h->step_pos = pos;
+    h->step_types = types;
+    for (int a = 0; a < 3; ++a) h->step_box[a] = box[a];
+    return NNP_OK;
+}
+
+int nnp_profile(nnp_handle* h, int enable)
+{
+    if (!h) return NNP_EINVAL;
+    DeviceGuard g(h->device);
+    CK(h, cudaDeviceSynchronize());
+    prof_flush(h);
+    for (int k = 0; k < KG_N; ++k) {
+        h->prof_ms[k] = 0.0;
+        h->prof_n[k] = 0;
+    }
+    h->prof_on = enable != 0;
+    return NNP_OK;
+}
+
+int nnp_num_kernel_groups(void) { return KG_N; }
+
+const char* nnp_kernel_group_name(int k) { return (k >= 0 && k < KG_N) ? kKgName[k] : ""; }
+
+int nnp_kernel_times(nnp_handle* h, int max_groups, double* total_ms, long long* launches)
+{
+    if (!h || max_groups < 0 || (max_groups > 0 && (!total_ms || !launches))) return NNP_EINVAL;
+    DeviceGuard g(h->device);
+    CK(h, cudaDeviceSynchronize());
+    prof_flush(h);
+    const int m = std::min(max_groups, (int)KG_N);
+    for (int k = 0; k < m; ++k) {
+        total_ms[k] = h->prof_ms[k];
+        launches[k] = h->prof_n[k];
+    }
+    return m;
 }
 
 int nnp_get_stats(nnp_handle* h, nnp_stats* out)
@@ -685,6 +888,7 @@ int nnp_get_stats(nnp_handle* h, nnp_stats* out)
     out->pairs = (long long)c[CNT_PAIRS];
     out->triplets = (long long)c[CNT_TRIPLETS];
     out->rebuilds = (long long)c[CNT_REBUILDS];
+    out->kernel_launches = h->launches;
     return NNP_OK;
 }
 

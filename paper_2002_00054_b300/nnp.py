@@ -157,6 +157,20 @@ class NNP:
         _need(w, torch.float32, (self.num_params,), "weights", self.device)
         self._check(self._lib.nnp_set_weights(self.h, _ptr(w), _stream(stream)))
 
+    def profile(self, enable=True):
+        """Start (clearing totals) or stop per-kernel-group device timing."""
+        self._check(self._lib.nnp_profile(self.h, 1 if enable else 0))
+
+    def kernel_times(self):
+        """{group name: (total ms, launches)} since profile(True)."""
+        k = self._lib.nnp_num_kernel_groups()
+        ms = (ctypes.c_double * k)()
+        n = (ctypes.c_longlong * k)()
+        m = self._lib.nnp_kernel_times(self.h, k, ms, n)
+        if m < 0:
+            self._check(m)
+        return {self._lib.nnp_kernel_group_name(i).decode(): (ms[i], n[i]) for i in range(m)}
+
     def stats(self):
         s = _capi.Stats()
         self._check(self._lib.nnp_get_stats(self.h, ctypes.byref(s)))

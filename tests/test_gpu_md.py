@@ -40,3 +40,45 @@ def test_nve_drift_small():
     etot = log.sum(1)
     assert np.abs(etot - etot[0]).max() / len(pos) < 2e-4
     assert nnp.stats()["rebuilds"] >= 1
+
+
+def test_step_continuation_is_bitwise_identical():
+    """step(4) then step(6) on the same buffers equals step(10): the second call
+    reuses the first call's final forces instead of recomputing them."""
+    from paper_2002_00054_b300 import NNP
+    m = workloads.water_model()
+    pos, types, box = workloads.water_random()
+    vel = workloads.maxwell_boltzmann(types, m["masses"])
+    nnp = NNP(m)
+    p1, t = to_dev(f32(pos), types)
+    v1 = torch.tensor(vel, dtype=torch.float32, device="cuda")
+    p2, v2 = p1.clone(), v1.clone()
+    la = nnp.step(p1, v1, t, f32(box), 0.5, 4)
+    n_first = nnp.stats()["kernel_launches"]
+    lb = nnp.step(p1, v1, t, f32(box), 0.5, 6)
+    assert nnp.stats()["kernel_launches"] < n_first * 6 / 4 + 2   # no extra force evaluation
+    ref = NNP(m)
+    lc = ref.step(p2, v2, t, f32(box), 0.5, 10)
+    assert torch.equal(p1, p2) and torch.equal(v1, v2)
+    assert torch.equal(torch.cat([la, lb[1:]]), lc)
+    # a modified position forces a fresh evaluation and still gives the right answer
+    p1[0, 0] += 0.01
+    nnp.step(p1, v1, t, f32(box), 0.5, 1)
+    p2[0, 0] += 0.01
+    ref2 = NNP(m)
+    ref2.step(p2, v2, t, f32(box), 0.5, 1)
+    assert torch.equal(p1, p2)
+
+
+def test_kernel_group_timing():
+    from paper_2002_00054_b300 import NNP
+    m = workloads.water_model()
+    pos, types, box = workloads.water_lattice((2, 2, 2))
+    nnp = NNP(m)
+    p, t = to_dev(f32(pos), types)
+    v = torch.zeros_like(p)
+    nnp.profile(True)
+    nnp.step(p, v, t, f32(box), 0.5, 3)
+    kt = nnp.kernel_times()
+    assert kt["force"][1] == 4 and kt["descriptors"][1] == 4 and kt["force"][0] > 0
+    assert kt["integrate"][1] == 1 + 3 * 2
