@@ -1,4 +1,4 @@
-// k_neighbors.cuh -- neighbour-list maintenance.
+// k_neighbors.cuh -- neighbour-list maintenance: cell binning and a full Verlet list.
 //
 // The paper keeps a Cabana neighbour list (Sec. 3.2) and notes that random
 // neighbour access dominates (Sec. 4.3).  Here: a full (both directions) Verlet

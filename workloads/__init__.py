@@ -23,7 +23,7 @@ WATER_DENSITY_ATOMS = 3 * 0.0334277  # atoms per A^3 at 1.0 g/cm^3 (0.03343 mole
 WATER_CELL = 12.42                # A, 64 molecules at liquid density
 MASS = {"O": 15.999, "H": 1.008, "M": 58.6934}
 
-# Seeds of every preset (fixed; recorded in the design doc).
+# Seeds of every preset (fixed).
 SEED_WATER_MODEL = 1001
 SEED_TEACHER_MODEL = 2002
 SEED_FCC_MODEL = 3003
