@@ -184,6 +184,42 @@ NNP_API int nnp_num_kernel_groups(void);
 NNP_API const char* nnp_kernel_group_name(int k);
 NNP_API int nnp_kernel_times(nnp_handle* h, int max_groups, double* total_ms, long long* launches);
 
+/* ------------------------------------------------ allocation-free evaluation */
+/* The paper has no counterpart to this entry point.
+ *
+ * nnp_compute_static computes what nnp_compute computes (energy, per-atom
+ * energies, forces) for one small system without allocating any memory, on
+ * the device or the host.  It is meant for callers that cannot allocate at the
+ * time they need forces: a host MD code or framework that reserves all device
+ * memory at start-up and forbids allocation inside its time loop, or a
+ * latency-bound loop that cannot afford the device-wide synchronisation that
+ * cudaMalloc / cudaFree may imply.  Such a caller creates the handle once at
+ * start-up (nnp_create allocates the model parameters) and then calls this
+ * entry point every step.
+ *
+ * Scratch: one file-scope device array of NNP_STATIC_SCRATCH_BYTES (8 MiB) per
+ * GPU that loads this library, held until the process exits.  The handle's own
+ * scratch is neither used nor changed.  Limits: n_atoms <= NNP_STATIC_MAX_ATOMS
+ * and the scratch the call needs (about n_atoms * max_neighbors * 24 bytes)
+ * must fit the array; otherwise NNP_EINVAL with a message naming the limit.
+ * Neighbours are found by brute force over periodic images on every call.
+ *
+ * The first call on a device looks up the array's device address (a runtime
+ * call, made once per device with that device current); make that first call
+ * before any stream capture.  Every call shares the one array and leaves its
+ * contents behind: calls whose work overlaps on the GPU (different streams or
+ * host threads without ordering) race on it; serialise them.
+ *
+ * Arguments as nnp_compute (energy, atom_energy, forces device pointers, each
+ * nullable; box host double [3]); errbuf (nullable) receives a message of at
+ * most errbuf_len bytes on failure, since nnp_last_error is not updated.
+ * Synchronises 'stream' at the end to read the status. */
+#define NNP_STATIC_MAX_ATOMS 1024
+#define NNP_STATIC_SCRATCH_BYTES (8u << 20)
+NNP_API int nnp_compute_static(const nnp_handle* h, int n_atoms, const float* pos, const int* types,
+                               const double* box, double* energy, float* atom_energy, float* forces,
+                               char* errbuf, int errbuf_len, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -58,6 +58,7 @@ SIGNATURES = {
     "nnp_num_kernel_groups": (I, []),
     "nnp_kernel_group_name": (ctypes.c_char_p, [I]),
     "nnp_kernel_times": (I, [V, I, c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
+    "nnp_compute_static": (I, [V, I, V, V, c_double_p, V, V, V, ctypes.c_char_p, I, V]),
 }
 
 _lib = None

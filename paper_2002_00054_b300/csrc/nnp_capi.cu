@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -893,3 +894,179 @@ int nnp_get_stats(nnp_handle* h, nnp_stats* out)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------- allocation-free evaluation
+// nnp_compute_static: the evaluation of run_eval for one small system, with all
+// per-call scratch carved from a file-scope device array instead of allocated.
+static __device__ __align__(256) unsigned char g_static_pool[NNP_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+const int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices];   // device address of g_static_pool, looked up once per device
+bool g_static_ready[kMaxDevices];
+
+// Host-side carving of the pool (pointer arithmetic only); base == nullptr sizes it.
+struct Carve {
+    unsigned char* base;
+    size_t off = 0;
+    template <typename T>
+    T* take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T* p = reinterpret_cast<T*>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+int static_fail(char* eb, int el, int code, const char* fmt, ...) __attribute__((format(printf, 4, 5)));
+int static_fail(char* eb, int el, int code, const char* fmt, ...)
+{
+    if (eb && el > 0) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(eb, (size_t)el, fmt, ap);
+        va_end(ap);
+    }
+    return code;
+}
+
+}  // namespace
+
+extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, const int* types, const double* box,
+                                  double* energy, float* atom_energy, float* forces, char* eb, int el, void* stream)
+{
+    if (eb && el > 0) eb[0] = '\0';
+    if (!h) return static_fail(eb, el, NNP_EINVAL, "handle is NULL");
+    if (n < 0 || n > NNP_STATIC_MAX_ATOMS)
+        return static_fail(eb, el, NNP_EINVAL, "n_atoms = %d is outside 0..%d, the limit of nnp_compute_static",
+                           n, NNP_STATIC_MAX_ATOMS);
+    if (n > 0 && (!pos || !types)) return static_fail(eb, el, NNP_EINVAL, "pos and types must not be NULL");
+    if (!box) return static_fail(eb, el, NNP_EINVAL, "box is NULL");
+    const double rcut = h->cutoff + h->skin;
+    int nim = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (!(box[a] > 0.0) || !std::isfinite(box[a]))
+            return static_fail(eb, el, NNP_EBOX, "box edges must be finite and > 0");
+        if (box[a] < 0.5 * rcut)
+            return static_fail(eb, el, NNP_EBOX, "box edge %g is below (cutoff + skin) / 2 = %g", box[a], 0.5 * rcut);
+        nim = std::max(nim, (int)std::ceil(rcut / box[a]));
+    }
+    if (h->device < 0 || h->device >= kMaxDevices) return static_fail(eb, el, NNP_ECUDA, "device index out of range");
+    const Plan& P = h->plan;
+    const int S = h->stride, T = 256;
+    const int gf = std::min(blocks_for(std::max(n, 1), h->wpb_force), h->grid_force);
+    const int nvp = gf * h->wpb_force;
+    const int gred = std::min(blocks_for(std::max(n, 1), T), 4 * h->num_sms);
+
+    // scratch layout (the same carving sizes and places it)
+    auto layout = [&](Carve& c, int** flags, unsigned long long** counters, float4** sys_box, float4** off, float4** ref,
+                      float4** pos4, uint32_t** nbr, int** ncount, int** rev, float** G, float** dEdG, float** Ei,
+                      float4** gbuf, float4** Fown, double** vpart, double** epart, float** F) {
+        *flags = c.take<int>(4);
+        *counters = c.take<unsigned long long>(CNT_N);
+        *sys_box = c.take<float4>(1);
+        *off = c.take<float4>(n);
+        *ref = c.take<float4>(n);
+        *pos4 = c.take<float4>(n);
+        *nbr = c.take<uint32_t>((size_t)n * S);
+        *ncount = c.take<int>(n);
+        *rev = c.take<int>((size_t)n * S);
+        *G = c.take<float>((size_t)n * P.gs);
+        *dEdG = c.take<float>((size_t)n * P.gs);
+        *Ei = c.take<float>(n);
+        *gbuf = c.take<float4>((size_t)n * S);
+        *Fown = c.take<float4>(n);
+        *vpart = c.take<double>((size_t)nvp * 9);
+        *epart = c.take<double>(gred);
+        *F = c.take<float>((size_t)n * 3);
+    };
+    int* flags;
+    unsigned long long* counters;
+    float4 *sys_box, *off, *ref, *pos4, *gbuf, *Fown;
+    uint32_t* nbr;
+    int *ncount, *rev;
+    float *G, *dEdG, *Ei, *Fs;
+    double *vpart, *epart;
+    {
+        Carve dry{nullptr};
+        layout(dry, &flags, &counters, &sys_box, &off, &ref, &pos4, &nbr, &ncount, &rev, &G, &dEdG, &Ei, &gbuf, &Fown,
+               &vpart, &epart, &Fs);
+        if (dry.off > NNP_STATIC_SCRATCH_BYTES)
+            return static_fail(eb, el, NNP_EINVAL,
+                               "needs %zu bytes of scratch for n_atoms = %d and max_neighbors = %d; the static "
+                               "scratch array holds %u bytes",
+                               dry.off, n, S, (unsigned)NNP_STATIC_SCRATCH_BYTES);
+    }
+
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ready[h->device]) {
+            // In host code g_static_pool names a host-side stand-in; the kernels need
+            // the device address, looked up here once with the device current.
+            cudaError_t e = cudaGetSymbolAddress(&g_static_addr[h->device], g_static_pool);
+            if (e != cudaSuccess)
+                return static_fail(eb, el, NNP_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            g_static_ready[h->device] = true;
+        }
+        base = g_static_addr[h->device];
+    }
+    Carve c{static_cast<unsigned char*>(base)};
+    layout(c, &flags, &counters, &sys_box, &off, &ref, &pos4, &nbr, &ncount, &rev, &G, &dEdG, &Ei, &gbuf, &Fown, &vpart,
+           &epart, &Fs);
+
+#define CKS(call)                                                                                      \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return static_fail(eb, el, NNP_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+    if (n == 0) {
+        if (energy) CKS(cudaMemsetAsync(energy, 0, sizeof(double), st));
+        CKS(cudaStreamSynchronize(st));
+        return NNP_OK;
+    }
+    // what must start at zero: the error word, the work counters; the rebuild flag is set
+    CKS(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+    CKS(cudaMemsetAsync(flags + FLAG_REBUILD, 1, sizeof(int), st));
+    CKS(cudaMemsetAsync(counters, 0, CNT_N * sizeof(unsigned long long), st));
+    Box bx;
+    for (int a = 0; a < 3; ++a) bx.L[a] = (float)box[a];
+    const float4 sb = make_float4(bx.L[0], bx.L[1], bx.L[2], (float)nim);
+    CKS(cudaMemcpyAsync(sys_box, &sb, sizeof(float4), cudaMemcpyHostToDevice, st));
+
+    const int rows_grid = std::min(blocks_for(n, 8), h->num_sms * 8);
+    k_rebuild_pos<<<blocks_for(n, T), T, 0, st>>>(n, pos, types, bx, P.n_elem, off, pos4, ref, flags, counters);
+    k_rows_brute<<<rows_grid, 256, 0, st>>>(n, pos4, nullptr, nullptr, sys_box, P.rcut2, S, nbr, ncount, flags);
+    k_rev<<<rows_grid, 256, 0, st>>>(n, nbr, ncount, S, rev, flags);
+    NbView nv{nbr, ncount, S};
+    SfKernel ksf;
+    ForceKernel kf;
+    pick_kernels(P, ksf, kf);
+    const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
+    ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, G, nullptr, flags, counters);
+    const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
+    k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
+    kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, vpart,
+                                                     flags);
+    k_gather<<<rows_grid, 256, 0, st>>>(n, nv, rev, gbuf, Fown, forces ? forces : Fs, flags);
+    k_sum_partial<<<gred, T, 0, st>>>(n, Ei, epart, flags);
+    k_finalize<<<1, 256, 0, st>>>(gred, epart, energy, nvp, vpart, nullptr);
+    if (atom_energy) CKS(cudaMemcpyAsync(atom_energy, Ei, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
+    CKS(cudaGetLastError());
+    int hf = 0;
+    CKS(cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CKS(cudaStreamSynchronize(st));
+#undef CKS
+    if (hf & (ERR_NEIGH_OVERFLOW | ERR_RC_OVERFLOW))
+        return static_fail(eb, el, NNP_ENEIGH_OVERFLOW, "an atom has more than max_neighbors = %d neighbours", S);
+    if (hf & ERR_CLOSE) return static_fail(eb, el, NNP_ENONFINITE, "two atoms are closer than 1e-4 A");
+    if (hf & ERR_NONFINITE)
+        return static_fail(eb, el, NNP_ENONFINITE, "non-finite position/energy/force or invalid element type");
+    if (hf) return static_fail(eb, el, NNP_ECUDA, "device error word 0x%x", hf);
+    return NNP_OK;
+}
