@@ -96,7 +96,9 @@ typedef struct {
                                  /* bias b_l [widths[l+1]]; elements back to back     */
     int mlp_precision;           /* nnp_precision                                     */
     int max_neighbors;           /* capacity of one atom's neighbour-list row (entries */
-                                 /* within cutoff + skin), 32..1024                   */
+                                 /* within cutoff + skin), 32..1024; entries within   */
+                                 /* the cutoff alone are limited to max_neighbors *   */
+                                 /* (cutoff / (cutoff + skin))^3 (at least 32)         */
 } nnp_params;
 
 typedef struct nnp_handle nnp_handle;

@@ -117,6 +117,42 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// Knuth's TwoSum: s + e == a + b exactly
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Reduce-scatter of 32 per-lane float accumulators over the warp with compensated
+// (hi + lo) additions: lane t returns the total of v[t] over all lanes, in double.
+// 31 exchange steps in all (16 + 8 + 4 + 2 + 1) instead of 32 butterflies.
+__device__ __forceinline__ double warp_reduce_scatter32(const float (&v)[32], int lane)
+{
+    float hi[32], lo[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        hi[t] = v[t];
+        lo[t] = 0.f;
+    }
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+        const bool upper = (lane & half) != 0;
+#pragma unroll
+        for (int t = 0; t < half; ++t) {
+            const float send_h = upper ? hi[t] : hi[t + half], send_l = upper ? lo[t] : lo[t + half];
+            const float keep_h = upper ? hi[t + half] : hi[t], keep_l = upper ? lo[t + half] : lo[t];
+            const float rh = __shfl_xor_sync(FULL, send_h, half), rl = __shfl_xor_sync(FULL, send_l, half);
+            float s, e;
+            two_sum(keep_h, rh, s, e);
+            hi[t] = s;
+            lo[t] = keep_l + rl + e;
+        }
+    }
+    return (double)hi[0] + (double)lo[0];
+}
+
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll

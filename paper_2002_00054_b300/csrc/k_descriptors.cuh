@@ -1,13 +1,23 @@
 // k_descriptors.cuh -- symmetry functions (Fig. 1b step 1 and the angular loop of
 // Sec. 3.1) and the chain-rule force pass (Fig. 1b step 3).
 //
-// Mapping: one warp per centre atom i (the paper's "flat" atom parallelism, but
-// with the neighbour and pair loops spread over the 32 lanes of the warp instead
-// of one thread).  The warp stages its atom's neighbours inside the cutoff into
-// shared memory (compacted with a ballot), with per-neighbour radius and the
-// angular pair factors P_q(r) = exp(-eta_q r^2) f_c(r) precomputed once, then
-// walks all pairs j < k of that list in a flattened order (pair p = lane, lane+32,
-// ...), so lanes stay busy however short the rows get.
+// Mapping: one warp per centre atom i (the paper's "flat" atom parallelism,
+// Sec. 4.3, with the neighbour and pair loops spread over the 32 lanes).
+//
+// Staging.  The warp keeps its atom's neighbours inside the cutoff in shared
+// memory, sorted by distance: per neighbour the displacement d, r, 1/r and the
+// angular pair factors P_q(r) = exp(-eta_q r^2) f_c(r) (force pass also
+// dP_q/dr), computed once per atom.  Sorting groups neighbours of similar r,
+// which have similar numbers of contributing partners.
+//
+// Pairs j < k are walked as 32 x 32 blocks of the sorted list: in block (A, B)
+// lane l takes j = 32A + l and partners k = 32B + (l + s) mod 32.  For the
+// narrow functions each lane first builds a bitmask of the partners with
+// r_jk < r_c (about half of them).  The descriptor pass keeps j in registers
+// and visits its live partners; the force pass, whose per-pair work is three
+// times larger, packs the live pairs of a block into a warp queue (s-major, so
+// j and k stay distinct within a batch) and processes them 32 at a time with
+// every lane busy.
 //
 // Angular accumulators are dense in (eta_q, lambda, k) with zeta = 2^k: the
 // powers (1 +- cos)^(2^k) come from repeated squaring, and the model's
@@ -16,8 +26,8 @@
 // The force pass recomputes every descriptor derivative instead of storing
 // dG/dr (the paper's recompute-not-store rule, Sec. 3.3 and Sec. 5): for each
 // pair it contracts the derivative with dE_i/dG_i on the fly and accumulates
-// g_ij = dE_i/dd_ij per neighbour entry in shared memory.  g is written per
-// neighbour-list slot; forces are then gathered per atom (k_gather).
+// g_ij = dE_i/dd_ij per neighbour.  g is written per neighbour-list slot;
+// forces are then gathered per atom without atomics (k_gather).
 #pragma once
 #include "common.cuh"
 
@@ -27,111 +37,187 @@ struct NbView {
     int stride;
 };
 
-// Stages the neighbours of atom i within the cutoff.  Returns M (count kept).
-// nd[m] = (dx, dy, dz, r); npf[m] = P_q (q < 4); nfe[m] = (f_c, element, f_c', unused)
-// FORCE: ndp[m] = dP_q/dr, cmap[slot] = compact index or -1, sg[3m..] = radial part of g.
+// Per-warp shared-memory arrays (C = capacity inside the cutoff, S = list stride).
+struct WarpSmem {
+    float4* nd;     // (dx, dy, dz, r), distance-sorted
+    float* ninv;    // 1 / r
+    float4* npf;    // P_q
+    float4* ndp;    // dP_q / dr (force)
+    float2* nfe;    // (f_c, element) (descriptor pass)
+    float* sg;      // g accumulators, 3 per neighbour (force)
+    unsigned short* queue;   // live pairs of the current block (force)
+    short* srt;     // list slot of each sorted neighbour
+    short* cmap;    // sorted index of each list slot, -1 outside the cutoff (force)
+};
+
+__host__ __device__ inline size_t sf_warp_bytes(int C) { return (size_t)C * (16 + 16 + 4 + 8 + 2) + NNP_MAXG * 8; }
+#define PAIR_QUEUE 1024   // live pairs of one 32 x 32 block, as (l | s << 5)
+__host__ __device__ inline size_t force_warp_bytes(int C, int S)
+{
+    return (size_t)C * (16 + 16 + 16 + 12 + 2) + (size_t)S * 2 + PAIR_QUEUE * 2 + NNP_MAXG * 4;
+}
+
+// Stages the neighbours of atom i within the cutoff (see file comment).  Returns M.
+// nd[m].w holds r (descriptor pass, 1/r in ninv) or 1/r (force pass).
+// FORCE: also dP/dr, the radial part of g (into sg) and the slot map.
 template <int NETA, bool FORCE>
 __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box& bx, const NbView& nv,
-                                               const float4* __restrict__ pos4, const Plan& P,
-                                               const ElemPlan& E, const float* __restrict__ khi,
-                                               const float* __restrict__ klo, const float* __restrict__ etav, int cap, float4* nd, float4* npf,
-                                               float4* ndp, float2* nfe, int* cmap, float* sg,
-                                               const float* sW, int lane, int* flags, int& n_list)
+                                               const float4* __restrict__ pos4, const Plan& P, const ElemPlan& E,
+                                               const float* khi, const float* klo, const float* etav, int C,
+                                               const WarpSmem& w, const float* sW, int lane, int* flags, int& n_list)
 {
     const int cnt = nv.ncount[i];
     n_list = cnt;
     const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
+    // the key and compact-slot temporaries live in the npf area, written only in pass 3
+    float* skey = reinterpret_cast<float*>(w.npf);
+    int* cslot = reinterpret_cast<int*>(w.npf) + C;
+    // pass 1: compact the slots inside the cutoff (key r^2)
     int M = 0;
     for (int base = 0; base < cnt; base += 32) {
         const int s = base + lane;
         bool keep = false;
-        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        int ej = 0;
+        float r2 = 0.f;
         if (s < cnt) {
             const uint32_t e = row[s];
             const float4 pj = pos4[e & NB_INDEX_MASK];
             float ox, oy, oz;
             nb_shift(e, bx.L[0], bx.L[1], bx.L[2], ox, oy, oz);
-            dx = pair_disp(pj.x, pi.x, ox);
-            dy = pair_disp(pj.y, pi.y, oy);
-            dz = pair_disp(pj.z, pi.z, oz);
+            const float dx = pair_disp(pj.x, pi.x, ox), dy = pair_disp(pj.y, pi.y, oy), dz = pair_disp(pj.z, pi.z, oz);
             r2 = dx * dx + dy * dy + dz * dz;
-            ej = __float_as_int(pj.w);
             keep = r2 < P.rc2;
+            if (FORCE) w.cmap[s] = -1;
         }
         const unsigned m = __ballot_sync(FULL, keep);
         const int at = M + __popc(m & ((1u << lane) - 1u));
-        if (FORCE && s < cnt) cmap[s] = (keep && at < cap) ? at : -1;
-        if (keep && at < cap) {
-            if (r2 < 1e-8f) atomicOr(&flags[FLAG_ERR], ERR_CLOSE);
-            const float r = sqrtf(r2);
-            float fc, dfc;
-            cutoff_fn(r, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, fc, dfc);
-            nd[at] = make_float4(dx, dy, dz, r);
-            float pq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int q = 0; q < NETA; ++q) {
-                const float ex = gauss2(khi[q], klo[q], r2);
-                pq[q] = ex * fc;
-                dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
-            }
-            npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
-            nfe[at] = make_float2(fc, __int_as_float(ej));
-            if (FORCE) {
-                ndp[at] = make_float4(dq[0], dq[1], dq[2], dq[3]);
-                // radial part of g_ij: sum over radial descriptors of dE/dG * dG/dr * d/r
-                float gr = 0.f;
-                for (int rr = 0; rr < E.n_rad; ++rr) {
-                    const int el = E.rad_elem[rr];
-                    if (el < 0 || el == ej) {
-                        const float x = r - E.rad_rs[rr];
-                        const float ex = gauss2(E.rad_khi[rr], E.rad_klo[rr], x * x);
-                        gr += sW[E.rad_out[rr]] * ex * (dfc - 2.0f * E.rad_eta[rr] * x * fc);
-                    }
-                }
-                const float gs = gr / r;
-                sg[3 * at + 0] = gs * dx;
-                sg[3 * at + 1] = gs * dy;
-                sg[3 * at + 2] = gs * dz;
-            }
+        if (keep && at < C) {
+            skey[at] = r2;
+            cslot[at] = s;
         }
         M += __popc(m);
     }
-    if (M > cap) {
+    if (M > C) {
         if (lane == 0) atomicOr(&flags[FLAG_ERR], ERR_RC_OVERFLOW);
-        M = cap;
+        M = C;
+    }
+    __syncwarp();
+    // pass 2: rank by r^2 (ties by compact index) -> srt[rank] = slot
+    for (int m = lane; m < M; m += 32) {
+        const float key = skey[m];
+        int rank = 0;
+        for (int t = 0; t < M; ++t) {
+            const float kt = skey[t];
+            rank += (kt < key) || (kt == key && t < m);
+        }
+        w.srt[rank] = (short)cslot[m];
+    }
+    __syncwarp();
+    // pass 3: per sorted neighbour, recompute d from the list entry and fill the arrays
+    for (int m = lane; m < M; m += 32) {
+        const int s = w.srt[m];
+        const uint32_t e = row[s];
+        const float4 pj = pos4[e & NB_INDEX_MASK];
+        float ox, oy, oz;
+        nb_shift(e, bx.L[0], bx.L[1], bx.L[2], ox, oy, oz);
+        const float dx = pair_disp(pj.x, pi.x, ox), dy = pair_disp(pj.y, pi.y, oy), dz = pair_disp(pj.z, pi.z, oz);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        if (r2 < 1e-8f) atomicOr(&flags[FLAG_ERR], ERR_CLOSE);
+        const float r = sqrtf(r2);
+        const float ir = 1.0f / r;
+        float fc, dfc;
+        cutoff_fn(r, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, fc, dfc);
+        if (FORCE) {
+            w.nd[m] = make_float4(dx, dy, dz, ir);
+        } else {
+            w.nd[m] = make_float4(dx, dy, dz, r);
+            w.ninv[m] = ir;
+        }
+        float pq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < NETA; ++q) {
+            const float ex = gauss2(khi[q], klo[q], r2);
+            pq[q] = ex * fc;
+            dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
+        }
+        const int ej = __float_as_int(pj.w);
+        if (!FORCE) {
+            w.nfe[m] = make_float2(fc, __int_as_float(ej));
+        } else {
+            w.ndp[m] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+            w.cmap[s] = (short)m;
+            // radial part of g_ij: sum over radial descriptors of dE/dG * dG/dr * d / r
+            float gr = 0.f;
+            for (int rr = 0; rr < E.n_rad; ++rr) {
+                const int el = E.rad_elem[rr];
+                if (el < 0 || el == ej) {
+                    const float x = r - E.rad_rs[rr];
+                    const float ex = gauss2(E.rad_khi[rr], E.rad_klo[rr], x * x);
+                    gr += sW[E.rad_out[rr]] * ex * (dfc - 2.0f * E.rad_eta[rr] * x * fc);
+                }
+            }
+            const float gs = gr * ir;
+            w.sg[3 * m + 0] = gs * dx;
+            w.sg[3 * m + 1] = gs * dy;
+            w.sg[3 * m + 2] = gs * dz;
+        }
+        // npf overlays the pass-1 temporaries, which pass 3 no longer reads
+        w.npf[m] = make_float4(pq[0], pq[1], pq[2], pq[3]);
     }
     __syncwarp();
     return M;
 }
 
-// advance a lane's flattened pair (j, k), j < k < M, by 'step' pairs
-__device__ __forceinline__ void pair_normalize(int& j, int& k, int M)
+// Partner step s of lane l in block pair (A, B): valid when both exist and, on the
+// diagonal block, each unordered pair is taken once (s in 1..15, or 16 for l < 16).
+__device__ __forceinline__ bool pair_valid(int A, int B, int l, int s, int M)
 {
-    while (j < M - 1 && k >= M) {
-        k = k - M + j + 2;
-        ++j;
+    const int j = 32 * A + l, k = 32 * B + ((l + s) & 31);
+    if (j >= M || k >= M) return false;
+    if (A < B) return true;
+    return (s >= 1 && s <= 15) || (s == 16 && l < 16);
+}
+
+// Bitmask over s = 0..31 of the contributing partners of lane l's j in block (A, B).
+template <bool NARROW>
+__device__ __forceinline__ unsigned live_mask(int A, int B, int l, int M, const float4 a, const float4* nd, float rc2)
+{
+    unsigned mask = 0u;
+#pragma unroll 4
+    for (int s = 0; s < 32; ++s) {
+        if (!pair_valid(A, B, l, s, M)) continue;
+        if (NARROW) {
+            const float4 b = nd[32 * B + ((l + s) & 31)];
+            const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+            if (ex * ex + ey * ey + ez * ez < rc2) mask |= 1u << s;
+        } else {
+            mask |= 1u << s;
+        }
     }
+    return mask;
 }
 
 // ---------------------------------------------------------------- value pass
 template <int NETA, bool NARROW>
 __global__ void __launch_bounds__(256)
 k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g,
-     int cap, float* __restrict__ Gs, float* __restrict__ Graw, int* __restrict__ flags,
+     int C, float* __restrict__ Gs, float* __restrict__ Graw, int* __restrict__ flags,
      unsigned long long* __restrict__ counters)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    // per-warp shared memory
-    const size_t per = (size_t)cap * (16 + 16 + 8) + NNP_MAXG * 8;
-    unsigned char* base = smem + per * wib;
-    float4* nd = (float4*)base;
-    float4* npf = nd + cap;
-    float2* nfe = (float2*)(npf + cap);
-    double* sG = (double*)(nfe + cap);   // cap is a multiple of 2: 8-byte aligned
+    unsigned char* base = smem + sf_warp_bytes(C) * wib;
+    WarpSmem w;
+    w.nd = reinterpret_cast<float4*>(base);
+    w.npf = w.nd + C;
+    double* sG = reinterpret_cast<double*>(w.npf + C);
+    w.ninv = reinterpret_cast<float*>(sG + NNP_MAXG);
+    w.nfe = reinterpret_cast<float2*>(w.ninv + C);
+    w.srt = reinterpret_cast<short*>(w.nfe + C);
+    w.ndp = nullptr;
+    w.sg = nullptr;
+    w.cmap = nullptr;
 
     unsigned long long c_list = 0, c_rc = 0, c_pairs = 0, c_trip = 0;
     const int nw = gridDim.x * wpb;
@@ -147,55 +233,75 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             klo[q] = (q < E.n_eta) ? E.ang_klo[q] : 0.f;
         }
         int n_list;
-        const int M = stage_neighbors<NETA, false>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, cap, nd, npf,
-                                                   nullptr, nfe, nullptr, nullptr, nullptr, lane, flags, n_list);
-        // radial: lane <-> descriptor, loop over neighbours (broadcast reads)
-        for (int rr = lane; rr < E.n_rad; rr += 32) {
-            const float kh = E.rad_khi[rr], kl = E.rad_klo[rr], rs = E.rad_rs[rr];
-            const int el = E.rad_elem[rr];
-            double acc = 0.0;   // radial sums feed G~ = (G - mu)/s with |mu/s| up to ~1e2
-            for (int m = 0; m < M; ++m) {
-                const float r = nd[m].w;
-                const float2 fe = nfe[m];
-                if (el < 0 || el == __float_as_int(fe.y)) {
-                    const float x = r - rs;
-                    acc += (double)(gauss2(kh, kl, x * x) * fe.x);
+        const int M = stage_neighbors<NETA, false>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, nullptr, lane,
+                                                   flags, n_list);
+        // radial: lane <-> descriptor (two neighbour halves when n_rad <= 16), loop over
+        // neighbours with broadcast reads; Kahan-compensated sums (they feed
+        // G~ = (G - mu)/s with |mu/s| up to ~20)
+        {
+            const int halves = (E.n_rad <= 16) ? 2 : 1;
+            const int per = 32 / halves;
+            const int hf = lane / per, slot = lane % per;
+            for (int rb = 0; rb < E.n_rad; rb += per) {
+                const int rr = rb + slot;
+                const bool act = rr < E.n_rad;
+                const float kh = act ? E.rad_khi[rr] : 0.f, kl = act ? E.rad_klo[rr] : 0.f;
+                const float rs = act ? E.rad_rs[rr] : 0.f;
+                const int el = act ? E.rad_elem[rr] : -2;
+                float sum = 0.f, comp = 0.f;
+                for (int m = hf; m < M; m += halves) {
+                    const float r = w.nd[m].w;
+                    const float2 fe = w.nfe[m];
+                    if (el == -1 || el == __float_as_int(fe.y)) {
+                        const float x = r - rs;
+                        const float y = gauss2(kh, kl, x * x) * fe.x - comp;
+                        const float t = sum + y;
+                        comp = (t - sum) - y;
+                        sum = t;
+                    }
                 }
+                double tot = (double)sum - (double)comp;
+                if (halves == 2) tot += __shfl_xor_sync(FULL, tot, 16);
+                if (act && hf == 0) sG[E.rad_out[rr]] = tot;
             }
-            sG[E.rad_out[rr]] = acc;
         }
         // angular
-        long long live = 0;
         if (NETA > 0) {
-            float acc[NETA > 0 ? NETA : 1][2][NNP_KMAX + 1];
+            constexpr int NQ = NETA > 0 ? NETA : 1;
+            constexpr int NA = NQ * 2 * (NNP_KMAX + 1);   // dense accumulators, index (q*2 + l)*(KMAX+1) + k
+            float acc[NQ][2][NNP_KMAX + 1];
 #pragma unroll
-            for (int q = 0; q < (NETA > 0 ? NETA : 1); ++q)
+            for (int q = 0; q < NQ; ++q)
 #pragma unroll
                 for (int l = 0; l < 2; ++l)
 #pragma unroll
-                    for (int k = 0; k <= NNP_KMAX; ++k) acc[q][l][k] = 0.f;
-            int j = 0, k = 1 + lane;
-            pair_normalize(j, k, M);
-            const int T = M * (M - 1) / 2;
-            for (int b0 = 0; b0 < T; b0 += 32) {
-                if (j < M - 1) {
-                    const float4 a = nd[j], b = nd[k];
-                    bool ok = true;
-                    float fcd = 1.f, rd2 = 0.f;
-                    if (NARROW) {
-                        const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
-                        rd2 = ex * ex + ey * ey + ez * ez;
-                        ok = rd2 < P.rc2;
-                        if (ok) {
+                    for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[q][l][kk] = 0.f;
+            const int nb = (M + 31) >> 5;
+            for (int A = 0; A < nb; ++A) {
+                const int j = 32 * A + lane;
+                const bool vj = j < M;
+                const float4 a = vj ? w.nd[j] : make_float4(0.f, 0.f, 0.f, 1.f);
+                const float ia = vj ? w.ninv[j] : 0.f;
+                const float4 pa4 = vj ? w.npf[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float pav[4] = {pa4.x, pa4.y, pa4.z, pa4.w};
+                for (int B = A; B < nb; ++B) {
+                    unsigned mask = live_mask<NARROW>(A, B, lane, M, a, w.nd, P.rc2);
+                    c_trip += __popc(mask);
+                    while (mask) {
+                        const int s = __ffs(mask) - 1;
+                        mask &= mask - 1u;
+                        const int k = 32 * B + ((lane + s) & 31);
+                        const float4 b = w.nd[k];
+                        const float4 pb4 = w.npf[k];
+                        const float pbv[4] = {pb4.x, pb4.y, pb4.z, pb4.w};
+                        const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * (ia * w.ninv[k]);
+                        float fcd = 1.f, rd2 = 0.f;
+                        if (NARROW) {
+                            const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+                            rd2 = ex * ex + ey * ey + ez * ez;
                             float dfcd;
                             cutoff_fn_fast(sqrtf(rd2), P.hpi_rc, fcd, dfcd);
                         }
-                    }
-                    if (ok) {
-                        ++live;
-                        const float4 pa = npf[j], pb = npf[k];
-                        const float pav[4] = {pa.x, pa.y, pa.z, pa.w}, pbv[4] = {pb.x, pb.y, pb.z, pb.w};
-                        const float c = __fdividef(a.x * b.x + a.y * b.y + a.z * b.z, a.w * b.w);
                         float pw[2][NNP_KMAX + 1];
                         pw[0][0] = 1.f + c;
                         pw[1][0] = 1.f - c;
@@ -215,23 +321,27 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                         }
                     }
                 }
-                k += 32;
-                pair_normalize(j, k, M);
             }
+            // lane partials: compensated reduce-scatter, lane t gets accumulator 32c + t;
+            // prefactor 2^(1 - zeta), zeta = 2^k
 #pragma unroll
-            for (int q = 0; q < NETA; ++q)
+            for (int c0 = 0; c0 < NA; c0 += 32) {
+                float v[32];
 #pragma unroll
-                for (int l = 0; l < 2; ++l)
-#pragma unroll
-                    for (int kk = 0; kk <= NNP_KMAX; ++kk) {
-                        // lane partials summed in FP64; prefactor 2^(1 - zeta), zeta = 2^kk
-                        const double v = warp_sum_d((double)acc[q][l][kk]);
-                        const int o = E.ang_out[q][l][kk];
-                        if (lane == 0 && o >= 0) sG[o] = v * (double)exp2f((float)(1 - (1 << kk)));
-                    }
-            if (lane == 0) {
-                c_pairs += (unsigned long long)T;
+                for (int t = 0; t < 32; ++t) {
+                    const int idx = c0 + t;
+                    v[t] = (idx < NA) ? acc[idx / (2 * (NNP_KMAX + 1))][(idx / (NNP_KMAX + 1)) % 2][idx % (NNP_KMAX + 1)]
+                                      : 0.f;
+                }
+                const double tot = warp_reduce_scatter32(v, lane);
+                const int idx = c0 + lane;
+                if (idx < NA) {
+                    const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
+                    const int o = (q < E.n_eta) ? E.ang_out[q][l][kk] : -1;
+                    if (o >= 0) sG[o] = tot * (double)exp2f((float)(1 - (1 << kk)));
+                }
             }
+            if (lane == 0) c_pairs += (unsigned long long)M * (M - 1) / 2;
         }
         __syncwarp();
         for (int s = lane; s < E.n_g; s += 32) {
@@ -240,7 +350,6 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             if (Graw) Graw[(size_t)i * E.n_g + s] = (float)g;
         }
         __syncwarp();
-        c_trip += (unsigned long long)live;   // per lane; reduced over the warp at the end
         if (lane == 0) {
             c_list += (unsigned long long)n_list;
             c_rc += (unsigned long long)M;
@@ -259,11 +368,41 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
 }
 
 // ---------------------------------------------------------------- force pass
+// Writes the live pairs (l, s) of block (A, B), s-major, into the warp queue and
+// returns their number.  The 32 x 32 liveness bits are transposed with ballots so
+// that lane s owns column s; consecutive queue entries then share s, which keeps
+// both j and k distinct inside a batch of 32.
+__device__ __forceinline__ int enqueue_block(unsigned mask, int lane, unsigned short* queue)
+{
+    unsigned col = 0u;
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+        const unsigned b = __ballot_sync(FULL, (mask >> s) & 1u);
+        if (lane == s) col = b;
+    }
+    const int cnt = __popc(col);
+    int off = cnt;   // inclusive scan over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, off, o);
+        if (lane >= o) off += t;
+    }
+    const int total = __shfl_sync(FULL, off, 31);
+    off -= cnt;
+    while (col) {
+        const int l = __ffs(col) - 1;
+        col &= col - 1u;
+        queue[off++] = (unsigned short)(l | (lane << 5));
+    }
+    __syncwarp();
+    return total;
+}
+
 // g[i, slot] = dE_i/dd_ij for each list slot (0 outside the cutoff), Fown[i] =
 // sum_j g_ij (the force on i from its own energy), per-warp virial partials.
 template <int NETA, bool NARROW>
 __global__ void __launch_bounds__(256)
-k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int cap,
+k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
         double* __restrict__ vir_part, int* __restrict__ flags)
 {
@@ -271,15 +410,18 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     const Plan& P = *plan_g;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    const size_t per = (size_t)cap * (16 + 16 + 16 + 8 + 12) + (size_t)nv.stride * 4 + NNP_MAXG * 4;
-    unsigned char* base = smem + per * wib;
-    float4* nd = (float4*)base;
-    float4* npf = nd + cap;
-    float4* ndp = npf + cap;
-    float2* nfe = (float2*)(ndp + cap);
-    float* sg = (float*)(nfe + cap);
-    int* cmap = (int*)(sg + 3 * cap);
-    float* sW = (float*)(cmap + nv.stride);
+    unsigned char* base = smem + force_warp_bytes(C, nv.stride) * wib;
+    WarpSmem w;
+    w.nd = reinterpret_cast<float4*>(base);
+    w.npf = w.nd + C;
+    w.ndp = w.npf + C;
+    w.sg = reinterpret_cast<float*>(w.ndp + C);
+    float* sW = w.sg + 3 * C;
+    w.queue = reinterpret_cast<unsigned short*>(sW + NNP_MAXG);
+    w.srt = reinterpret_cast<short*>(w.queue + PAIR_QUEUE);
+    w.cmap = w.srt + C;
+    w.ninv = nullptr;
+    w.nfe = nullptr;
 
     double vir[9];
 #pragma unroll
@@ -299,8 +441,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             klo[q] = (q < E.n_eta) ? E.ang_klo[q] : 0.f;
         }
         int n_list;
-        const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, cap, nd, npf, ndp, nfe,
-                                                  cmap, sg, sW, lane, flags, n_list);
+        const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
+                                                  n_list);
         if (NETA > 0) {
             // dense weights W[q][l][k] = dE/dG_o * 2^(1-zeta); Wd = W * lambda * zeta
             float W[NETA > 0 ? NETA : 1][2][NNP_KMAX + 1], Wd[NETA > 0 ? NETA : 1][2][NNP_KMAX + 1];
@@ -311,86 +453,89 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
 #pragma unroll
                     for (int kk = 0; kk <= NNP_KMAX; ++kk) {
                         const int o = (q < E.n_eta) ? E.ang_out[q][l][kk] : -1;
-                        const float w = (o >= 0) ? sW[o] * exp2f((float)(1 - (1 << kk))) : 0.f;
-                        W[q][l][kk] = w;
-                        Wd[q][l][kk] = w * (l == 0 ? 1.f : -1.f) * (float)(1 << kk);
+                        const float wt = (o >= 0) ? sW[o] * exp2f((float)(1 - (1 << kk))) : 0.f;
+                        W[q][l][kk] = wt;
+                        Wd[q][l][kk] = wt * (l == 0 ? 1.f : -1.f) * (float)(1 << kk);
                     }
-            int j = 0, k = 1 + lane;
-            pair_normalize(j, k, M);
-            const int T = M * (M - 1) / 2;
-            for (int b0 = 0; b0 < T; b0 += 32) {
-                if (j < M - 1) {
-                    const float4 a = nd[j], b = nd[k];
-                    const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
-                    bool ok = true;
-                    float fcd = 1.f, dfcd = 0.f, rd2 = 0.f, rd = 1.f;
-                    if (NARROW) {
-                        rd2 = ex * ex + ey * ey + ez * ez;
-                        ok = rd2 < P.rc2;
-                        if (ok) {
-                            rd = sqrtf(rd2);
-                            cutoff_fn_fast(rd, P.hpi_rc, fcd, dfcd);
-                        }
-                    }
-                    if (ok) {
-                        const float4 pa = npf[j], pb = npf[k], qa = ndp[j], qb = ndp[k];
-                        const float pav[4] = {pa.x, pa.y, pa.z, pa.w}, pbv[4] = {pb.x, pb.y, pb.z, pb.w};
-                        const float qav[4] = {qa.x, qa.y, qa.z, qa.w}, qbv[4] = {qb.x, qb.y, qb.z, qb.w};
-                        const float inv_a = __frcp_rn(a.w), inv_b = __frcp_rn(b.w);
-                        const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * inv_a * inv_b;
-                        // p[l][k] = b_l^(2^k), qq[l][k] = b_l^(2^k - 1), b_l = 1 +- c
-                        float pw[2][NNP_KMAX + 1], qw[2][NNP_KMAX + 1];
-#pragma unroll
-                        for (int l = 0; l < 2; ++l) {
-                            const float bl = (l == 0) ? 1.f + c : 1.f - c;
-                            qw[l][0] = 1.f;
-                            pw[l][0] = bl;
-#pragma unroll
-                            for (int kk = 1; kk <= NNP_KMAX; ++kk) {
-                                qw[l][kk] = qw[l][kk - 1] * pw[l][kk - 1];
-                                pw[l][kk] = pw[l][kk - 1] * pw[l][kk - 1];
-                            }
-                        }
-                        float phic = 0.f, phia = 0.f, phib = 0.f, phid = 0.f;
-#pragma unroll
-                        for (int q = 0; q < NETA; ++q) {
-                            float S = 0.f, D = 0.f;
-#pragma unroll
-                            for (int l = 0; l < 2; ++l)
-#pragma unroll
-                                for (int kk = 0; kk <= NNP_KMAX; ++kk) {
-                                    S = fmaf(W[q][l][kk], pw[l][kk], S);
-                                    D = fmaf(Wd[q][l][kk], qw[l][kk], D);
-                                }
-                            float Pd = 1.f, dPd = 0.f;
+            const int nb = (M + 31) >> 5;
+            for (int A = 0; A < nb; ++A) {
+                const int jl = 32 * A + lane;
+                const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int B = A; B < nb; ++B) {
+                    const unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
+                    const int total = enqueue_block(mask, lane, w.queue);
+                    for (int e0 = 0; e0 < total; e0 += 32) {
+                        const int e = e0 + lane;
+                        if (e < total) {
+                            const int ent = w.queue[e];
+                            const int l = ent & 31, s = ent >> 5;
+                            const int j = 32 * A + l, k = 32 * B + ((l + s) & 31);
+                            const float4 a = w.nd[j], b = w.nd[k];
+                            const float ia = a.w, ib = b.w;
+                            const float4 pa4 = w.npf[j], qa4 = w.ndp[j], pb4 = w.npf[k], qb4 = w.ndp[k];
+                            const float pav[4] = {pa4.x, pa4.y, pa4.z, pa4.w}, qav[4] = {qa4.x, qa4.y, qa4.z, qa4.w};
+                            const float pbv[4] = {pb4.x, pb4.y, pb4.z, pb4.w}, qbv[4] = {qb4.x, qb4.y, qb4.z, qb4.w};
+                            const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+                            const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * (ia * ib);
+                            float fcd = 1.f, dfcd = 0.f, rd2 = 0.f, rd = 1.f;
                             if (NARROW) {
-                                const float ed = gauss2(khi[q], klo[q], rd2);
-                                Pd = ed * fcd;
-                                dPd = ed * (dfcd - 2.0f * etav[q] * rd * fcd);
+                                rd2 = ex * ex + ey * ey + ez * ez;
+                                rd = sqrtf(rd2);
+                                cutoff_fn_fast(rd, P.hpi_rc, fcd, dfcd);
                             }
-                            const float pab = pav[q] * pbv[q];
-                            phic = fmaf(D, pab * Pd, phic);
-                            const float SPd = S * Pd;
-                            phia = fmaf(SPd * qav[q], pbv[q], phia);
-                            phib = fmaf(SPd * pav[q], qbv[q], phib);
-                            if (NARROW) phid = fmaf(S * pab, dPd, phid);
+                            // p[l][k] = b_l^(2^k), qw[l][k] = b_l^(2^k - 1), b_l = 1 +- c
+                            float pw[2][NNP_KMAX + 1], qw[2][NNP_KMAX + 1];
+#pragma unroll
+                            for (int lb = 0; lb < 2; ++lb) {
+                                const float bl = (lb == 0) ? 1.f + c : 1.f - c;
+                                qw[lb][0] = 1.f;
+                                pw[lb][0] = bl;
+#pragma unroll
+                                for (int kk = 1; kk <= NNP_KMAX; ++kk) {
+                                    qw[lb][kk] = qw[lb][kk - 1] * pw[lb][kk - 1];
+                                    pw[lb][kk] = pw[lb][kk - 1] * pw[lb][kk - 1];
+                                }
+                            }
+                            float phic = 0.f, phia = 0.f, phib = 0.f, phid = 0.f;
+#pragma unroll
+                            for (int q = 0; q < NETA; ++q) {
+                                float S = 0.f, D = 0.f;
+#pragma unroll
+                                for (int lb = 0; lb < 2; ++lb)
+#pragma unroll
+                                    for (int kk = 0; kk <= NNP_KMAX; ++kk) {
+                                        S = fmaf(W[q][lb][kk], pw[lb][kk], S);
+                                        D = fmaf(Wd[q][lb][kk], qw[lb][kk], D);
+                                    }
+                                float Pd = 1.f, dPd = 0.f;
+                                if (NARROW) {
+                                    const float ed = gauss2(khi[q], klo[q], rd2);
+                                    Pd = ed * fcd;
+                                    dPd = ed * (dfcd - 2.0f * etav[q] * rd * fcd);
+                                }
+                                const float pab = pav[q] * pbv[q];
+                                phic = fmaf(D, pab * Pd, phic);
+                                const float SPd = S * Pd;
+                                phia = fmaf(SPd * qav[q], pbv[q], phia);
+                                phib = fmaf(SPd * pav[q], qbv[q], phib);
+                                if (NARROW) phid = fmaf(S * pab, dPd, phid);
+                            }
+                            // g_a = phic (b/(ra rb) - c a/ra^2) + phia a/ra - phid (b - a)/rd
+                            // g_b = phic (a/(ra rb) - c b/rb^2) + phib b/rb + phid (b - a)/rd
+                            const float cab = phic * ia * ib;
+                            const float ca = phia * ia - phic * c * ia * ia;
+                            const float cb = phib * ib - phic * c * ib * ib;
+                            const float cd = NARROW ? phid / rd : 0.f;
+                            atomicAdd(&w.sg[3 * j + 0], ca * a.x + cab * b.x - cd * ex);
+                            atomicAdd(&w.sg[3 * j + 1], ca * a.y + cab * b.y - cd * ey);
+                            atomicAdd(&w.sg[3 * j + 2], ca * a.z + cab * b.z - cd * ez);
+                            atomicAdd(&w.sg[3 * k + 0], cb * b.x + cab * a.x + cd * ex);
+                            atomicAdd(&w.sg[3 * k + 1], cb * b.y + cab * a.y + cd * ey);
+                            atomicAdd(&w.sg[3 * k + 2], cb * b.z + cab * a.z + cd * ez);
                         }
-                        // g_a = phic (b/(ra rb) - c a/ra^2) + phia a/ra - phid (b - a)/rd
-                        // g_b = phic (a/(ra rb) - c b/rb^2) + phib b/rb + phid (b - a)/rd
-                        const float cab = phic * inv_a * inv_b;
-                        const float ca = phia * inv_a - phic * c * inv_a * inv_a;
-                        const float cb = phib * inv_b - phic * c * inv_b * inv_b;
-                        const float cd = NARROW ? phid / rd : 0.f;
-                        atomicAdd(&sg[3 * j + 0], ca * a.x + cab * b.x - cd * ex);
-                        atomicAdd(&sg[3 * j + 1], ca * a.y + cab * b.y - cd * ey);
-                        atomicAdd(&sg[3 * j + 2], ca * a.z + cab * b.z - cd * ez);
-                        atomicAdd(&sg[3 * k + 0], cb * b.x + cab * a.x + cd * ex);
-                        atomicAdd(&sg[3 * k + 1], cb * b.y + cab * a.y + cd * ey);
-                        atomicAdd(&sg[3 * k + 2], cb * b.z + cab * a.z + cd * ez);
                     }
+                    __syncwarp();
                 }
-                k += 32;
-                pair_normalize(j, k, M);
             }
         }
         __syncwarp();
@@ -398,15 +543,16 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         const int cnt = n_list;
         float4* grow = gbuf + (size_t)i * nv.stride;
         for (int s = lane; s < cnt; s += 32) {
-            const int c = cmap[s];
-            grow[s] = (c >= 0) ? make_float4(sg[3 * c], sg[3 * c + 1], sg[3 * c + 2], 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const int c = w.cmap[s];
+            grow[s] = (c >= 0) ? make_float4(w.sg[3 * c], w.sg[3 * c + 1], w.sg[3 * c + 2], 0.f)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float fx = 0.f, fy = 0.f, fz = 0.f, v[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) v[q] = 0.f;
         for (int m = lane; m < M; m += 32) {
-            const float4 d = nd[m];
-            const float gx = sg[3 * m], gy = sg[3 * m + 1], gz = sg[3 * m + 2];
+            const float4 d = w.nd[m];
+            const float gx = w.sg[3 * m], gy = w.sg[3 * m + 1], gz = w.sg[3 * m + 2];
             fx += gx; fy += gy; fz += gz;
             v[0] -= d.x * gx; v[1] -= d.x * gy; v[2] -= d.x * gz;
             v[3] -= d.y * gx; v[4] -= d.y * gy; v[5] -= d.y * gz;

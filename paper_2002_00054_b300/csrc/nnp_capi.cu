@@ -266,11 +266,8 @@ static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
     }
 }
 
-static size_t sf_smem_per_warp(int cap) { return (size_t)cap * (16 + 16 + 8) + NNP_MAXG * 8; }
-static size_t force_smem_per_warp(int cap, int stride)
-{
-    return (size_t)cap * (16 + 16 + 16 + 8 + 12) + (size_t)stride * 4 + NNP_MAXG * 4;
-}
+static size_t sf_smem_per_warp(int cap) { return sf_warp_bytes(cap); }
+static size_t force_smem_per_warp(int cap, int stride) { return force_warp_bytes(cap, stride); }
 
 // ------------------------------------------------------------------ scratch
 template <typename T>
@@ -612,9 +609,16 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     h->n_params = n_params;
     h->cutoff = params->cutoff;
     h->skin = params->skin;
-    h->stride = (params->max_neighbors + 3) & ~3;   // multiple of 4 keeps per-warp shared arrays 16-byte aligned
+    h->stride = (params->max_neighbors + 7) & ~7;   // multiple of 8 keeps per-warp shared arrays 16-byte aligned
     h->precision = params->mlp_precision;
-    h->cap_rc = h->stride;
+    {
+        // capacity for entries inside the cutoff: the list's headroom over the same
+        // volume ratio, (rc / (rc + skin))^3
+        const double ratio = std::pow(params->cutoff / (params->cutoff + params->skin), 3.0);
+        int c = (int)std::ceil(h->stride * ratio);
+        c = std::max(32, (c + 7) & ~7);
+        h->cap_rc = std::min(c, h->stride);
+    }
     DeviceGuard g(device);
     auto fail = [&](int code) {
         g_create_err = h->err;
