@@ -30,7 +30,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
     tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
+    # -ftz=true: denormal results flush to zero (no quantity here is ever below 1e-38)
+    cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-ftz=true", "-shared", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-fvisibility=hidden", "-I", os.path.join(ROOT, "include"),
            "-o", tmp, MAIN, "-lcudart", *extra]
     if verbose:

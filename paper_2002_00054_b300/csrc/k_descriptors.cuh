@@ -5,19 +5,16 @@
 // Sec. 4.3, with the neighbour and pair loops spread over the 32 lanes).
 //
 // Staging.  The warp keeps its atom's neighbours inside the cutoff in shared
-// memory, sorted by distance: per neighbour the displacement d, r, 1/r and the
-// angular pair factors P_q(r) = exp(-eta_q r^2) f_c(r) (force pass also
-// dP_q/dr), computed once per atom.  Sorting groups neighbours of similar r,
-// which have similar numbers of contributing partners.
+// memory (compacted with a ballot): per neighbour the displacement d, r or 1/r
+// and the angular pair factors P_q(r) = exp(-eta_q r^2) f_c(r) (force pass also
+// dP_q/dr), computed once per atom.
 //
-// Pairs j < k are walked as 32 x 32 blocks of the sorted list: in block (A, B)
-// lane l takes j = 32A + l and partners k = 32B + (l + s) mod 32.  For the
-// narrow functions each lane first builds a bitmask of the partners with
-// r_jk < r_c (about half of them).  The descriptor pass keeps j in registers
-// and visits its live partners; the force pass, whose per-pair work is three
-// times larger, packs the live pairs of a block into a warp queue (s-major, so
-// j and k stay distinct within a batch) and processes them 32 at a time with
-// every lane busy.
+// Pairs j < k are walked as 32 x 32 blocks of the list: in block (A, B) lane l
+// takes j = 32A + l and partners k = 32B + (l + s) mod 32.  Each lane builds a
+// bitmask of its partners that contribute (narrow: r_jk < r_c, about half);
+// the 32 masks are transposed into a warp queue of live pairs (s-major, so j
+// and k stay distinct within a batch) and processed 32 at a time with every
+// lane busy, whatever the spread of live partners per j.
 //
 // Angular accumulators are dense in (eta_q, lambda, k) with zeta = 2^k: the
 // powers (1 +- cos)^(2^k) come from repeated squaring, and the model's
@@ -37,29 +34,31 @@ struct NbView {
     int stride;
 };
 
+#define PAIR_QUEUE 1024   // live pairs of one 32 x 32 block, as (l | s << 5)
+
 // Per-warp shared-memory arrays (C = capacity inside the cutoff, S = list stride).
 struct WarpSmem {
-    float4* nd;     // (dx, dy, dz, r), distance-sorted
-    float* ninv;    // 1 / r
+    float4* nd;     // (dx, dy, dz, r) (descriptor pass) or (dx, dy, dz, 1/r) (force pass)
+    float* ninv;    // 1 / r (descriptor pass)
     float4* npf;    // P_q
     float4* ndp;    // dP_q / dr (force)
     float2* nfe;    // (f_c, element) (descriptor pass)
     float* sg;      // g accumulators, 3 per neighbour (force)
-    unsigned short* queue;   // live pairs of the current block (force)
-    short* srt;     // list slot of each sorted neighbour
-    short* cmap;    // sorted index of each list slot, -1 outside the cutoff (force)
+    unsigned short* queue;   // live pairs of the current block
+    short* cmap;    // compact index of each list slot, -1 outside the cutoff (force)
 };
 
-__host__ __device__ inline size_t sf_warp_bytes(int C) { return (size_t)C * (16 + 16 + 4 + 8 + 2) + NNP_MAXG * 8; }
-#define PAIR_QUEUE 1024   // live pairs of one 32 x 32 block, as (l | s << 5)
+__host__ __device__ inline size_t sf_warp_bytes(int C)
+{
+    return (size_t)C * (16 + 4 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2;
+}
 __host__ __device__ inline size_t force_warp_bytes(int C, int S)
 {
-    return (size_t)C * (16 + 16 + 16 + 12 + 2) + (size_t)S * 2 + PAIR_QUEUE * 2 + NNP_MAXG * 4;
+    return (size_t)C * (16 + 16 + 16 + 12) + PAIR_QUEUE * 2 + NNP_MAXG * 4 + (size_t)S * 2;
 }
 
-// Stages the neighbours of atom i within the cutoff (see file comment).  Returns M.
-// nd[m].w holds r (descriptor pass, 1/r in ninv) or 1/r (force pass).
-// FORCE: also dP/dr, the radial part of g (into sg) and the slot map.
+// Stages the neighbours of atom i within the cutoff, compacted in list order.
+// Returns M.  FORCE: nd.w = 1/r, dP/dr, the radial part of g (into sg), slot map.
 template <int NETA, bool FORCE>
 __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box& bx, const NbView& nv,
                                                const float4* __restrict__ pos4, const Plan& P, const ElemPlan& E,
@@ -69,30 +68,63 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
     const int cnt = nv.ncount[i];
     n_list = cnt;
     const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
-    // the key and compact-slot temporaries live in the npf area, written only in pass 3
-    float* skey = reinterpret_cast<float*>(w.npf);
-    int* cslot = reinterpret_cast<int*>(w.npf) + C;
-    // pass 1: compact the slots inside the cutoff (key r^2)
     int M = 0;
     for (int base = 0; base < cnt; base += 32) {
         const int s = base + lane;
         bool keep = false;
-        float r2 = 0.f;
+        float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
+        int ej = 0;
         if (s < cnt) {
             const uint32_t e = row[s];
             const float4 pj = pos4[e & NB_INDEX_MASK];
             float ox, oy, oz;
             nb_shift(e, bx.L[0], bx.L[1], bx.L[2], ox, oy, oz);
-            const float dx = pair_disp(pj.x, pi.x, ox), dy = pair_disp(pj.y, pi.y, oy), dz = pair_disp(pj.z, pi.z, oz);
+            dx = pair_disp(pj.x, pi.x, ox);
+            dy = pair_disp(pj.y, pi.y, oy);
+            dz = pair_disp(pj.z, pi.z, oz);
             r2 = dx * dx + dy * dy + dz * dz;
+            ej = __float_as_int(pj.w);
             keep = r2 < P.rc2;
-            if (FORCE) w.cmap[s] = -1;
         }
         const unsigned m = __ballot_sync(FULL, keep);
         const int at = M + __popc(m & ((1u << lane) - 1u));
+        if (FORCE && s < cnt) w.cmap[s] = (keep && at < C) ? (short)at : (short)-1;
         if (keep && at < C) {
-            skey[at] = r2;
-            cslot[at] = s;
+            if (r2 < 1e-8f) atomicOr(&flags[FLAG_ERR], ERR_CLOSE);
+            const float r = sqrtf(r2);
+            const float ir = 1.0f / r;
+            float fc, dfc;
+            cutoff_fn(r, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, fc, dfc);
+            float pq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int q = 0; q < NETA; ++q) {
+                const float ex = gauss2(khi[q], klo[q], r2);
+                pq[q] = ex * fc;
+                dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
+            }
+            w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
+            if (!FORCE) {
+                w.nd[at] = make_float4(dx, dy, dz, r);
+                w.ninv[at] = ir;
+                w.nfe[at] = make_float2(fc, __int_as_float(ej));
+            } else {
+                w.nd[at] = make_float4(dx, dy, dz, ir);
+                w.ndp[at] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+                // radial part of g_ij: sum over radial descriptors of dE/dG * dG/dr * d / r
+                float gr = 0.f;
+                for (int rr = 0; rr < E.n_rad; ++rr) {
+                    const int el = E.rad_elem[rr];
+                    if (el < 0 || el == ej) {
+                        const float x = r - E.rad_rs[rr];
+                        const float ex = gauss2(E.rad_khi[rr], E.rad_klo[rr], x * x);
+                        gr += sW[E.rad_out[rr]] * ex * (dfc - 2.0f * E.rad_eta[rr] * x * fc);
+                    }
+                }
+                const float gs = gr * ir;
+                w.sg[3 * at + 0] = gs * dx;
+                w.sg[3 * at + 1] = gs * dy;
+                w.sg[3 * at + 2] = gs * dz;
+            }
         }
         M += __popc(m);
     }
@@ -101,103 +133,84 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
         M = C;
     }
     __syncwarp();
-    // pass 2: rank by r^2 (ties by compact index) -> srt[rank] = slot
-    for (int m = lane; m < M; m += 32) {
-        const float key = skey[m];
-        int rank = 0;
-        for (int t = 0; t < M; ++t) {
-            const float kt = skey[t];
-            rank += (kt < key) || (kt == key && t < m);
-        }
-        w.srt[rank] = (short)cslot[m];
-    }
-    __syncwarp();
-    // pass 3: per sorted neighbour, recompute d from the list entry and fill the arrays
-    for (int m = lane; m < M; m += 32) {
-        const int s = w.srt[m];
-        const uint32_t e = row[s];
-        const float4 pj = pos4[e & NB_INDEX_MASK];
-        float ox, oy, oz;
-        nb_shift(e, bx.L[0], bx.L[1], bx.L[2], ox, oy, oz);
-        const float dx = pair_disp(pj.x, pi.x, ox), dy = pair_disp(pj.y, pi.y, oy), dz = pair_disp(pj.z, pi.z, oz);
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        if (r2 < 1e-8f) atomicOr(&flags[FLAG_ERR], ERR_CLOSE);
-        const float r = sqrtf(r2);
-        const float ir = 1.0f / r;
-        float fc, dfc;
-        cutoff_fn(r, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, fc, dfc);
-        if (FORCE) {
-            w.nd[m] = make_float4(dx, dy, dz, ir);
-        } else {
-            w.nd[m] = make_float4(dx, dy, dz, r);
-            w.ninv[m] = ir;
-        }
-        float pq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int q = 0; q < NETA; ++q) {
-            const float ex = gauss2(khi[q], klo[q], r2);
-            pq[q] = ex * fc;
-            dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
-        }
-        const int ej = __float_as_int(pj.w);
-        if (!FORCE) {
-            w.nfe[m] = make_float2(fc, __int_as_float(ej));
-        } else {
-            w.ndp[m] = make_float4(dq[0], dq[1], dq[2], dq[3]);
-            w.cmap[s] = (short)m;
-            // radial part of g_ij: sum over radial descriptors of dE/dG * dG/dr * d / r
-            float gr = 0.f;
-            for (int rr = 0; rr < E.n_rad; ++rr) {
-                const int el = E.rad_elem[rr];
-                if (el < 0 || el == ej) {
-                    const float x = r - E.rad_rs[rr];
-                    const float ex = gauss2(E.rad_khi[rr], E.rad_klo[rr], x * x);
-                    gr += sW[E.rad_out[rr]] * ex * (dfc - 2.0f * E.rad_eta[rr] * x * fc);
-                }
-            }
-            const float gs = gr * ir;
-            w.sg[3 * m + 0] = gs * dx;
-            w.sg[3 * m + 1] = gs * dy;
-            w.sg[3 * m + 2] = gs * dz;
-        }
-        // npf overlays the pass-1 temporaries, which pass 3 no longer reads
-        w.npf[m] = make_float4(pq[0], pq[1], pq[2], pq[3]);
-    }
-    __syncwarp();
     return M;
 }
 
-// Partner step s of lane l in block pair (A, B): valid when both exist and, on the
-// diagonal block, each unordered pair is taken once (s in 1..15, or 16 for l < 16).
-__device__ __forceinline__ bool pair_valid(int A, int B, int l, int s, int M)
+// Valid partner steps s of lane l in block pair (A, B): k = 32B + (l + s) mod 32
+// must exist (and j = 32A + l); on the diagonal block each unordered pair is
+// taken once (s in 1..15, or 16 for l < 16).
+__device__ __forceinline__ unsigned valid_mask(int A, int B, int l, int M)
 {
-    const int j = 32 * A + l, k = 32 * B + ((l + s) & 31);
-    if (j >= M || k >= M) return false;
-    if (A < B) return true;
-    return (s >= 1 && s <= 15) || (s == 16 && l < 16);
+    if (32 * A + l >= M) return 0u;
+    const int nk = M - 32 * B;   // partners present in block B
+    unsigned m = 0xffffffffu;
+    if (nk < 32) {
+        const unsigned low = (1u << nk) - 1u;          // positions p < nk
+        m = __funnelshift_r(low, low, l);               // bit s <-> position (l + s) mod 32
+    }
+    if (A == B) m &= 0x0000fffeu | (l < 16 ? 0x00010000u : 0u);
+    return m;
 }
 
-// Bitmask over s = 0..31 of the contributing partners of lane l's j in block (A, B).
+// Bitmask over s of the contributing partners of lane l's j in block (A, B).
 template <bool NARROW>
 __device__ __forceinline__ unsigned live_mask(int A, int B, int l, int M, const float4 a, const float4* nd, float rc2)
 {
+    unsigned v = valid_mask(A, B, l, M);
+    if (!NARROW) return v;
     unsigned mask = 0u;
-#pragma unroll 4
-    for (int s = 0; s < 32; ++s) {
-        if (!pair_valid(A, B, l, s, M)) continue;
-        if (NARROW) {
-            const float4 b = nd[32 * B + ((l + s) & 31)];
-            const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
-            if (ex * ex + ey * ey + ez * ez < rc2) mask |= 1u << s;
-        } else {
-            mask |= 1u << s;
-        }
+    while (v) {
+        const int s = __ffs(v) - 1;
+        v &= v - 1u;
+        const float4 b = nd[32 * B + ((l + s) & 31)];
+        const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+        if (ex * ex + ey * ey + ez * ez < rc2) mask |= 1u << s;
     }
     return mask;
 }
 
+// Transposes the warp's 32 x 32 bit matrix (row = lane): lane s returns column s.
+__device__ __forceinline__ unsigned transpose32(unsigned m, int lane)
+{
+    const unsigned lo[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const int j = 16 >> t;
+        const unsigned o = __shfl_xor_sync(FULL, m, j);
+        if (lane & j) m = (m & ~lo[t]) | ((o & ~lo[t]) >> j);
+        else m = (m & lo[t]) | ((o & lo[t]) << j);
+    }
+    return m;
+}
+
+// Writes the live pairs (l, s) of one block, s-major, into the warp queue and
+// returns their number.  Consecutive entries share s, so j and k are distinct
+// across the lanes of a batch of 32 (up to where the batch crosses an s boundary).
+__device__ __forceinline__ int enqueue_block(unsigned mask, int lane, unsigned short* queue)
+{
+    unsigned col = transpose32(mask, lane);
+    const int cnt = __popc(col);
+    int off = cnt;   // inclusive scan over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, off, o);
+        if (lane >= o) off += t;
+    }
+    const int total = __shfl_sync(FULL, off, 31);
+    off -= cnt;
+    while (col) {
+        const int l = __ffs(col) - 1;
+        col &= col - 1u;
+        queue[off++] = (unsigned short)(l | (lane << 5));
+    }
+    __syncwarp();
+    return total;
+}
+
 // ---------------------------------------------------------------- value pass
-template <int NETA, bool NARROW>
+// KP / KN: largest k (zeta = 2^k) among the lambda = +1 / -1 functions; powers and
+// terms beyond them are compiled out.
+template <int NETA, bool NARROW, int KP, int KN>
 __global__ void __launch_bounds__(256)
 k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g,
      int C, float* __restrict__ Gs, float* __restrict__ Graw, int* __restrict__ flags,
@@ -214,7 +227,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     double* sG = reinterpret_cast<double*>(w.npf + C);
     w.ninv = reinterpret_cast<float*>(sG + NNP_MAXG);
     w.nfe = reinterpret_cast<float2*>(w.ninv + C);
-    w.srt = reinterpret_cast<short*>(w.nfe + C);
+    w.queue = reinterpret_cast<unsigned short*>(w.nfe + C);
     w.ndp = nullptr;
     w.sg = nullptr;
     w.cmap = nullptr;
@@ -278,48 +291,50 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                     for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[q][l][kk] = 0.f;
             const int nb = (M + 31) >> 5;
             for (int A = 0; A < nb; ++A) {
-                const int j = 32 * A + lane;
-                const bool vj = j < M;
-                const float4 a = vj ? w.nd[j] : make_float4(0.f, 0.f, 0.f, 1.f);
-                const float ia = vj ? w.ninv[j] : 0.f;
-                const float4 pa4 = vj ? w.npf[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float pav[4] = {pa4.x, pa4.y, pa4.z, pa4.w};
+                const int jl = 32 * A + lane;
+                const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
                 for (int B = A; B < nb; ++B) {
-                    unsigned mask = live_mask<NARROW>(A, B, lane, M, a, w.nd, P.rc2);
+                    const unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
                     c_trip += __popc(mask);
-                    while (mask) {
-                        const int s = __ffs(mask) - 1;
-                        mask &= mask - 1u;
-                        const int k = 32 * B + ((lane + s) & 31);
-                        const float4 b = w.nd[k];
-                        const float4 pb4 = w.npf[k];
-                        const float pbv[4] = {pb4.x, pb4.y, pb4.z, pb4.w};
-                        const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * (ia * w.ninv[k]);
-                        float fcd = 1.f, rd2 = 0.f;
-                        if (NARROW) {
-                            const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
-                            rd2 = ex * ex + ey * ey + ez * ez;
-                            float dfcd;
-                            cutoff_fn_fast(sqrtf(rd2), P.hpi_rc, fcd, dfcd);
-                        }
-                        float pw[2][NNP_KMAX + 1];
-                        pw[0][0] = 1.f + c;
-                        pw[1][0] = 1.f - c;
+                    const int total = enqueue_block(mask, lane, w.queue);
+                    for (int e0 = 0; e0 < total; e0 += 32) {
+                        const int e = e0 + lane;
+                        if (e < total) {
+                            const int ent = w.queue[e];
+                            const int l = ent & 31, sidx = ent >> 5;
+                            const int j = 32 * A + l, k = 32 * B + ((l + sidx) & 31);
+                            const float4 a = w.nd[j], b = w.nd[k];
+                            const float4 pa4 = w.npf[j], pb4 = w.npf[k];
+                            const float pav[4] = {pa4.x, pa4.y, pa4.z, pa4.w}, pbv[4] = {pb4.x, pb4.y, pb4.z, pb4.w};
+                            const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * (w.ninv[j] * w.ninv[k]);
+                            float fcd = 1.f, rd2 = 0.f;
+                            if (NARROW) {
+                                const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+                                rd2 = ex * ex + ey * ey + ez * ez;
+                                float dfcd;
+                                cutoff_fn_fast(rd2 * rsqrtf(rd2), P.hpi_rc, fcd, dfcd);
+                            }
+                            float pw[2][NNP_KMAX + 1];
+                            pw[0][0] = 1.f + c;
+                            pw[1][0] = 1.f - c;
 #pragma unroll
-                        for (int kk = 1; kk <= NNP_KMAX; ++kk) {
-                            pw[0][kk] = pw[0][kk - 1] * pw[0][kk - 1];
-                            pw[1][kk] = pw[1][kk - 1] * pw[1][kk - 1];
-                        }
+                            for (int kk = 1; kk <= NNP_KMAX; ++kk) {
+                                if (kk <= KP) pw[0][kk] = pw[0][kk - 1] * pw[0][kk - 1];
+                                if (kk <= KN) pw[1][kk] = pw[1][kk - 1] * pw[1][kk - 1];
+                            }
 #pragma unroll
-                        for (int q = 0; q < NETA; ++q) {
-                            float R = pav[q] * pbv[q];
-                            if (NARROW) R *= gauss2(khi[q], klo[q], rd2) * fcd;
+                            for (int q = 0; q < NETA; ++q) {
+                                float R = pav[q] * pbv[q];
+                                if (NARROW) R *= gauss2(khi[q], klo[q], rd2) * fcd;
 #pragma unroll
-                            for (int l = 0; l < 2; ++l)
+                                for (int lb = 0; lb < 2; ++lb)
 #pragma unroll
-                                for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[q][l][kk] = fmaf(pw[l][kk], R, acc[q][l][kk]);
+                                    for (int kk = 0; kk <= NNP_KMAX; ++kk)
+                                        if (kk <= (lb == 0 ? KP : KN)) acc[q][lb][kk] = fmaf(pw[lb][kk], R, acc[q][lb][kk]);
+                            }
                         }
                     }
+                    __syncwarp();
                 }
             }
             // lane partials: compensated reduce-scatter, lane t gets accumulator 32c + t;
@@ -368,39 +383,9 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
 }
 
 // ---------------------------------------------------------------- force pass
-// Writes the live pairs (l, s) of block (A, B), s-major, into the warp queue and
-// returns their number.  The 32 x 32 liveness bits are transposed with ballots so
-// that lane s owns column s; consecutive queue entries then share s, which keeps
-// both j and k distinct inside a batch of 32.
-__device__ __forceinline__ int enqueue_block(unsigned mask, int lane, unsigned short* queue)
-{
-    unsigned col = 0u;
-#pragma unroll
-    for (int s = 0; s < 32; ++s) {
-        const unsigned b = __ballot_sync(FULL, (mask >> s) & 1u);
-        if (lane == s) col = b;
-    }
-    const int cnt = __popc(col);
-    int off = cnt;   // inclusive scan over lanes
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(FULL, off, o);
-        if (lane >= o) off += t;
-    }
-    const int total = __shfl_sync(FULL, off, 31);
-    off -= cnt;
-    while (col) {
-        const int l = __ffs(col) - 1;
-        col &= col - 1u;
-        queue[off++] = (unsigned short)(l | (lane << 5));
-    }
-    __syncwarp();
-    return total;
-}
-
 // g[i, slot] = dE_i/dd_ij for each list slot (0 outside the cutoff), Fown[i] =
 // sum_j g_ij (the force on i from its own energy), per-warp virial partials.
-template <int NETA, bool NARROW>
+template <int NETA, bool NARROW, int KP, int KN>
 __global__ void __launch_bounds__(256)
 k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
@@ -418,8 +403,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     w.sg = reinterpret_cast<float*>(w.ndp + C);
     float* sW = w.sg + 3 * C;
     w.queue = reinterpret_cast<unsigned short*>(sW + NNP_MAXG);
-    w.srt = reinterpret_cast<short*>(w.queue + PAIR_QUEUE);
-    w.cmap = w.srt + C;
+    w.cmap = reinterpret_cast<short*>(w.queue + PAIR_QUEUE);
     w.ninv = nullptr;
     w.nfe = nullptr;
 
@@ -477,10 +461,11 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             const float pbv[4] = {pb4.x, pb4.y, pb4.z, pb4.w}, qbv[4] = {qb4.x, qb4.y, qb4.z, qb4.w};
                             const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
                             const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * (ia * ib);
-                            float fcd = 1.f, dfcd = 0.f, rd2 = 0.f, rd = 1.f;
+                            float fcd = 1.f, dfcd = 0.f, rd2 = 0.f, rd = 1.f, ird = 0.f;
                             if (NARROW) {
                                 rd2 = ex * ex + ey * ey + ez * ez;
-                                rd = sqrtf(rd2);
+                                ird = rsqrtf(rd2);
+                                rd = rd2 * ird;
                                 cutoff_fn_fast(rd, P.hpi_rc, fcd, dfcd);
                             }
                             // p[l][k] = b_l^(2^k), qw[l][k] = b_l^(2^k - 1), b_l = 1 +- c
@@ -492,8 +477,10 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                 pw[lb][0] = bl;
 #pragma unroll
                                 for (int kk = 1; kk <= NNP_KMAX; ++kk) {
-                                    qw[lb][kk] = qw[lb][kk - 1] * pw[lb][kk - 1];
-                                    pw[lb][kk] = pw[lb][kk - 1] * pw[lb][kk - 1];
+                                    if (kk <= (lb == 0 ? KP : KN)) {
+                                        qw[lb][kk] = qw[lb][kk - 1] * pw[lb][kk - 1];
+                                        pw[lb][kk] = pw[lb][kk - 1] * pw[lb][kk - 1];
+                                    }
                                 }
                             }
                             float phic = 0.f, phia = 0.f, phib = 0.f, phid = 0.f;
@@ -504,8 +491,10 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                 for (int lb = 0; lb < 2; ++lb)
 #pragma unroll
                                     for (int kk = 0; kk <= NNP_KMAX; ++kk) {
-                                        S = fmaf(W[q][lb][kk], pw[lb][kk], S);
-                                        D = fmaf(Wd[q][lb][kk], qw[lb][kk], D);
+                                        if (kk <= (lb == 0 ? KP : KN)) {
+                                            S = fmaf(W[q][lb][kk], pw[lb][kk], S);
+                                            D = fmaf(Wd[q][lb][kk], qw[lb][kk], D);
+                                        }
                                     }
                                 float Pd = 1.f, dPd = 0.f;
                                 if (NARROW) {
@@ -525,7 +514,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             const float cab = phic * ia * ib;
                             const float ca = phia * ia - phic * c * ia * ia;
                             const float cb = phib * ib - phic * c * ib * ib;
-                            const float cd = NARROW ? phid / rd : 0.f;
+                            const float cd = NARROW ? phid * ird : 0.f;
                             atomicAdd(&w.sg[3 * j + 0], ca * a.x + cab * b.x - cd * ex);
                             atomicAdd(&w.sg[3 * j + 1], ca * a.y + cab * b.y - cd * ey);
                             atomicAdd(&w.sg[3 * j + 2], ca * a.z + cab * b.z - cd * ez);

@@ -247,22 +247,40 @@ typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, floa
 typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
                             double*, int*);
 
-template <int NETA, bool NARROW>
+template <int NETA, bool NARROW, int KP, int KN>
 static void pick(SfKernel& s, ForceKernel& f)
 {
-    s = k_sf<NETA, NARROW>;
-    f = k_force<NETA, NARROW>;
+    s = k_sf<NETA, NARROW, KP, KN>;
+    f = k_force<NETA, NARROW, KP, KN>;
 }
 
+// Largest k (zeta = 2^k) used with lambda = +1 (l = 0) or -1 (l = 1), -1 if none.
+static int kmax_of(const Plan& P, int l)
+{
+    int km = -1;
+    for (int e = 0; e < P.n_elem; ++e)
+        for (int q = 0; q < NNP_MAXETA; ++q)
+            for (int k = 0; k <= NNP_KMAX; ++k)
+                if (P.e[e].ang_out[q][l][k] >= 0) km = std::max(km, k);
+    return km;
+}
+
+// Specialised instantiations for the term sets of the water-like (narrow, two
+// eta, lambda +1 up to zeta 16, lambda -1 up to zeta 4) and FCC-like (wide,
+// three eta, both lambda up to zeta 16) models; every other set runs the
+// generic instantiation with all powers up to zeta 16.
 static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
 {
     const bool nar = (P.ang_kind == NNP_SF_ANG_NARROW);
+    const int kp = kmax_of(P, 0), kn = kmax_of(P, 1);
+    if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f); return; }
+    if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f); return; }
     switch (P.n_eta_max) {
-    case 0: pick<0, false>(s, f); break;
-    case 1: if (nar) pick<1, true>(s, f); else pick<1, false>(s, f); break;
-    case 2: if (nar) pick<2, true>(s, f); else pick<2, false>(s, f); break;
-    case 3: if (nar) pick<3, true>(s, f); else pick<3, false>(s, f); break;
-    default: if (nar) pick<4, true>(s, f); else pick<4, false>(s, f); break;
+    case 0: pick<0, false, 4, 4>(s, f); break;
+    case 1: if (nar) pick<1, true, 4, 4>(s, f); else pick<1, false, 4, 4>(s, f); break;
+    case 2: if (nar) pick<2, true, 4, 4>(s, f); else pick<2, false, 4, 4>(s, f); break;
+    case 3: if (nar) pick<3, true, 4, 4>(s, f); else pick<3, false, 4, 4>(s, f); break;
+    default: if (nar) pick<4, true, 4, 4>(s, f); else pick<4, false, 4, 4>(s, f); break;
     }
 }
 
