@@ -211,7 +211,7 @@ __device__ __forceinline__ int enqueue_block(unsigned mask, int lane, unsigned s
 // KP / KN: largest k (zeta = 2^k) among the lambda = +1 / -1 functions; powers and
 // terms beyond them are compiled out.
 template <int NETA, bool NARROW, int KP, int KN>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128, 6)
 k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g,
      int C, float* __restrict__ Gs, float* __restrict__ Graw, int* __restrict__ flags,
      unsigned long long* __restrict__ counters)
@@ -386,7 +386,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
 // g[i, slot] = dE_i/dd_ij for each list slot (0 outside the cutoff), Fown[i] =
 // sum_j g_ij (the force on i from its own energy), per-warp virial partials.
 template <int NETA, bool NARROW, int KP, int KN>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128, 5)
 k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
         double* __restrict__ vir_part, int* __restrict__ flags)
@@ -428,8 +428,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
                                                   n_list);
         if (NETA > 0) {
-            // dense weights W[q][l][k] = dE/dG_o * 2^(1-zeta); Wd = W * lambda * zeta
-            float W[NETA > 0 ? NETA : 1][2][NNP_KMAX + 1], Wd[NETA > 0 ? NETA : 1][2][NNP_KMAX + 1];
+            // dense weights W[q][l][k] = dE/dG_o * 2^(1-zeta), zeta = 2^k
+            float W[NETA > 0 ? NETA : 1][2][NNP_KMAX + 1];
 #pragma unroll
             for (int q = 0; q < (NETA > 0 ? NETA : 1); ++q)
 #pragma unroll
@@ -437,9 +437,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
 #pragma unroll
                     for (int kk = 0; kk <= NNP_KMAX; ++kk) {
                         const int o = (q < E.n_eta) ? E.ang_out[q][l][kk] : -1;
-                        const float wt = (o >= 0) ? sW[o] * exp2f((float)(1 - (1 << kk))) : 0.f;
-                        W[q][l][kk] = wt;
-                        Wd[q][l][kk] = wt * (l == 0 ? 1.f : -1.f) * (float)(1 << kk);
+                        W[q][l][kk] = (o >= 0) ? sW[o] * exp2f((float)(1 - (1 << kk))) : 0.f;
                     }
             const int nb = (M + 31) >> 5;
             for (int A = 0; A < nb; ++A) {
@@ -468,18 +466,21 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                 rd = rd2 * ird;
                                 cutoff_fn_fast(rd, P.hpi_rc, fcd, dfcd);
                             }
-                            // p[l][k] = b_l^(2^k), qw[l][k] = b_l^(2^k - 1), b_l = 1 +- c
-                            float pw[2][NNP_KMAX + 1], qw[2][NNP_KMAX + 1];
+                            // pw[l][k] = b_l^(2^k); qs[l][k] = lambda_l 2^k b_l^(2^k - 1) = d pw / dc,
+                            // b_l = 1 + lambda_l c (shared by every eta)
+                            float pw[2][NNP_KMAX + 1], qs[2][NNP_KMAX + 1];
 #pragma unroll
                             for (int lb = 0; lb < 2; ++lb) {
                                 const float bl = (lb == 0) ? 1.f + c : 1.f - c;
-                                qw[lb][0] = 1.f;
+                                float qk = 1.f;
                                 pw[lb][0] = bl;
+                                qs[lb][0] = (lb == 0) ? 1.f : -1.f;
 #pragma unroll
                                 for (int kk = 1; kk <= NNP_KMAX; ++kk) {
                                     if (kk <= (lb == 0 ? KP : KN)) {
-                                        qw[lb][kk] = qw[lb][kk - 1] * pw[lb][kk - 1];
+                                        qk = qk * pw[lb][kk - 1];
                                         pw[lb][kk] = pw[lb][kk - 1] * pw[lb][kk - 1];
+                                        qs[lb][kk] = qk * ((lb == 0 ? 1.f : -1.f) * (float)(1 << kk));
                                     }
                                 }
                             }
@@ -493,7 +494,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                     for (int kk = 0; kk <= NNP_KMAX; ++kk) {
                                         if (kk <= (lb == 0 ? KP : KN)) {
                                             S = fmaf(W[q][lb][kk], pw[lb][kk], S);
-                                            D = fmaf(Wd[q][lb][kk], qw[lb][kk], D);
+                                            D = fmaf(W[q][lb][kk], qs[lb][kk], D);
                                         }
                                     }
                                 float Pd = 1.f, dPd = 0.f;

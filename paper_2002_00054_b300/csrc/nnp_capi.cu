@@ -672,8 +672,9 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     pick_kernels(P, ksf, kf);
     // warps per block limited by shared memory
     const size_t ps = sf_smem_per_warp(h->cap_rc), pf = force_smem_per_warp(h->cap_rc, h->stride);
-    h->wpb_sf = (int)std::min<size_t>(8, (size_t)max_smem / ps);
-    h->wpb_force = (int)std::min<size_t>(8, (size_t)max_smem / pf);
+    // 4-warp blocks (the kernels' launch bounds): finer granularity for occupancy
+    h->wpb_sf = (int)std::min<size_t>(4, (size_t)max_smem / ps);
+    h->wpb_force = (int)std::min<size_t>(4, (size_t)max_smem / pf);
     if (h->wpb_sf < 1 || h->wpb_force < 1) {
         set_err(h, NNP_EINVAL, "max_neighbors = %d needs more shared memory than one block has", h->stride);
         return fail(NNP_EINVAL);
