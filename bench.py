@@ -182,6 +182,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water_2m", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-network leg")
     ap.add_argument("--e2e-steps", type=int, default=5)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -305,6 +306,33 @@ def main():
            "work": {"list_entries": units[0], "cutoff_entries": units[1], "pairs": units[2], "triplets": units[3],
                     "rebuilds_total": st["rebuilds"]},
            "nve_drift_ev_per_atom": drift}
+    # ---- precision form: the same steps with the BF16 tensor-core network
+    if not args.no_bf16:
+        bf = NNP(model, device=local, max_neighbors=max_nb, precision="bf16")
+        pos_b = torch.from_numpy(pos_h).to(dev)
+        vel_b = torch.from_numpy(vel_h).to(dev)
+        bf.step(pos_b, vel_b, types, box, DT_FS, args.warmup)
+        bf.profile(True)
+        barrier()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        bf.step(pos_b, vel_b, types, box, DT_FS, args.steps)
+        b1.record(stream)
+        barrier()
+        bms = b0.elapsed_time(b1)
+        bk = bf.kernel_times()
+        # force error of the BF16 network against the FP32 path on the whole system
+        p0 = torch.from_numpy(pos_h).to(dev)
+        f32_out = nnp.compute(p0, types, box)
+        b16_out = bf.compute(p0, types, box)
+        dF = (b16_out["F"] - f32_out["F"]).double()
+        out["bf16_mlp"] = {
+            "value": n * args.steps * world / (bms * 1e-3), "unit": UNIT, "ms_per_step": bms / args.steps,
+            "network_ms_per_step": bk["network"][0] / max(1, bk["network"][1]),
+            "force_rms_err_vs_fp32_ev_per_A": float(dF.pow(2).mean().sqrt().item()),
+            "force_max_err_vs_fp32_ev_per_A": float(dF.abs().max().item()),
+            "energy_err_vs_fp32_ev_per_atom": float(abs(b16_out["energy"].item() - f32_out["energy"].item()) / n)}
+        bf.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model["name"])
     if rank == 0:

@@ -60,7 +60,8 @@ enum nnp_status {
 enum nnp_sf_type { NNP_SF_RADIAL = 2, NNP_SF_ANG_NARROW = 3, NNP_SF_ANG_WIDE = 4 };
 
 /* Network precision: FP32 everywhere, or BF16 operands with FP32 accumulation
- * for the network layers (descriptors and forces stay FP32). */
+ * for the network layers on the tensor cores (descriptors and forces stay FP32;
+ * NNP_BF16 needs two hidden layers, n_layers = 3). */
 enum nnp_precision { NNP_FP32 = 0, NNP_BF16 = 1 };
 
 typedef struct {
@@ -205,6 +206,7 @@ NNP_API int nnp_kernel_times(nnp_handle* h, int max_groups, double* total_ms, lo
  * and the scratch the call needs (about n_atoms * max_neighbors * 24 bytes)
  * must fit the array; otherwise NNP_EINVAL with a message naming the limit.
  * Neighbours are found by brute force over periodic images on every call.
+ * The handle's network must be NNP_FP32 (NNP_EUNSUPPORTED otherwise).
  *
  * The first call on a device looks up the array's device address (a runtime
  * call, made once per device with that device current); make that first call

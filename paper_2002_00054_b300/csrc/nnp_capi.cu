@@ -18,6 +18,7 @@
 #include "k_descriptors.cuh"
 #include "k_md.cuh"
 #include "k_mlp.cuh"
+#include "k_mlp_tc.cuh"
 #include "k_neighbors.cuh"
 
 namespace {
@@ -89,6 +90,13 @@ struct nnp_handle {
     double prof_ms[8] = {0};
     long long prof_n[8] = {0};
     long long launches = 0;   // kernels launched by the current / last call
+
+    // BF16 tensor-core network: shapes, per-element atom lists
+    TcShape tcs{0, 0, 0};
+    size_t smem_tc = 0;
+    int* elem_idx = nullptr;
+    int* elem_part = nullptr;
+    int* elem_off = nullptr;   // [NNP_MAXE + 1] atoms, then [NNP_MAXE + 1] tiles
 
     // launch configuration
     int num_sms = 148;
@@ -288,6 +296,8 @@ static size_t sf_smem_per_warp(int cap) { return sf_warp_bytes(cap); }
 static size_t force_smem_per_warp(int cap, int stride) { return force_warp_bytes(cap, stride); }
 
 // ------------------------------------------------------------------ scratch
+static int blocks_for(int n, int t) { return (n + t - 1) / t; }
+
 template <typename T>
 static cudaError_t regrow(T*& p, size_t count)
 {
@@ -317,6 +327,10 @@ static int ensure_atoms(nnp_handle* h, int n)
     CK(h, regrow(h->cell_atoms, cap));
     CK(h, regrow(h->pos_cache, (size_t)cap * 3));
     CK(h, regrow(h->types_cache, cap));
+    if (h->precision == NNP_BF16) {
+        CK(h, regrow(h->elem_idx, cap));
+        CK(h, regrow(h->elem_part, (size_t)blocks_for(cap, 256) * NNP_MAXE));
+    }
     h->cap_n = cap;
     h->list_valid = false;
     h->step_valid = false;
@@ -449,7 +463,6 @@ static int read_status(nnp_handle* h, cudaStream_t st)
     return NNP_OK;
 }
 
-static int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
 // Neighbour maintenance + descriptors + network + forces for one system.
 // Outputs (device, each nullable): energy[1], Ei_out[n], F_out[n*3], vir_out[9], G_out, dEdG_out [n][n_G].
@@ -533,7 +546,17 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
                                                      h->counters);
     }
     if (stop_after == 1 && !dEdG_out) return read_status(h, st);
-    {
+    if (h->precision == NNP_BF16) {
+        KScope ks(h, KG_MLP, st, 4);
+        const int nblk = blocks_for(n, 256);
+        int* toff = h->elem_off + NNP_MAXE + 1;
+        k_elem_count<<<nblk, 256, 0, st>>>(n, h->pos4, P.n_elem, h->elem_part);
+        k_elem_scan<<<1, 1024, 0, st>>>(nblk, P.n_elem, h->elem_part, h->elem_off, toff);
+        k_elem_fill<<<nblk, 256, 0, st>>>(n, h->pos4, P.n_elem, h->elem_part, h->elem_idx);
+        const int gtc = std::min(blocks_for(n, TC_TILE) + P.n_elem, 2 * h->num_sms);
+        k_mlp_tc<<<gtc, 128, h->smem_tc, st>>>(n, h->d_plan, h->d_w, h->tcs, h->elem_idx, h->elem_off, toff, h->G,
+                                                h->Ei, h->dEdG, h->flags);
+    } else {
         KScope ks(h, KG_MLP, st);
         const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
         k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, h->pos4, h->d_plan, h->d_w, h->G, h->Ei, h->dEdG);
@@ -616,8 +639,9 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     std::string why;
     int rc = build_plan(params, P, n_params, why);
     if (rc) return set_err(nullptr, rc, "%s", why.c_str());
-    if (params->mlp_precision == NNP_BF16)
-        return set_err(nullptr, NNP_EUNSUPPORTED, "the BF16 network path is not built in this library version");
+    if (params->mlp_precision == NNP_BF16 && (params->n_layers != 3 || params->widths[0] > 64))
+        return set_err(nullptr, NNP_EUNSUPPORTED,
+                       "the BF16 tensor-core network takes two hidden layers (n_layers = 3) and n_G <= 64");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
         return set_err(nullptr, NNP_ECUDA, "CUDA device %d not available", device);
@@ -664,6 +688,7 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     CKC(cudaMemset(h->counters, 0, sizeof(unsigned long long) * CNT_N));
     CKC(cudaMalloc((void**)&h->sys_box, sizeof(float4) * 4));
     CKC(cudaMalloc((void**)&h->d_energy, sizeof(double) * 4));
+    CKC(cudaMalloc((void**)&h->elem_off, sizeof(int) * 2 * (NNP_MAXE + 1)));
     CKC(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device));
     int max_smem = 0;
     CKC(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
@@ -691,6 +716,23 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     CKC(cudaFuncSetAttribute((const void*)ksf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     CKC(cudaFuncSetAttribute((const void*)kf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     CKC(cudaFuncSetAttribute((const void*)k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    if (h->precision == NNP_BF16) {
+        auto r16 = [](int x) { return (x + 15) & ~15; };
+        h->tcs = TcShape{r16(P.width[0]), r16(P.width[1]), r16(P.width[2])};
+        h->smem_tc = (size_t)((P.n_elem * tc_elem_bytes(h->tcs) + 1023) & ~1023) + tc_tile_bytes(h->tcs);
+        if (h->smem_tc > (size_t)max_smem) {
+            set_err(h, NNP_EUNSUPPORTED, "BF16 network weights do not fit in shared memory");
+            return fail(NNP_EUNSUPPORTED);
+        }
+        cudaFuncAttributes fa;
+        CKC(cudaFuncGetAttributes(&fa, (const void*)k_mlp_tc));   // its static mbarrier counts against the limit
+        if (h->smem_tc + fa.sharedSizeBytes > (size_t)max_smem) {
+            set_err(h, NNP_EUNSUPPORTED, "BF16 network weights do not fit in shared memory");
+            return fail(NNP_EUNSUPPORTED);
+        }
+        CKC(cudaFuncSetAttribute((const void*)k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem - (int)fa.sharedSizeBytes));
+    }
     int bs = 0;
     CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)ksf, 32 * h->wpb_sf, h->smem_sf));
     h->grid_sf = std::max(1, bs) * h->num_sms;
@@ -708,7 +750,7 @@ int nnp_destroy(nnp_handle* h)
     if (!h) return NNP_OK;
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
-    void* dev[] = {h->d_plan, h->d_w, h->off, h->ref, h->pos4, h->Fown, h->G, h->dEdG, h->Ei, h->F, h->nbr,
+    void* dev[] = {h->elem_idx, h->elem_part, h->elem_off, h->d_plan, h->d_w, h->off, h->ref, h->pos4, h->Fown, h->G, h->dEdG, h->Ei, h->F, h->nbr,
                    h->ncount, h->rev, h->cell_of, h->cell_atoms, h->gbuf, h->cell_count, h->cell_start, h->cursor,
                    h->epart, h->vpart, h->d_energy, h->d_log, h->flags, h->counters, h->sys_box};
     for (void* p : dev)
@@ -978,6 +1020,8 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
         nim = std::max(nim, (int)std::ceil(rcut / box[a]));
     }
     if (h->device < 0 || h->device >= kMaxDevices) return static_fail(eb, el, NNP_ECUDA, "device index out of range");
+    if (h->precision != NNP_FP32)
+        return static_fail(eb, el, NNP_EUNSUPPORTED, "nnp_compute_static evaluates FP32 networks only");
     const Plan& P = h->plan;
     const int S = h->stride, T = 256;
     const int gf = std::min(blocks_for(std::max(n, 1), h->wpb_force), h->grid_force);

@@ -121,3 +121,9 @@ def test_create_without_device_fails_cleanly(lib):
         pytest.skip("a GPU is present")
     rc, h, msg = _create(lib, _P(workloads.water_model()))
     assert rc == _capi.NNP_ECUDA and not h.value
+
+
+def test_create_rejects_bf16_network_shape(lib):
+    m = workloads.water_model(hidden=(25,))
+    rc, h, msg = _create(lib, _P(m, mlp_precision=_capi.NNP_BF16))
+    assert rc == _capi.NNP_EUNSUPPORTED and "n_layers = 3" in msg
