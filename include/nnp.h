@@ -162,6 +162,31 @@ NNP_API int nnp_descriptors(nnp_handle* h, int n_atoms, const float* pos, const 
 NNP_API int nnp_step(nnp_handle* h, int n_atoms, float* pos, float* vel, const int* types, const double* box,
              double dt_fs, int n_steps, double* pe_ke_log, void* stream);
 
+/* ----------------------------------------------------- batches and training */
+/* A batch of n_systems independent periodic systems (e.g. a training batch of
+ * configurations of different sizes): system b holds atoms sys_start[b] ..
+ * sys_start[b+1]-1 (host int [n_systems + 1], sys_start[0] = 0) in the box
+ * boxes[3b .. 3b+2] (host double).  Every box edge must be >= (cutoff + skin)/2;
+ * neighbours include every periodic image within the cutoff.
+ *
+ * nnp_compute_batch: energies (device double [n_systems], FP64 sums), per-atom
+ * energies and forces (device, nullable) of every system; Fig. 1b steps 1-3. */
+NNP_API int nnp_compute_batch(nnp_handle* h, int n_systems, const int* sys_start, const double* boxes,
+                              const float* pos, const int* types, double* energies, float* atom_energy,
+                              float* forces, void* stream);
+
+/* Gradient of a loss with respect to the network parameters (force-matching
+ * training; the paper fits these parameters by least squares, Sec. 2):
+ *   grad = sum_b dLdE[b] dE_b/dtheta + sum_m dLdF[m] . dF_m/dtheta
+ * dLdE: device double [n_systems] (nullable); dLdF: device float [n_atoms][3]
+ * (nullable); grad: device float [nnp_num_params(h)] in the packed weight layout,
+ * overwritten.  The force term is the double backward: because F = -dE/dr it
+ * equals -d/dtheta sum_i dE_i/dG_i . t_i with t_i = sum_j dG_i/dd_ij . (u_j - u_i),
+ * u = dLdF; dG/dr is recomputed, not stored.  Needs two hidden layers. */
+NNP_API int nnp_param_grad(nnp_handle* h, int n_systems, const int* sys_start, const double* boxes,
+                           const float* pos, const int* types, const double* dLdE, const float* dLdF,
+                           float* grad, void* stream);
+
 /* Work counters summed over the last nnp_compute / nnp_descriptors / nnp_step
  * call (rebuilds: since creation).  Synchronises the handle's device. */
 typedef struct {

@@ -59,6 +59,8 @@ SIGNATURES = {
     "nnp_kernel_group_name": (ctypes.c_char_p, [I]),
     "nnp_kernel_times": (I, [V, I, c_double_p, ctypes.POINTER(ctypes.c_longlong)]),
     "nnp_compute_static": (I, [V, I, V, V, c_double_p, V, V, V, ctypes.c_char_p, I, V]),
+    "nnp_compute_batch": (I, [V, I, c_int_p, c_double_p, V, V, V, V, V, V]),
+    "nnp_param_grad": (I, [V, I, c_int_p, c_double_p, V, V, V, V, V, V]),
 }
 
 _lib = None

@@ -32,7 +32,20 @@ struct NbView {
     const uint32_t* nbr;
     const int* ncount;
     int stride;
+    const int* sys_of = nullptr;      // batches: system of each atom (nullptr: one system)
+    const float4* sys_box = nullptr;  // batches: box edges of each system
 };
+
+// box edges seen by atom i
+__device__ __forceinline__ void atom_box(const NbView& nv, const Box& bx, int i, float& Lx, float& Ly, float& Lz)
+{
+    if (nv.sys_of) {
+        const float4 b = nv.sys_box[nv.sys_of[i]];
+        Lx = b.x; Ly = b.y; Lz = b.z;
+    } else {
+        Lx = bx.L[0]; Ly = bx.L[1]; Lz = bx.L[2];
+    }
+}
 
 #define PAIR_QUEUE 1024   // live pairs of one 32 x 32 block, as (l | s << 5)
 
@@ -68,6 +81,8 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
     const int cnt = nv.ncount[i];
     n_list = cnt;
     const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
+    float Lx, Ly, Lz;
+    atom_box(nv, bx, i, Lx, Ly, Lz);
     int M = 0;
     for (int base = 0; base < cnt; base += 32) {
         const int s = base + lane;
@@ -78,7 +93,7 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
             const uint32_t e = row[s];
             const float4 pj = pos4[e & NB_INDEX_MASK];
             float ox, oy, oz;
-            nb_shift(e, bx.L[0], bx.L[1], bx.L[2], ox, oy, oz);
+            nb_shift(e, Lx, Ly, Lz, ox, oy, oz);
             dx = pair_disp(pj.x, pi.x, ox);
             dy = pair_disp(pj.y, pi.y, oy);
             dz = pair_disp(pj.z, pi.z, oz);

@@ -38,7 +38,8 @@ __global__ void k_check_disp(int n, const float* __restrict__ pos, const int* __
 __global__ void k_rebuild_pos(int n, const float* __restrict__ pos, const int* __restrict__ types, Box box,
                               int n_elem, float4* __restrict__ off, float4* __restrict__ pos4,
                               float4* __restrict__ ref, int* __restrict__ flags,
-                              unsigned long long* __restrict__ counters)
+                              unsigned long long* __restrict__ counters,
+                              const int* __restrict__ sys_of = nullptr, const float4* __restrict__ sys_box = nullptr)
 {
     if (!flags[FLAG_REBUILD]) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -53,6 +54,10 @@ __global__ void k_rebuild_pos(int n, const float* __restrict__ pos, const int* _
     if (t < 0 || t >= n_elem) {
         atomicOr(&flags[FLAG_ERR], ERR_NONFINITE);
         t = 0;
+    }
+    if (sys_of) {
+        const float4 b = sys_box[sys_of[i]];
+        box.L[0] = b.x; box.L[1] = b.y; box.L[2] = b.z;
     }
     float ox = floorf(x / box.L[0]) * box.L[0];
     float oy = floorf(y / box.L[1]) * box.L[1];

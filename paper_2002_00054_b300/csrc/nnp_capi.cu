@@ -20,6 +20,7 @@
 #include "k_mlp.cuh"
 #include "k_mlp_tc.cuh"
 #include "k_neighbors.cuh"
+#include "k_train.cuh"
 
 namespace {
 
@@ -90,6 +91,18 @@ struct nnp_handle {
     double prof_ms[8] = {0};
     long long prof_n[8] = {0};
     long long launches = 0;   // kernels launched by the current / last call
+
+    // batches of independent systems (training): layout of the cached list
+    int cap_sys = 0;
+    int* sys_of = nullptr;        // [cap_n]
+    int* sys_start_d = nullptr;   // [cap_sys + 1]
+    std::vector<int> bt_start;    // host copy of the last batch layout
+    std::vector<double> bt_boxes;
+    float* T = nullptr;           // descriptor tangents [cap_n][gs]
+    float* gpart = nullptr;       // per-warp parameter-gradient partials
+    size_t cap_gpart = 0;
+    size_t smem_tan = 0, smem_pg = 0;
+    int grid_tan = 0;
 
     // BF16 tensor-core network: shapes, per-element atom lists
     TcShape tcs{0, 0, 0};
@@ -255,11 +268,14 @@ typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, floa
 typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
                             double*, int*);
 
+typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*);
+
 template <int NETA, bool NARROW, int KP, int KN>
-static void pick(SfKernel& s, ForceKernel& f)
+static void pick(SfKernel& s, ForceKernel& f, TangentKernel& t)
 {
     s = k_sf<NETA, NARROW, KP, KN>;
     f = k_force<NETA, NARROW, KP, KN>;
+    t = k_tangent<NETA, NARROW, KP, KN>;
 }
 
 // Largest k (zeta = 2^k) used with lambda = +1 (l = 0) or -1 (l = 1), -1 if none.
@@ -277,19 +293,24 @@ static int kmax_of(const Plan& P, int l)
 // eta, lambda +1 up to zeta 16, lambda -1 up to zeta 4) and FCC-like (wide,
 // three eta, both lambda up to zeta 16) models; every other set runs the
 // generic instantiation with all powers up to zeta 16.
-static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
+static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t)
 {
     const bool nar = (P.ang_kind == NNP_SF_ANG_NARROW);
     const int kp = kmax_of(P, 0), kn = kmax_of(P, 1);
-    if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f); return; }
-    if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f); return; }
+    if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f, t); return; }
+    if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f, t); return; }
     switch (P.n_eta_max) {
-    case 0: pick<0, false, 4, 4>(s, f); break;
-    case 1: if (nar) pick<1, true, 4, 4>(s, f); else pick<1, false, 4, 4>(s, f); break;
-    case 2: if (nar) pick<2, true, 4, 4>(s, f); else pick<2, false, 4, 4>(s, f); break;
-    case 3: if (nar) pick<3, true, 4, 4>(s, f); else pick<3, false, 4, 4>(s, f); break;
-    default: if (nar) pick<4, true, 4, 4>(s, f); else pick<4, false, 4, 4>(s, f); break;
+    case 0: pick<0, false, 4, 4>(s, f, t); break;
+    case 1: if (nar) pick<1, true, 4, 4>(s, f, t); else pick<1, false, 4, 4>(s, f, t); break;
+    case 2: if (nar) pick<2, true, 4, 4>(s, f, t); else pick<2, false, 4, 4>(s, f, t); break;
+    case 3: if (nar) pick<3, true, 4, 4>(s, f, t); else pick<3, false, 4, 4>(s, f, t); break;
+    default: if (nar) pick<4, true, 4, 4>(s, f, t); else pick<4, false, 4, 4>(s, f, t); break;
     }
+}
+static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
+{
+    TangentKernel t;
+    pick_kernels(P, s, f, t);
 }
 
 static size_t sf_smem_per_warp(int cap) { return sf_warp_bytes(cap); }
@@ -327,10 +348,11 @@ static int ensure_atoms(nnp_handle* h, int n)
     CK(h, regrow(h->cell_atoms, cap));
     CK(h, regrow(h->pos_cache, (size_t)cap * 3));
     CK(h, regrow(h->types_cache, cap));
-    if (h->precision == NNP_BF16) {
-        CK(h, regrow(h->elem_idx, cap));
-        CK(h, regrow(h->elem_part, (size_t)blocks_for(cap, 256) * NNP_MAXE));
-    }
+    CK(h, regrow(h->elem_idx, cap));
+    CK(h, regrow(h->elem_part, (size_t)blocks_for(cap, 256) * NNP_MAXE));
+    CK(h, regrow(h->sys_of, cap));
+    CK(h, regrow(h->T, (size_t)cap * h->plan.gs));
+    h->bt_start.clear();
     h->cap_n = cap;
     h->list_valid = false;
     h->step_valid = false;
@@ -467,9 +489,25 @@ static int read_status(nnp_handle* h, cudaStream_t st)
 // Neighbour maintenance + descriptors + network + forces for one system.
 // Outputs (device, each nullable): energy[1], Ei_out[n], F_out[n*3], vir_out[9], G_out, dEdG_out [n][n_G].
 // stop_after: 0 full, 1 after descriptors, 2 after network.
+// A batch of B independent periodic systems: atoms start[b] .. start[b+1]-1 in box b.
+struct Batch {
+    int B;
+    const int* start;     // host [B + 1], start[0] = 0, start[B] = n
+    const double* boxes;  // host [3 B]
+};
+
+static int ensure_sys(nnp_handle* h, int B)
+{
+    if (B <= h->cap_sys) return NNP_OK;
+    CK(h, regrow(h->sys_box, B));
+    CK(h, regrow(h->sys_start_d, B + 1));
+    h->cap_sys = B;
+    return NNP_OK;
+}
+
 static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, const double* box, cudaStream_t st,
                     double* energy, float* Ei_out, float* F_out, double* vir_out, float* G_out, float* dEdG_out,
-                    int stop_after)
+                    int stop_after, const Batch* bt = nullptr)
 {
     int rc = ensure_atoms(h, n);
     if (rc) return rc;
@@ -477,24 +515,54 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     const double rcut = h->cutoff + h->skin;
     // path and rebuild decision
     bool same_box = h->list_valid && h->list_n == n;
-    for (int a = 0; a < 3; ++a) same_box = same_box && (h->list_box[a] == box[a]);
-    int nc[3];
+    int nc[3] = {0, 0, 0};
     bool cell = true;
-    for (int a = 0; a < 3; ++a) {
-        nc[a] = (int)std::floor(box[a] / rcut);
-        if (nc[a] < 3) cell = false;
-    }
     int nim = 0;
-    for (int a = 0; a < 3; ++a) nim = std::max(nim, (int)std::ceil(rcut / box[a]));
-    if (!cell && nim > 2) return set_err(h, NNP_EBOX, "box too small for the image range");
     Box bx;
-    for (int a = 0; a < 3; ++a) bx.L[a] = (float)box[a];
+    if (!bt) {
+        same_box = same_box && h->bt_start.empty();
+        for (int a = 0; a < 3; ++a) same_box = same_box && (h->list_box[a] == box[a]);
+        for (int a = 0; a < 3; ++a) {
+            nc[a] = (int)std::floor(box[a] / rcut);
+            if (nc[a] < 3) cell = false;
+        }
+        for (int a = 0; a < 3; ++a) nim = std::max(nim, (int)std::ceil(rcut / box[a]));
+        if (!cell && nim > 2) return set_err(h, NNP_EBOX, "box too small for the image range");
+        for (int a = 0; a < 3; ++a) bx.L[a] = (float)box[a];
+    } else {
+        cell = false;
+        same_box = same_box && (int)h->bt_start.size() == bt->B + 1 &&
+                   std::equal(bt->start, bt->start + bt->B + 1, h->bt_start.begin()) &&
+                   std::equal(bt->boxes, bt->boxes + 3 * bt->B, h->bt_boxes.begin());
+        for (int a = 0; a < 3; ++a) bx.L[a] = (float)bt->boxes[a];
+    }
     const int T = 256;
     CK(h, cudaMemsetAsync(h->flags + FLAG_ERR, 0, sizeof(int), st));
     const int rows_grid = std::min(blocks_for(n, 8), h->num_sms * 8);
     {
         KScope ks(h, KG_NEIGH, st, 0);
-        if (!same_box) {
+        if (!same_box && bt) {
+            rc = ensure_sys(h, bt->B);
+            if (rc) return rc;
+            std::vector<float4> sb(bt->B);
+            std::vector<int> so(n);
+            for (int b = 0; b < bt->B; ++b) {
+                int nimb = 0;
+                for (int a = 0; a < 3; ++a) nimb = std::max(nimb, (int)std::ceil(rcut / bt->boxes[3 * b + a]));
+                sb[b] = make_float4((float)bt->boxes[3 * b], (float)bt->boxes[3 * b + 1], (float)bt->boxes[3 * b + 2],
+                                    (float)nimb);
+                for (int i = bt->start[b]; i < bt->start[b + 1]; ++i) so[i] = b;
+            }
+            CK(h, cudaMemcpyAsync(h->sys_box, sb.data(), sizeof(float4) * bt->B, cudaMemcpyHostToDevice, st));
+            CK(h, cudaMemcpyAsync(h->sys_start_d, bt->start, sizeof(int) * (bt->B + 1), cudaMemcpyHostToDevice, st));
+            CK(h, cudaMemcpyAsync(h->sys_of, so.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+            CK(h, cudaStreamSynchronize(st));   // the host vectors above are pageable staging
+            h->bt_start.assign(bt->start, bt->start + bt->B + 1);
+            h->bt_boxes.assign(bt->boxes, bt->boxes + 3 * bt->B);
+            h->cell_path = false;
+            CK(h, cudaMemsetAsync(h->flags + FLAG_REBUILD, 1, sizeof(int), st));
+        } else if (!same_box) {
+            h->bt_start.clear();
             CK(h, cudaMemsetAsync(h->flags + FLAG_REBUILD, 1, sizeof(int), st));   // any non-zero value
             h->cell_path = cell;
             for (int a = 0; a < 3; ++a) h->nc[a] = nc[a];
@@ -507,7 +575,8 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
             h->launches++;
         }
         k_rebuild_pos<<<blocks_for(n, T), T, 0, st>>>(n, pos, types, bx, P.n_elem, h->off, h->pos4, h->ref, h->flags,
-                                                      h->counters);
+                                                      h->counters, bt ? h->sys_of : nullptr,
+                                                      bt ? h->sys_box : nullptr);
         h->launches++;
         if (h->cell_path) {
             const int ncell = h->nc[0] * h->nc[1] * h->nc[2];
@@ -524,8 +593,8 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
                                                    h->cell_atoms, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
             h->launches += 5;
         } else {
-            k_rows_brute<<<rows_grid, 256, 0, st>>>(n, h->pos4, nullptr, nullptr, h->sys_box, P.rcut2, h->stride,
-                                                    h->nbr, h->ncount, h->flags);
+            k_rows_brute<<<rows_grid, 256, 0, st>>>(n, h->pos4, bt ? h->sys_of : nullptr, bt ? h->sys_start_d : nullptr,
+                                                    h->sys_box, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
             h->launches++;
         }
         k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
@@ -536,6 +605,10 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     for (int a = 0; a < 3; ++a) h->list_box[a] = box[a];
 
     NbView nv{h->nbr, h->ncount, h->stride};
+    if (bt) {
+        nv.sys_of = h->sys_of;
+        nv.sys_box = h->sys_box;
+    }
     SfKernel ksf;
     ForceKernel kf;
     pick_kernels(P, ksf, kf);
@@ -578,7 +651,10 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         KScope ks(h, KG_GATHER, st);
         k_gather<<<rows_grid, 256, 0, st>>>(n, nv, h->rev, h->gbuf, h->Fown, F_out ? F_out : h->F, h->flags);
     }
-    {
+    if (bt) {
+        KScope ks(h, KG_REDUCE, st);
+        if (energy) k_sys_energy<<<bt->B, 256, 0, st>>>(h->sys_start_d, h->Ei, energy, h->flags);
+    } else {
         KScope ks(h, KG_REDUCE, st, 2);
         k_sum_partial<<<gred, T, 0, st>>>(n, h->Ei, h->epart, h->flags);
         k_finalize<<<1, 256, 0, st>>>(gred, h->epart, energy ? energy : h->d_energy, nvp, h->vpart, vir_out);
@@ -733,6 +809,23 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
         CKC(cudaFuncSetAttribute((const void*)k_mlp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  max_smem - (int)fa.sharedSizeBytes));
     }
+    {
+        SfKernel s2;
+        ForceKernel f2;
+        TangentKernel kt;
+        pick_kernels(P, s2, f2, kt);
+        h->smem_tan = tangent_warp_bytes(h->cap_rc) * 4;
+        h->smem_pg = sizeof(float) * (size_t)P.s_elem * (P.n_elem + 4);
+        if (h->smem_tan <= (size_t)max_smem && h->smem_pg <= (size_t)max_smem && P.n_layers == 3) {
+            CKC(cudaFuncSetAttribute((const void*)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+            CKC(cudaFuncSetAttribute((const void*)k_param_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+            int bt = 0;
+            CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, (const void*)kt, 128, h->smem_tan));
+            h->grid_tan = std::max(1, bt) * h->num_sms;
+        } else {
+            h->smem_pg = 0;   // gradients unavailable for this model (reported by nnp_param_grad)
+        }
+    }
     int bs = 0;
     CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)ksf, 32 * h->wpb_sf, h->smem_sf));
     h->grid_sf = std::max(1, bs) * h->num_sms;
@@ -755,6 +848,8 @@ int nnp_destroy(nnp_handle* h)
                    h->epart, h->vpart, h->d_energy, h->d_log, h->flags, h->counters, h->sys_box};
     for (void* p : dev)
         if (p) cudaFree(p);
+    for (void* p2 : {(void*)h->sys_of, (void*)h->sys_start_d, (void*)h->T, (void*)h->gpart})
+        if (p2) cudaFree(p2);
     if (h->pos_cache) cudaFree(h->pos_cache);
     if (h->types_cache) cudaFree(h->types_cache);
     for (auto& p : h->pending) {
@@ -907,6 +1002,109 @@ int nnp_step(nnp_handle* h, int n, float* pos, float* vel, const int* types, con
     h->step_types = types;
     for (int a = 0; a < 3; ++a) h->step_box[a] = box[a];
     return NNP_OK;
+}
+
+static int batch_args(nnp_handle* h, int B, const int* start, const double* boxes, const float* pos, const int* types,
+                      int& n)
+{
+    if (B < 1 || !start || !boxes) return set_err(h, NNP_EINVAL, "n_systems must be >= 1 with start and boxes");
+    if (start[0] != 0) return set_err(h, NNP_EINVAL, "sys_start[0] must be 0");
+    for (int b = 0; b < B; ++b) {
+        if (start[b + 1] < start[b]) return set_err(h, NNP_EINVAL, "sys_start must be non-decreasing");
+        int rc = check_box(h, boxes + 3 * b);
+        if (rc) return rc;
+        for (int a = 0; a < 3; ++a)
+            if ((int)std::ceil((h->cutoff + h->skin) / boxes[3 * b + a]) > 2)
+                return set_err(h, NNP_EBOX, "box of system %d too small for the image range", b);
+    }
+    n = start[B];
+    if (n > (int)NB_INDEX_MASK) return set_err(h, NNP_EINVAL, "n_atoms must be < 2^24");
+    if (n > 0 && (!pos || !types)) return set_err(h, NNP_EINVAL, "pos and types must not be NULL");
+    return NNP_OK;
+}
+
+int nnp_compute_batch(nnp_handle* h, int B, const int* start, const double* boxes, const float* pos,
+                      const int* types, double* energies, float* atom_energy, float* forces, void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    h->err.clear();
+    int n = 0;
+    int rc = batch_args(h, B, start, boxes, pos, types, n);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    h->step_valid = false;
+    if (n == 0) {
+        if (energies) CK(h, cudaMemsetAsync(energies, 0, sizeof(double) * B, st));
+        CK(h, cudaStreamSynchronize(st));
+        return NNP_OK;
+    }
+    rc = begin_call(h, st);
+    if (rc) return rc;
+    Batch bt{B, start, boxes};
+    rc = run_eval(h, n, pos, types, boxes, st, energies, atom_energy, forces, nullptr, nullptr, nullptr, 0, &bt);
+    if (rc) return rc;
+    return read_status(h, st);
+}
+
+int nnp_param_grad(nnp_handle* h, int B, const int* start, const double* boxes, const float* pos,
+                   const int* types, const double* dLdE, const float* dLdF, float* grad, void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    h->err.clear();
+    if (!grad) return set_err(h, NNP_EINVAL, "grad must not be NULL");
+    if (h->smem_pg == 0)
+        return set_err(h, NNP_EUNSUPPORTED, "parameter gradients need two hidden layers (n_layers = 3)");
+    int n = 0;
+    int rc = batch_args(h, B, start, boxes, pos, types, n);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    h->step_valid = false;
+    CK(h, cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)h->n_params, st));
+    if (n == 0 || (!dLdE && !dLdF)) {
+        CK(h, cudaStreamSynchronize(st));
+        return NNP_OK;
+    }
+    rc = begin_call(h, st);
+    if (rc) return rc;
+    Batch bt{B, start, boxes};
+    // descriptors G~ of the current positions (stop after the descriptor pass)
+    rc = run_eval(h, n, pos, types, boxes, st, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, &bt);
+    if (rc) return rc;
+    const Plan& P = h->plan;
+    Box bx;
+    for (int a = 0; a < 3; ++a) bx.L[a] = (float)boxes[a];
+    if (dLdF) {
+        SfKernel ksf;
+        ForceKernel kf;
+        TangentKernel kt;
+        pick_kernels(P, ksf, kf, kt);
+        NbView nv{h->nbr, h->ncount, h->stride, h->sys_of, h->sys_box};
+        KScope ks(h, KG_FORCE, st);
+        kt<<<std::min(blocks_for(n, 4), h->grid_tan), 128, h->smem_tan, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc,
+                                                                            dLdF, h->T, h->flags);
+    }
+    const int gpg = std::min(blocks_for(n, 4), 2 * h->num_sms);
+    const int nwarps = gpg * 4;
+    const size_t need = (size_t)nwarps * P.n_elem * P.n_params_elem;
+    if (need > h->cap_gpart) {
+        CK(h, regrow(h->gpart, need));
+        h->cap_gpart = need;
+    }
+    {
+        KScope ks(h, KG_MLP, st, 6);
+        const int nblk = blocks_for(n, 256);
+        int* toff = h->elem_off + NNP_MAXE + 1;
+        k_elem_count<<<nblk, 256, 0, st>>>(n, h->pos4, P.n_elem, h->elem_part);
+        k_elem_scan<<<1, 1024, 0, st>>>(nblk, P.n_elem, h->elem_part, h->elem_off, toff);
+        k_elem_fill<<<nblk, 256, 0, st>>>(n, h->pos4, P.n_elem, h->elem_part, h->elem_idx);
+        CK(h, cudaMemsetAsync(h->gpart, 0, sizeof(float) * need, st));
+        k_param_grad<<<gpg, 128, h->smem_pg, st>>>(n, h->d_plan, h->d_w, h->pos4, h->elem_idx, h->sys_of, dLdE, h->G,
+                                                   dLdF ? h->T : nullptr, h->gpart);
+        k_grad_reduce<<<blocks_for(h->n_params, 256), 256, 0, st>>>(nwarps, P.n_elem, P.n_params_elem, h->gpart, grad);
+    }
+    return read_status(h, st);
 }
 
 int nnp_profile(nnp_handle* h, int enable)

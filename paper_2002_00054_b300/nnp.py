@@ -153,6 +153,46 @@ class NNP:
                                        _ptr(lg), _stream(stream)))
         return lg
 
+    # --------------------------------------------------------------- batches
+    @staticmethod
+    def _layout(starts, boxes):
+        st = np.ascontiguousarray(np.asarray(starts, np.int32).reshape(-1))
+        bx = np.ascontiguousarray(np.asarray(boxes, np.float64).reshape(-1, 3))
+        if st.size != bx.shape[0] + 1:
+            raise ValueError("starts must have n_systems + 1 entries")
+        return st, bx
+
+    def compute_batch(self, pos, types, starts, boxes, forces=True, atom_energy=False, stream=None):
+        """Energies [B] (fp64), forces and per-atom energies of a batch of systems."""
+        st, bx = self._layout(starts, boxes)
+        n = int(st[-1])
+        _need(pos, torch.float32, (n, 3), "pos", self.device)
+        _need(types, torch.int32, (n,), "types", self.device)
+        dev = pos.device
+        out = {"energy": torch.empty(len(bx), dtype=torch.float64, device=dev),
+               "F": torch.empty((n, 3), dtype=torch.float32, device=dev) if forces else None,
+               "Ei": torch.empty(n, dtype=torch.float32, device=dev) if atom_energy else None}
+        self._check(self._lib.nnp_compute_batch(
+            self.h, len(bx), st.ctypes.data_as(_capi.c_int_p), bx.ctypes.data_as(_capi.c_double_p), _ptr(pos),
+            _ptr(types), _ptr(out["energy"]), _ptr(out["Ei"]), _ptr(out["F"]), _stream(stream)))
+        return out
+
+    def param_grad(self, pos, types, starts, boxes, dLdE=None, dLdF=None, stream=None):
+        """sum_b dLdE_b dE_b/dtheta + sum_m dLdF_m . dF_m/dtheta  (float32 [num_params])."""
+        st, bx = self._layout(starts, boxes)
+        n = int(st[-1])
+        _need(pos, torch.float32, (n, 3), "pos", self.device)
+        _need(types, torch.int32, (n,), "types", self.device)
+        if dLdE is not None:
+            _need(dLdE, torch.float64, (len(bx),), "dLdE", self.device)
+        if dLdF is not None:
+            _need(dLdF, torch.float32, (n, 3), "dLdF", self.device)
+        g = torch.empty(self.num_params, dtype=torch.float32, device=pos.device)
+        self._check(self._lib.nnp_param_grad(
+            self.h, len(bx), st.ctypes.data_as(_capi.c_int_p), bx.ctypes.data_as(_capi.c_double_p), _ptr(pos),
+            _ptr(types), _ptr(dLdE), _ptr(dLdF), _ptr(g), _stream(stream)))
+        return g
+
     def set_weights(self, w, stream=None):
         _need(w, torch.float32, (self.num_params,), "weights", self.device)
         self._check(self._lib.nnp_set_weights(self.h, _ptr(w), _stream(stream)))
