@@ -174,6 +174,121 @@ def reference_arm(args, rank):
     print(json.dumps(out), flush=True)
 
 
+def training_leg(dev, steps, warmup):
+    """Force-matching training step on the ragged batch of 256 water-like
+    configurations (66-510 atoms): energies and forces, loss, gradient with
+    respect to every network parameter (energy term + double backward)."""
+    import torch
+    from paper_2002_00054_b300 import NNP
+    from paper_2002_00054_b300.autograd import EnergyForces, NNPEnergy, TrainingBatch, force_matching_loss
+    systems = workloads.train_batch()
+    starts = np.cumsum([0] + [len(p) for p, _, _ in systems]).astype(np.int32)
+    pos = np.concatenate([p for p, _, _ in systems]).astype(np.float32)
+    types = np.concatenate([t for _, t, _ in systems]).astype(np.int32)
+    boxes = np.stack([b for _, _, b in systems]).astype(np.float32).astype(np.float64)
+    model = workloads.water_model()
+    teacher = NNP(workloads.water_model(seed=workloads.SEED_TEACHER_MODEL), device=dev.index)
+    p = torch.from_numpy(pos).to(dev)
+    t = torch.from_numpy(types).to(dev)
+    lab = teacher.compute_batch(p, t, starts, boxes)   # labels: teacher network + force noise
+    gen = torch.Generator(device=dev).manual_seed(workloads.SEED_TRAIN)
+    Fref = lab["F"].double() + 0.01 * torch.randn(lab["F"].shape, generator=gen, device=dev, dtype=torch.float64)
+    Eref = lab["energy"]
+    teacher.close()
+    nnp = NNP(model, device=dev.index)
+    batch = TrainingBatch(nnp, t, starts, boxes)
+    w = torch.tensor(np.concatenate(model["weights"]), dtype=torch.float32, device=dev, requires_grad=True)
+    n_atoms = torch.tensor(np.diff(starts), dtype=torch.float64, device=dev)
+    out = {}
+    for form in ("energy_forces", "double_backward"):
+        def step():
+            w.grad = None
+            if form == "energy_forces":
+                E, F = EnergyForces.apply(p, w, batch)
+            else:
+                x = p.clone().requires_grad_(True)
+                E = NNPEnergy.apply(x, w, batch)
+                F = -torch.autograd.grad(E.sum(), x, create_graph=True)[0]
+            loss = force_matching_loss(E, F, Eref, Fref, n_atoms, 10.0)
+            loss.backward()
+            return loss
+        for _ in range(warmup):
+            step()
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        for _ in range(steps):
+            loss = step()
+        a1.record()
+        torch.cuda.synchronize()
+        ms = a0.elapsed_time(a1) / steps
+        out[form] = {"ms_per_step": ms, "configs": len(systems), "atoms": int(starts[-1]),
+                     "atom_gradients_per_s": starts[-1] / (ms * 1e-3), "loss": float(loss.item())}
+    nnp.close()
+    return out
+
+
+def combined_run(args, dev):
+    """1,048,320-atom water-like box, BF16 tensor-core network, forces from the
+    autograd backward (NNPEnergy), velocity Verlet for --steps steps at 0.5 fs;
+    conserved-energy drift in FP64, force RMS against the FP32 path."""
+    import torch
+    from paper_2002_00054_b300 import NNP
+    from paper_2002_00054_b300.autograd import NNPEnergy, TrainingBatch
+    pos_h, types_h, box = workloads.water_lattice((13, 20, 21))
+    box = np.asarray(box, np.float32).astype(np.float64)
+    model = workloads.water_model()
+    n = len(pos_h)
+    nnp = NNP(model, device=dev.index, precision="bf16", max_neighbors=200)
+    ref = NNP(model, device=dev.index, max_neighbors=200)
+    x = torch.tensor(pos_h, dtype=torch.float32, device=dev)
+    v = torch.tensor(workloads.maxwell_boltzmann(types_h, model["masses"]), dtype=torch.float32, device=dev)
+    t = torch.tensor(types_h, dtype=torch.int32, device=dev)
+    batch = TrainingBatch(nnp, t, [0, n], box[None, :])
+    w = torch.tensor(np.concatenate(model["weights"]), dtype=torch.float32, device=dev)
+    inv_m = (workloads.ACC / torch.tensor(model["masses"], dtype=torch.float32, device=dev))[t.long()][:, None]
+    mass = torch.tensor(model["masses"], dtype=torch.float64, device=dev)[t.long()][:, None]
+
+    def forces(xx):
+        xr = xx.detach().requires_grad_(True)
+        E = NNPEnergy.apply(xr, w, batch)
+        F = -torch.autograd.grad(E.sum(), xr)[0]
+        return E.detach(), F.detach()
+
+    E, F = forces(x)
+    f32 = ref.compute(x, t, box)
+    f_rms = float((F - f32["F"]).double().pow(2).mean().sqrt().item())
+    dt = DT_FS
+
+    def etot(E):
+        return float(E.item() + (0.5 * mass * v.double() ** 2).sum().item() / workloads.ACC)
+
+    e0 = etot(E)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    log = []
+    for k in range(args.steps):
+        v += 0.5 * dt * F * inv_m
+        x += dt * v
+        E, F = forces(x)
+        v += 0.5 * dt * F * inv_m
+        if (k + 1) % 100 == 0:
+            log.append(etot(E))
+    a1.record()
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1)
+    e1 = etot(E)
+    drift = (e1 - e0) / n / (args.steps * dt * 1e-6)   # eV per atom per ns
+    return {"metric": METRIC, "mode": "combined", "value": n * args.steps / (ms * 1e-3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "dtype": "bf16-network/f32", "data": "synthetic",
+            "config": {"workload": "water_1m", "atoms": n, "dt_fs": dt,
+                       "forces": "NNPEnergy autograd backward, BF16 tensor-core network"},
+            "conserved_energy_drift_ev_per_atom_per_ns": drift, "energy_log_every_100_steps": log,
+            "initial_force_rms_vs_fp32_ev_per_A": f_rms}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -184,6 +299,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-network leg")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
+    ap.add_argument("--mode", default="standard", choices=["standard", "combined"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -202,6 +319,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_2002_00054_b300 import NNP, opcount
+    if args.mode == "combined":
+        if rank == 0:
+            print(json.dumps(combined_run(args, dev)), flush=True)
+        return
 
     model, pos_h, types_h, box, desc, max_nb = make_workload(args.workload)
     n = len(pos_h)
@@ -333,6 +454,8 @@ def main():
             "force_max_err_vs_fp32_ev_per_A": float(dF.abs().max().item()),
             "energy_err_vs_fp32_ev_per_atom": float(abs(b16_out["energy"].item() - f32_out["energy"].item()) / n)}
         bf.close()
+    if not args.no_train:
+        out["training_step"] = training_leg(dev, max(3, args.steps // 2), args.warmup)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model["name"])
     if rank == 0:

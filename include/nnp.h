@@ -167,7 +167,10 @@ NNP_API int nnp_step(nnp_handle* h, int n_atoms, float* pos, float* vel, const i
  * configurations of different sizes): system b holds atoms sys_start[b] ..
  * sys_start[b+1]-1 (host int [n_systems + 1], sys_start[0] = 0) in the box
  * boxes[3b .. 3b+2] (host double).  Every box edge must be >= (cutoff + skin)/2;
- * neighbours include every periodic image within the cutoff.
+ * neighbours include every periodic image within the cutoff.  With n_systems > 1
+ * each system is searched by brute force over images (cost ~ N_b^2; at most
+ * 16384 atoms per system, NNP_EINVAL beyond); a single system takes the
+ * cell-list path of nnp_compute.
  *
  * nnp_compute_batch: energies (device double [n_systems], FP64 sums), per-atom
  * energies and forces (device, nullable) of every system; Fig. 1b steps 1-3. */

@@ -1019,6 +1019,12 @@ static int batch_args(nnp_handle* h, int B, const int* start, const double* boxe
     }
     n = start[B];
     if (n > (int)NB_INDEX_MASK) return set_err(h, NNP_EINVAL, "n_atoms must be < 2^24");
+    // systems of a multi-system batch are searched by brute force over images (cost ~ N_b^2)
+    if (B > 1)
+        for (int b = 0; b < B; ++b)
+            if (start[b + 1] - start[b] > 16384)
+                return set_err(h, NNP_EINVAL, "system %d of a batch has %d atoms; batch systems are limited to 16384 "
+                               "(a single system of any size takes the cell-list path)", b, start[b + 1] - start[b]);
     if (n > 0 && (!pos || !types)) return set_err(h, NNP_EINVAL, "pos and types must not be NULL");
     return NNP_OK;
 }
@@ -1042,7 +1048,9 @@ int nnp_compute_batch(nnp_handle* h, int B, const int* start, const double* boxe
     rc = begin_call(h, st);
     if (rc) return rc;
     Batch bt{B, start, boxes};
-    rc = run_eval(h, n, pos, types, boxes, st, energies, atom_energy, forces, nullptr, nullptr, nullptr, 0, &bt);
+    // one system: the single-system path (cell lists for large boxes)
+    rc = run_eval(h, n, pos, types, boxes, st, energies, atom_energy, forces, nullptr, nullptr, nullptr, 0,
+                  B > 1 ? &bt : nullptr);
     if (rc) return rc;
     return read_status(h, st);
 }
@@ -1069,8 +1077,9 @@ int nnp_param_grad(nnp_handle* h, int B, const int* start, const double* boxes, 
     rc = begin_call(h, st);
     if (rc) return rc;
     Batch bt{B, start, boxes};
+    const Batch* btp = B > 1 ? &bt : nullptr;
     // descriptors G~ of the current positions (stop after the descriptor pass)
-    rc = run_eval(h, n, pos, types, boxes, st, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, &bt);
+    rc = run_eval(h, n, pos, types, boxes, st, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1, btp);
     if (rc) return rc;
     const Plan& P = h->plan;
     Box bx;
@@ -1080,7 +1089,11 @@ int nnp_param_grad(nnp_handle* h, int B, const int* start, const double* boxes, 
         ForceKernel kf;
         TangentKernel kt;
         pick_kernels(P, ksf, kf, kt);
-        NbView nv{h->nbr, h->ncount, h->stride, h->sys_of, h->sys_box};
+        NbView nv{h->nbr, h->ncount, h->stride};
+        if (btp) {
+            nv.sys_of = h->sys_of;
+            nv.sys_box = h->sys_box;
+        }
         KScope ks(h, KG_FORCE, st);
         kt<<<std::min(blocks_for(n, 4), h->grid_tan), 128, h->smem_tan, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc,
                                                                             dLdF, h->T, h->flags);
@@ -1100,7 +1113,8 @@ int nnp_param_grad(nnp_handle* h, int B, const int* start, const double* boxes, 
         k_elem_scan<<<1, 1024, 0, st>>>(nblk, P.n_elem, h->elem_part, h->elem_off, toff);
         k_elem_fill<<<nblk, 256, 0, st>>>(n, h->pos4, P.n_elem, h->elem_part, h->elem_idx);
         CK(h, cudaMemsetAsync(h->gpart, 0, sizeof(float) * need, st));
-        k_param_grad<<<gpg, 128, h->smem_pg, st>>>(n, h->d_plan, h->d_w, h->pos4, h->elem_idx, h->sys_of, dLdE, h->G,
+        k_param_grad<<<gpg, 128, h->smem_pg, st>>>(n, h->d_plan, h->d_w, h->pos4, h->elem_idx, btp ? h->sys_of : nullptr,
+                                                   dLdE, h->G,
                                                    dLdF ? h->T : nullptr, h->gpart);
         k_grad_reduce<<<blocks_for(h->n_params, 256), 256, 0, st>>>(nwarps, P.n_elem, P.n_params_elem, h->gpart, grad);
     }
