@@ -231,7 +231,11 @@ def training_leg(dev, steps, warmup):
 def combined_run(args, dev):
     """1,048,320-atom water-like box, BF16 tensor-core network, forces from the
     autograd backward (NNPEnergy), velocity Verlet for --steps steps at 0.5 fs;
-    conserved-energy drift in FP64, force RMS against the FP32 path."""
+    conserved-energy drift in FP64, force RMS against the FP32 path.  The same
+    start is then run by the FP32 path's own integrator (nnp_step) for the same
+    steps: its drift is what the dynamics on this random-weight model gives
+    without reduced precision (the model heats the box to several thousand K, so
+    the neighbour lists get a capacity of 320)."""
     import torch
     from paper_2002_00054_b300 import NNP
     from paper_2002_00054_b300.autograd import NNPEnergy, TrainingBatch
@@ -239,8 +243,8 @@ def combined_run(args, dev):
     box = np.asarray(box, np.float32).astype(np.float64)
     model = workloads.water_model()
     n = len(pos_h)
-    nnp = NNP(model, device=dev.index, precision="bf16", max_neighbors=200)
-    ref = NNP(model, device=dev.index, max_neighbors=200)
+    nnp = NNP(model, device=dev.index, precision="bf16", max_neighbors=320)
+    ref = NNP(model, device=dev.index, max_neighbors=320)
     x = torch.tensor(pos_h, dtype=torch.float32, device=dev)
     v = torch.tensor(workloads.maxwell_boltzmann(types_h, model["masses"]), dtype=torch.float32, device=dev)
     t = torch.tensor(types_h, dtype=torch.int32, device=dev)
@@ -255,10 +259,14 @@ def combined_run(args, dev):
         F = -torch.autograd.grad(E.sum(), xr)[0]
         return E.detach(), F.detach()
 
+    x0, v0 = x.clone(), v.clone()
     E, F = forces(x)
     f32 = ref.compute(x, t, box)
     f_rms = float((F - f32["F"]).double().pow(2).mean().sqrt().item())
     dt = DT_FS
+    # warm-up: the kernels' shared-memory capacity settles after the first calls
+    for _ in range(2):
+        forces(x)
 
     def etot(E):
         return float(E.item() + (0.5 * mass * v.double() ** 2).sum().item() / workloads.ACC)
@@ -268,11 +276,14 @@ def combined_run(args, dev):
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a0.record()
     log = []
+    max_row, spilled = 0, 0
     for k in range(args.steps):
         v += 0.5 * dt * F * inv_m
         x += dt * v
         E, F = forces(x)
         v += 0.5 * dt * F * inv_m
+        st = nnp.stats()
+        max_row, spilled = max(max_row, st["max_list_row"]), spilled + st["spilled_atoms"]
         if (k + 1) % 100 == 0:
             log.append(etot(E))
     a1.record()
@@ -280,13 +291,27 @@ def combined_run(args, dev):
     ms = a0.elapsed_time(a1)
     e1 = etot(E)
     drift = (e1 - e0) / n / (args.steps * dt * 1e-6)   # eV per atom per ns
+    # the FP32 path's own integrator from the same start
+    x, v = x0.clone(), v0.clone()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record()
+    lg = ref.step(x, v, t, box, dt, args.steps).cpu().numpy()
+    b1.record()
+    torch.cuda.synchronize()
+    et = lg.sum(1)
+    fp32_drift = (et[-1] - et[0]) / n / (args.steps * dt * 1e-6)
     return {"metric": METRIC, "mode": "combined", "value": n * args.steps / (ms * 1e-3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "dtype": "bf16-network/f32", "data": "synthetic",
             "config": {"workload": "water_1m", "atoms": n, "dt_fs": dt,
                        "forces": "NNPEnergy autograd backward, BF16 tensor-core network"},
             "conserved_energy_drift_ev_per_atom_per_ns": drift, "energy_log_every_100_steps": log,
-            "initial_force_rms_vs_fp32_ev_per_A": f_rms}
+            "initial_force_rms_vs_fp32_ev_per_A": f_rms,
+            "max_list_row": max_row, "spilled_atom_evaluations": spilled,
+            "fp32_nnp_step": {"conserved_energy_drift_ev_per_atom_per_ns": float(fp32_drift),
+                              "final_temperature_K": float(2 * lg[-1, 1] / (3 * n * workloads.KB_EV)),
+                              "ms_per_step": b0.elapsed_time(b1) / args.steps,
+                              "energy_log_every_100_steps": [float(e) for e in et[100::100]]}}
 
 
 def main():

@@ -200,6 +200,16 @@ typedef struct {
     long long triplets;        /* pairs that contribute (narrow: r_jk < r_c)       */
     long long rebuilds;        /* neighbour-list builds since creation             */
     long long kernel_launches; /* CUDA kernels launched by the last call           */
+    long long max_list_row;    /* largest neighbour-list row (entries within r_c +
+                                  skin) in any evaluation of the last call; a
+                                  row above max_neighbors fails the call          */
+    long long max_cutoff_row;  /* largest count of neighbours inside r_c          */
+    long long spilled_atoms;   /* atom evaluations of the last call that took the
+                                  wide-capacity pass (more neighbours inside r_c
+                                  than the main launch stages in shared memory)   */
+    long long rc_capacity;     /* neighbours inside r_c the main launches stage
+                                  per atom; re-tuned after every call from the
+                                  counts seen (results do not depend on it)      */
 } nnp_stats;
 NNP_API int nnp_get_stats(nnp_handle* h, nnp_stats* out);
 

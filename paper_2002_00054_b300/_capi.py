@@ -36,7 +36,9 @@ class Stats(ctypes.Structure):
     _fields_ = [("n_atoms", ctypes.c_longlong), ("list_entries", ctypes.c_longlong),
                 ("cutoff_entries", ctypes.c_longlong), ("pairs", ctypes.c_longlong),
                 ("triplets", ctypes.c_longlong), ("rebuilds", ctypes.c_longlong),
-                ("kernel_launches", ctypes.c_longlong)]
+                ("kernel_launches", ctypes.c_longlong), ("max_list_row", ctypes.c_longlong),
+                ("max_cutoff_row", ctypes.c_longlong), ("spilled_atoms", ctypes.c_longlong),
+                ("rc_capacity", ctypes.c_longlong)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/nnp.h

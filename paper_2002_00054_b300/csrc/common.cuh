@@ -31,7 +31,11 @@
 #define CNT_RC 1
 #define CNT_PAIRS 2
 #define CNT_TRIPLETS 3
-#define CNT_REBUILDS 4
+#define CNT_MAXLIST 4   // largest neighbour-list row seen by the call
+#define CNT_MAXRC 5     // largest count of neighbours inside the cutoff
+#define CNT_SPILL 6     // atoms handed to the wide-capacity pass
+#define CNT_PER_CALL 7  // counters [0, CNT_PER_CALL) restart with every API call
+#define CNT_REBUILDS 7
 #define CNT_N 8
 
 #define LOG2E 1.4426950408889634f

@@ -49,6 +49,35 @@ __device__ __forceinline__ void atom_box(const NbView& nv, const Box& bx, int i,
 
 #define PAIR_QUEUE 1024   // live pairs of one 32 x 32 block, as (l | s << 5)
 
+// Atoms with more neighbours inside the cutoff than the shared-memory capacity C
+// of the main launch.  The descriptor kernel's main pass (pass 0) appends them to
+// spill[1 ..] (count in spill[0]) and skips them; every kernel's pass 1 walks that
+// queue with C = list stride, which no atom can exceed.  The per-atom arithmetic
+// is the same in both passes.
+__device__ __forceinline__ int atom_count(int pass, int n, const int* spill)
+{
+    return pass ? spill[0] : n;
+}
+__device__ __forceinline__ int atom_at(int pass, int it, const int* spill)
+{
+    return pass ? spill[1 + it] : it;
+}
+// true when atom i must be skipped by this pass (M > C)
+__device__ __forceinline__ bool over_capacity(int M, int C, int pass, int i, int* spill, bool enqueue, int lane,
+                                              int* flags, unsigned long long& c_spill)
+{
+    if (M <= C) return false;
+    if (lane == 0) {
+        if (pass) {
+            atomicOr(&flags[FLAG_ERR], ERR_RC_OVERFLOW);   // C = stride in pass 1: unreachable
+        } else if (enqueue) {
+            spill[1 + atomicAdd(spill, 1)] = i;
+            ++c_spill;
+        }
+    }
+    return true;
+}
+
 // Per-warp shared-memory arrays (C = capacity inside the cutoff, S = list stride).
 struct WarpSmem {
     float4* nd;     // (dx, dy, dz, r) (descriptor pass) or (dx, dy, dz, 1/r) (force pass)
@@ -143,10 +172,6 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
         }
         M += __popc(m);
     }
-    if (M > C) {
-        if (lane == 0) atomicOr(&flags[FLAG_ERR], ERR_RC_OVERFLOW);
-        M = C;
-    }
     __syncwarp();
     return M;
 }
@@ -229,7 +254,7 @@ template <int NETA, bool NARROW, int KP, int KN>
 __global__ void __launch_bounds__(128, 6)
 k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g,
      int C, float* __restrict__ Gs, float* __restrict__ Graw, int* __restrict__ flags,
-     unsigned long long* __restrict__ counters)
+     unsigned long long* __restrict__ counters, int* __restrict__ spill, int pass)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -247,9 +272,11 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     w.sg = nullptr;
     w.cmap = nullptr;
 
-    unsigned long long c_list = 0, c_rc = 0, c_pairs = 0, c_trip = 0;
+    unsigned long long c_list = 0, c_rc = 0, c_pairs = 0, c_trip = 0, c_max = 0, c_maxrc = 0, c_spill = 0;
     const int nw = gridDim.x * wpb;
-    for (int i = blockIdx.x * wpb + wib; i < n; i += nw) {
+    const int n_items = atom_count(pass, n, spill);
+    for (int it = blockIdx.x * wpb + wib; it < n_items; it += nw) {
+        const int i = atom_at(pass, it, spill);
         const float4 pi = pos4[i];
         const int ti = __float_as_int(pi.w);
         const ElemPlan& E = P.e[ti];
@@ -263,6 +290,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         int n_list;
         const int M = stage_neighbors<NETA, false>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, nullptr, lane,
                                                    flags, n_list);
+        if (over_capacity(M, C, pass, i, spill, true, lane, flags, c_spill)) continue;
         // radial: lane <-> descriptor (two neighbour halves when n_rad <= 16), loop over
         // neighbours with broadcast reads; Kahan-compensated sums (they feed
         // G~ = (G - mu)/s with |mu/s| up to ~20)
@@ -382,6 +410,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         __syncwarp();
         if (lane == 0) {
             c_list += (unsigned long long)n_list;
+            c_max = max(c_max, (unsigned long long)n_list);
+            c_maxrc = max(c_maxrc, (unsigned long long)M);
             c_rc += (unsigned long long)M;
         }
     }
@@ -394,6 +424,9 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         atomicAdd(&counters[CNT_RC], c_rc);
         atomicAdd(&counters[CNT_PAIRS], c_pairs);
         atomicAdd(&counters[CNT_TRIPLETS], t);
+        atomicMax(&counters[CNT_MAXLIST], c_max);
+        atomicMax(&counters[CNT_MAXRC], c_maxrc);
+        if (c_spill) atomicAdd(&counters[CNT_SPILL], c_spill);
     }
 }
 
@@ -404,7 +437,7 @@ template <int NETA, bool NARROW, int KP, int KN>
 __global__ void __launch_bounds__(128, 5)
 k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
-        double* __restrict__ vir_part, int* __restrict__ flags)
+        double* __restrict__ vir_part, int* __restrict__ flags, int* __restrict__ spill, int pass)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -426,7 +459,10 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
 #pragma unroll
     for (int q = 0; q < 9; ++q) vir[q] = 0.0;
     const int nw = gridDim.x * wpb;
-    for (int i = blockIdx.x * wpb + wib; i < n; i += nw) {
+    const int n_items = atom_count(pass, n, spill);
+    unsigned long long c_spill = 0;
+    for (int it = blockIdx.x * wpb + wib; it < n_items; it += nw) {
+        const int i = atom_at(pass, it, spill);
         const float4 pi = pos4[i];
         const int ti = __float_as_int(pi.w);
         const ElemPlan& E = P.e[ti];
@@ -442,6 +478,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         int n_list;
         const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
                                                   n_list);
+        if (over_capacity(M, C, pass, i, spill, false, lane, flags, c_spill)) continue;
         if (NETA > 0) {
             // dense weights W[q][l][k] = dE/dG_o * 2^(1-zeta), zeta = 2^k
             float W[NETA > 0 ? NETA : 1][2][NNP_KMAX + 1];

@@ -23,7 +23,8 @@ __host__ __device__ inline size_t tangent_warp_bytes(int C)
 template <int NETA, bool NARROW, int KP, int KN>
 __global__ void __launch_bounds__(128, 4)
 k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
-          const float* __restrict__ u, float* __restrict__ T, int* __restrict__ flags)
+          const float* __restrict__ u, float* __restrict__ T, int* __restrict__ flags, int* __restrict__ spill,
+          int pass)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -40,7 +41,10 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
     unsigned short* queue = reinterpret_cast<unsigned short*>(ninv + C);
 
     const int nw = gridDim.x * wpb;
-    for (int i = blockIdx.x * wpb + wib; i < n; i += nw) {
+    const int n_items = atom_count(pass, n, spill);
+    unsigned long long c_spill = 0;
+    for (int it = blockIdx.x * wpb + wib; it < n_items; it += nw) {
+        const int i = atom_at(pass, it, spill);
         const float4 pi = pos4[i];
         const int ti = __float_as_int(pi.w);
         const ElemPlan& E = P.e[ti];
@@ -99,11 +103,8 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
             }
             M += __popc(m);
         }
-        if (M > C) {
-            if (lane == 0) atomicOr(&flags[FLAG_ERR], ERR_RC_OVERFLOW);
-            M = C;
-        }
         __syncwarp();
+        if (over_capacity(M, C, pass, i, spill, false, lane, flags, c_spill)) continue;
         // radial: lane <-> descriptor; t = sum_j dG/dr (r^ . du_j)
         for (int rr = lane; rr < E.n_rad; rr += 32) {
             const float kh = E.rad_khi[rr], kl = E.rad_klo[rr], rs = E.rad_rs[rr], eta = E.rad_eta[rr];

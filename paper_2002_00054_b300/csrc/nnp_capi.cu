@@ -113,10 +113,19 @@ struct nnp_handle {
 
     // launch configuration
     int num_sms = 148;
-    int wpb_sf = 8, wpb_force = 8;
+    int max_smem = 0;
+    int wpb_sf = 8, wpb_force = 8, wpb_tan = 4;
     size_t smem_sf = 0, smem_force = 0, smem_mlp = 0;
     int grid_sf = 0, grid_force = 0, grid_mlp = 0;
-    int cap_rc = 0;
+    int cap_rc = 0;   // main launches: neighbours inside the cutoff staged per warp (set_capacity)
+    // wide-capacity pass over the atoms above cap_rc (capacity = list stride)
+    int* spill = nullptr;   // [cap_n + 1]: count, then atom indices
+    int wpb_sf_sp = 1, wpb_force_sp = 1, wpb_tan_sp = 1;
+    size_t smem_sf_sp = 0, smem_force_sp = 0, smem_tan_sp = 0;
+    int grid_sp = 0;
+    // counters read back with the status; evaluations in the current call
+    unsigned long long* h_cnt = nullptr;
+    int evals = 0;
 };
 
 static thread_local std::string g_create_err;
@@ -264,11 +273,12 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
 }
 
 // --------------------------------------------------------------- dispatch
-typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, float*, float*, int*, unsigned long long*);
+typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, float*, float*, int*, unsigned long long*,
+                         int*, int);
 typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
-                            double*, int*);
+                            double*, int*, int*, int);
 
-typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*);
+typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*, int*, int);
 
 template <int NETA, bool NARROW, int KP, int KN>
 static void pick(SfKernel& s, ForceKernel& f, TangentKernel& t)
@@ -316,6 +326,61 @@ static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
 static size_t sf_smem_per_warp(int cap) { return sf_warp_bytes(cap); }
 static size_t force_smem_per_warp(int cap, int stride) { return force_warp_bytes(cap, stride); }
 
+// Shared-memory capacity C of the main descriptor, force and tangent launches:
+// warps per block (at most 4, the kernels' launch bounds), dynamic shared memory
+// and occupancy-sized grids.  Atoms with more than C neighbours inside the
+// cutoff take the wide-capacity pass, so C trades occupancy against that pass.
+static int set_capacity(nnp_handle* h, int C)
+{
+    SfKernel ksf;
+    ForceKernel kf;
+    TangentKernel kt;
+    pick_kernels(h->plan, ksf, kf, kt);
+    const size_t ps = sf_smem_per_warp(C), pf = force_smem_per_warp(C, h->stride), pt = tangent_warp_bytes(C);
+    const size_t ms = (size_t)h->max_smem;
+    if (ps > ms || pf > ms) return set_err(h, NNP_EINVAL, "shared-memory capacity %d does not fit one block", C);
+    h->cap_rc = C;
+    h->wpb_sf = (int)std::min<size_t>(4, ms / ps);
+    h->wpb_force = (int)std::min<size_t>(4, ms / pf);
+    h->wpb_tan = (int)std::max<size_t>(1, std::min<size_t>(4, ms / pt));
+    h->smem_sf = ps * h->wpb_sf;
+    h->smem_force = pf * h->wpb_force;
+    h->smem_tan = pt * h->wpb_tan;
+    int bs = 0;
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)ksf, 32 * h->wpb_sf, h->smem_sf));
+    h->grid_sf = std::max(1, bs) * h->num_sms;
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)kf, 32 * h->wpb_force, h->smem_force));
+    h->grid_force = std::max(1, bs) * h->num_sms;
+    if (h->smem_pg && pt <= ms) {
+        CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)kt, 32 * h->wpb_tan, h->smem_tan));
+        h->grid_tan = std::max(1, bs) * h->num_sms;
+    }
+    return NNP_OK;
+}
+
+// After a call: grow C by a quarter when more than 0.2% of the evaluated atoms
+// took the wide-capacity pass; shrink it to 1.1 x the largest count seen when
+// that is below 0.85 C.  Applies from the next call; results do not depend on C.
+static void retune_capacity(nnp_handle* h)
+{
+    if (h->evals <= 0 || h->list_n <= 0) return;
+    const double evaluated = (double)h->list_n * h->evals;
+    const double spilled = (double)h->h_cnt[CNT_SPILL];
+    const int maxrc = (int)h->h_cnt[CNT_MAXRC];
+    int C = h->cap_rc;
+    if (spilled > 0.002 * evaluated) {
+        C = (int)std::ceil(1.25 * C);
+    } else {
+        const int fit = (int)std::ceil(1.1 * maxrc);
+        if (maxrc > 0 && fit < 0.85 * C) C = fit;
+    }
+    C = std::min(h->stride, std::max(32, (C + 7) & ~7));
+    if (C != h->cap_rc) {
+        const int old = h->cap_rc;
+        if (set_capacity(h, C) != NNP_OK) set_capacity(h, old);
+    }
+}
+
 // ------------------------------------------------------------------ scratch
 static int blocks_for(int n, int t) { return (n + t - 1) / t; }
 
@@ -352,6 +417,7 @@ static int ensure_atoms(nnp_handle* h, int n)
     CK(h, regrow(h->elem_part, (size_t)blocks_for(cap, 256) * NNP_MAXE));
     CK(h, regrow(h->sys_of, cap));
     CK(h, regrow(h->T, (size_t)cap * h->plan.gs));
+    CK(h, regrow(h->spill, (size_t)cap + 1));
     h->bt_start.clear();
     h->cap_n = cap;
     h->list_valid = false;
@@ -467,6 +533,7 @@ static int read_status(nnp_handle* h, cudaStream_t st)
 {
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(h->h_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaMemcpyAsync(h->h_cnt, h->counters, sizeof(unsigned long long) * CNT_N, cudaMemcpyDeviceToHost, st));
     CK(h, cudaStreamSynchronize(st));
     prof_flush(h);
     const int f = h->h_flags[0];
@@ -474,14 +541,17 @@ static int read_status(nnp_handle* h, cudaStream_t st)
         // errors leave the neighbour list and the step state unknown
         h->list_valid = false;
         h->step_valid = false;
-        if (f & (ERR_NEIGH_OVERFLOW | ERR_RC_OVERFLOW))
-            return set_err(h, NNP_ENEIGH_OVERFLOW, "an atom has more than max_neighbors = %d neighbours", h->stride);
+        if (f & ERR_NEIGH_OVERFLOW)
+            return set_err(h, NNP_ENEIGH_OVERFLOW,
+                           "an atom has more than max_neighbors = %d neighbours within cutoff + skin", h->stride);
         if (f & ERR_CELL_OVERFLOW) return set_err(h, NNP_ENEIGH_OVERFLOW, "a cell holds more than %d atoms", CELL_CAP);
+        if (f & ERR_RC_OVERFLOW) return set_err(h, NNP_ECUDA, "internal error: wide-capacity pass overflowed");
         if (f & ERR_CLOSE) return set_err(h, NNP_ENONFINITE, "two atoms are closer than 1e-4 A");
         if (f & ERR_NONFINITE) return set_err(h, NNP_ENONFINITE, "non-finite position/energy/force or invalid element type");
         if (f & ERR_REV) return set_err(h, NNP_ECUDA, "internal error: neighbour list not symmetric");
         return set_err(h, NNP_ECUDA, "device error word 0x%x", f);
     }
+    retune_capacity(h);
     return NNP_OK;
 }
 
@@ -612,11 +682,15 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     SfKernel ksf;
     ForceKernel kf;
     pick_kernels(P, ksf, kf);
+    h->evals++;
     {
-        KScope ks(h, KG_SF, st);
+        KScope ks(h, KG_SF, st, 2);
+        CK(h, cudaMemsetAsync(h->spill, 0, sizeof(int), st));
         const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
         ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->G, G_out, h->flags,
-                                                     h->counters);
+                                                     h->counters, h->spill, 0);
+        ksf<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride, h->G, G_out,
+                                                                 h->flags, h->counters, h->spill, 1);
     }
     if (stop_after == 1 && !dEdG_out) return read_status(h, st);
     if (h->precision == NNP_BF16) {
@@ -638,14 +712,19 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
                                           sizeof(float) * P.width[0], n, cudaMemcpyDeviceToDevice, st));
     if (stop_after >= 1) return read_status(h, st);
     const int gf = std::min(blocks_for(n, h->wpb_force), h->grid_force);
-    const int nvp = gf * h->wpb_force;
+    const int nvp_main = gf * h->wpb_force;
+    const int nvp = nvp_main + h->grid_sp * h->wpb_force_sp;
     const int gred = std::min(blocks_for(n, T), 4 * h->num_sms);
     rc = ensure_red(h, gred, nvp);
     if (rc) return rc;
     {
-        KScope ks(h, KG_FORCE, st);
+        KScope ks(h, KG_FORCE, st, 2);
         kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf,
-                                                         h->Fown, h->vpart, h->flags);
+                                                         h->Fown, h->vpart, h->flags, h->spill, 0);
+        kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride,
+                                                                       h->dEdG, h->gbuf, h->Fown,
+                                                                       h->vpart + (size_t)nvp_main * 9, h->flags,
+                                                                       h->spill, 1);
     }
     {
         KScope ks(h, KG_GATHER, st);
@@ -667,7 +746,8 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
 static int begin_call(nnp_handle* h, cudaStream_t st)
 {
     h->launches = 0;
-    CK(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CNT_REBUILDS, st));
+    h->evals = 0;
+    CK(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CNT_PER_CALL, st));
     return NNP_OK;
 }
 
@@ -729,14 +809,6 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     h->skin = params->skin;
     h->stride = (params->max_neighbors + 7) & ~7;   // multiple of 8 keeps per-warp shared arrays 16-byte aligned
     h->precision = params->mlp_precision;
-    {
-        // capacity for entries inside the cutoff: the list's headroom over the same
-        // volume ratio, (rc / (rc + skin))^3
-        const double ratio = std::pow(params->cutoff / (params->cutoff + params->skin), 3.0);
-        int c = (int)std::ceil(h->stride * ratio);
-        c = std::max(32, (c + 7) & ~7);
-        h->cap_rc = std::min(c, h->stride);
-    }
     DeviceGuard g(device);
     auto fail = [&](int code) {
         g_create_err = h->err;
@@ -768,20 +840,25 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     CKC(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device));
     int max_smem = 0;
     CKC(cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device));
+    h->max_smem = max_smem;
+    CKC(cudaMallocHost((void**)&h->h_cnt, sizeof(unsigned long long) * CNT_N));
     SfKernel ksf;
     ForceKernel kf;
-    pick_kernels(P, ksf, kf);
-    // warps per block limited by shared memory
-    const size_t ps = sf_smem_per_warp(h->cap_rc), pf = force_smem_per_warp(h->cap_rc, h->stride);
-    // 4-warp blocks (the kernels' launch bounds): finer granularity for occupancy
-    h->wpb_sf = (int)std::min<size_t>(4, (size_t)max_smem / ps);
-    h->wpb_force = (int)std::min<size_t>(4, (size_t)max_smem / pf);
-    if (h->wpb_sf < 1 || h->wpb_force < 1) {
-        set_err(h, NNP_EINVAL, "max_neighbors = %d needs more shared memory than one block has", h->stride);
-        return fail(NNP_EINVAL);
+    TangentKernel kt;
+    pick_kernels(P, ksf, kf, kt);
+    {
+        // wide-capacity pass: capacity = list stride, as many warps as fit (<= 4)
+        const size_t ps = sf_smem_per_warp(h->stride), pf = force_smem_per_warp(h->stride, h->stride);
+        if (ps > (size_t)max_smem || pf > (size_t)max_smem) {
+            set_err(h, NNP_EINVAL, "max_neighbors = %d needs more shared memory than one block has", h->stride);
+            return fail(NNP_EINVAL);
+        }
+        h->wpb_sf_sp = (int)std::min<size_t>(4, (size_t)max_smem / ps);
+        h->wpb_force_sp = (int)std::min<size_t>(4, (size_t)max_smem / pf);
+        h->smem_sf_sp = ps * h->wpb_sf_sp;
+        h->smem_force_sp = pf * h->wpb_force_sp;
+        h->grid_sp = h->num_sms;
     }
-    h->smem_sf = ps * h->wpb_sf;
-    h->smem_force = pf * h->wpb_force;
     h->smem_mlp = sizeof(float) * (size_t)P.s_elem * P.n_elem;
     if (h->smem_mlp > (size_t)max_smem) {
         set_err(h, NNP_EUNSUPPORTED, "network weights do not fit in shared memory");
@@ -791,6 +868,7 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     // raise it to the device maximum (never lower it to this handle's need).
     CKC(cudaFuncSetAttribute((const void*)ksf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     CKC(cudaFuncSetAttribute((const void*)kf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    CKC(cudaFuncSetAttribute((const void*)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     CKC(cudaFuncSetAttribute((const void*)k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     if (h->precision == NNP_BF16) {
         auto r16 = [](int x) { return (x + 15) & ~15; };
@@ -810,27 +888,27 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
                                  max_smem - (int)fa.sharedSizeBytes));
     }
     {
-        SfKernel s2;
-        ForceKernel f2;
-        TangentKernel kt;
-        pick_kernels(P, s2, f2, kt);
-        h->smem_tan = tangent_warp_bytes(h->cap_rc) * 4;
+        // parameter gradients: two hidden layers, weights and the tangent pass's
+        // wide-capacity warp in shared memory
         h->smem_pg = sizeof(float) * (size_t)P.s_elem * (P.n_elem + 4);
-        if (h->smem_tan <= (size_t)max_smem && h->smem_pg <= (size_t)max_smem && P.n_layers == 3) {
-            CKC(cudaFuncSetAttribute((const void*)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        const size_t pt = tangent_warp_bytes(h->stride);
+        if (h->smem_pg <= (size_t)max_smem && pt <= (size_t)max_smem && P.n_layers == 3) {
             CKC(cudaFuncSetAttribute((const void*)k_param_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-            int bt = 0;
-            CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bt, (const void*)kt, 128, h->smem_tan));
-            h->grid_tan = std::max(1, bt) * h->num_sms;
+            h->wpb_tan_sp = (int)std::min<size_t>(4, (size_t)max_smem / pt);
+            h->smem_tan_sp = pt * h->wpb_tan_sp;
         } else {
             h->smem_pg = 0;   // gradients unavailable for this model (reported by nnp_param_grad)
         }
     }
+    {
+        // capacity inside the cutoff: the list's headroom over the same volume
+        // ratio, (rc / (rc + skin))^3; re-tuned after every call
+        const double ratio = std::pow(params->cutoff / (params->cutoff + params->skin), 3.0);
+        int c = (int)std::ceil(h->stride * ratio);
+        c = std::min(h->stride, std::max(32, (c + 7) & ~7));
+        if (set_capacity(h, c) != NNP_OK) return fail(NNP_EINVAL);
+    }
     int bs = 0;
-    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)ksf, 32 * h->wpb_sf, h->smem_sf));
-    h->grid_sf = std::max(1, bs) * h->num_sms;
-    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)kf, 32 * h->wpb_force, h->smem_force));
-    h->grid_force = std::max(1, bs) * h->num_sms;
     CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)k_mlp_fp32, 256, h->smem_mlp));
     h->grid_mlp = std::max(1, bs) * h->num_sms;
 #undef CKC
@@ -848,7 +926,7 @@ int nnp_destroy(nnp_handle* h)
                    h->epart, h->vpart, h->d_energy, h->d_log, h->flags, h->counters, h->sys_box};
     for (void* p : dev)
         if (p) cudaFree(p);
-    for (void* p2 : {(void*)h->sys_of, (void*)h->sys_start_d, (void*)h->T, (void*)h->gpart})
+    for (void* p2 : {(void*)h->sys_of, (void*)h->sys_start_d, (void*)h->T, (void*)h->gpart, (void*)h->spill})
         if (p2) cudaFree(p2);
     if (h->pos_cache) cudaFree(h->pos_cache);
     if (h->types_cache) cudaFree(h->types_cache);
@@ -858,6 +936,7 @@ int nnp_destroy(nnp_handle* h)
     }
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     if (h->h_flags) cudaFreeHost(h->h_flags);
+    if (h->h_cnt) cudaFreeHost(h->h_cnt);
     delete h;
     return NNP_OK;
 }
@@ -1094,9 +1173,11 @@ int nnp_param_grad(nnp_handle* h, int B, const int* start, const double* boxes, 
             nv.sys_of = h->sys_of;
             nv.sys_box = h->sys_box;
         }
-        KScope ks(h, KG_FORCE, st);
-        kt<<<std::min(blocks_for(n, 4), h->grid_tan), 128, h->smem_tan, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc,
-                                                                            dLdF, h->T, h->flags);
+        KScope ks(h, KG_FORCE, st, 2);
+        kt<<<std::min(blocks_for(n, h->wpb_tan), h->grid_tan), 32 * h->wpb_tan, h->smem_tan, st>>>(
+            n, h->pos4, bx, nv, h->d_plan, h->cap_rc, dLdF, h->T, h->flags, h->spill, 0);
+        kt<<<h->grid_sp, 32 * h->wpb_tan_sp, h->smem_tan_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride, dLdF, h->T,
+                                                                   h->flags, h->spill, 1);
     }
     const int gpg = std::min(blocks_for(n, 4), 2 * h->num_sms);
     const int nwarps = gpg * 4;
@@ -1167,6 +1248,10 @@ int nnp_get_stats(nnp_handle* h, nnp_stats* out)
     out->triplets = (long long)c[CNT_TRIPLETS];
     out->rebuilds = (long long)c[CNT_REBUILDS];
     out->kernel_launches = h->launches;
+    out->max_list_row = (long long)c[CNT_MAXLIST];
+    out->max_cutoff_row = (long long)c[CNT_MAXRC];
+    out->spilled_atoms = (long long)c[CNT_SPILL];
+    out->rc_capacity = h->cap_rc;
     return NNP_OK;
 }
 
@@ -1237,13 +1322,14 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     const Plan& P = h->plan;
     const int S = h->stride, T = 256;
     const int gf = std::min(blocks_for(std::max(n, 1), h->wpb_force), h->grid_force);
-    const int nvp = gf * h->wpb_force;
+    const int nvp_main = gf * h->wpb_force;
+    const int nvp = nvp_main + h->grid_sp * h->wpb_force_sp;
     const int gred = std::min(blocks_for(std::max(n, 1), T), 4 * h->num_sms);
 
     // scratch layout (the same carving sizes and places it)
     auto layout = [&](Carve& c, int** flags, unsigned long long** counters, float4** sys_box, float4** off, float4** ref,
                       float4** pos4, uint32_t** nbr, int** ncount, int** rev, float** G, float** dEdG, float** Ei,
-                      float4** gbuf, float4** Fown, double** vpart, double** epart, float** F) {
+                      float4** gbuf, float4** Fown, double** vpart, double** epart, float** F, int** spill) {
         *flags = c.take<int>(4);
         *counters = c.take<unsigned long long>(CNT_N);
         *sys_box = c.take<float4>(1);
@@ -1261,18 +1347,19 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
         *vpart = c.take<double>((size_t)nvp * 9);
         *epart = c.take<double>(gred);
         *F = c.take<float>((size_t)n * 3);
+        *spill = c.take<int>((size_t)n + 1);
     };
     int* flags;
     unsigned long long* counters;
     float4 *sys_box, *off, *ref, *pos4, *gbuf, *Fown;
     uint32_t* nbr;
-    int *ncount, *rev;
+    int *ncount, *rev, *spill;
     float *G, *dEdG, *Ei, *Fs;
     double *vpart, *epart;
     {
         Carve dry{nullptr};
         layout(dry, &flags, &counters, &sys_box, &off, &ref, &pos4, &nbr, &ncount, &rev, &G, &dEdG, &Ei, &gbuf, &Fown,
-               &vpart, &epart, &Fs);
+               &vpart, &epart, &Fs, &spill);
         if (dry.off > NNP_STATIC_SCRATCH_BYTES)
             return static_fail(eb, el, NNP_EINVAL,
                                "needs %zu bytes of scratch for n_atoms = %d and max_neighbors = %d; the static "
@@ -1297,7 +1384,7 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     }
     Carve c{static_cast<unsigned char*>(base)};
     layout(c, &flags, &counters, &sys_box, &off, &ref, &pos4, &nbr, &ncount, &rev, &G, &dEdG, &Ei, &gbuf, &Fown, &vpart,
-           &epart, &Fs);
+           &epart, &Fs, &spill);
 
 #define CKS(call)                                                                                      \
     do {                                                                                              \
@@ -1309,8 +1396,10 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
         CKS(cudaStreamSynchronize(st));
         return NNP_OK;
     }
-    // what must start at zero: the error word, the work counters; the rebuild flag is set
+    // what must start at zero: the error word, the work counters, the spill count;
+    // the rebuild flag is set
     CKS(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
+    CKS(cudaMemsetAsync(spill, 0, sizeof(int), st));
     CKS(cudaMemsetAsync(flags + FLAG_REBUILD, 1, sizeof(int), st));
     CKS(cudaMemsetAsync(counters, 0, CNT_N * sizeof(unsigned long long), st));
     Box bx;
@@ -1327,11 +1416,16 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     ForceKernel kf;
     pick_kernels(P, ksf, kf);
     const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
-    ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, G, nullptr, flags, counters);
+    ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, G, nullptr, flags, counters,
+                                                 spill, 0);
+    ksf<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, G, nullptr, flags, counters,
+                                                             spill, 1);
     const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
     k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
     kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, vpart,
-                                                     flags);
+                                                     flags, spill, 0);
+    kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, dEdG, gbuf, Fown,
+                                                                   vpart + (size_t)nvp_main * 9, flags, spill, 1);
     k_gather<<<rows_grid, 256, 0, st>>>(n, nv, rev, gbuf, Fown, forces ? forces : Fs, flags);
     k_sum_partial<<<gred, T, 0, st>>>(n, Ei, epart, flags);
     k_finalize<<<1, 256, 0, st>>>(gred, epart, energy, nvp, vpart, nullptr);
@@ -1341,8 +1435,10 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     CKS(cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKS(cudaStreamSynchronize(st));
 #undef CKS
-    if (hf & (ERR_NEIGH_OVERFLOW | ERR_RC_OVERFLOW))
-        return static_fail(eb, el, NNP_ENEIGH_OVERFLOW, "an atom has more than max_neighbors = %d neighbours", S);
+    if (hf & ERR_NEIGH_OVERFLOW)
+        return static_fail(eb, el, NNP_ENEIGH_OVERFLOW,
+                           "an atom has more than max_neighbors = %d neighbours within cutoff + skin", S);
+    if (hf & ERR_RC_OVERFLOW) return static_fail(eb, el, NNP_ECUDA, "internal error: wide-capacity pass overflowed");
     if (hf & ERR_CLOSE) return static_fail(eb, el, NNP_ENONFINITE, "two atoms are closer than 1e-4 A");
     if (hf & ERR_NONFINITE)
         return static_fail(eb, el, NNP_ENONFINITE, "non-finite position/energy/force or invalid element type");
