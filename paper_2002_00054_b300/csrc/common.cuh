@@ -22,6 +22,7 @@
 #define ERR_CLOSE 8
 #define ERR_REV 16
 #define ERR_RC_OVERFLOW 32
+#define ERR_RANGE 64        // a force contribution non-finite or >= 1024 eV/A (fixed-point range)
 
 #define FLAG_ERR 0
 #define FLAG_REBUILD 1

@@ -82,10 +82,11 @@ __device__ __forceinline__ bool over_capacity(int M, int C, int pass, int i, int
 struct WarpSmem {
     float4* nd;     // (dx, dy, dz, r) (descriptor pass) or (dx, dy, dz, 1/r) (force pass)
     float* ninv;    // 1 / r (descriptor pass)
-    float4* npf;    // P_q
-    float4* ndp;    // dP_q / dr (force)
+    float4* npf;    // P_q; force pass with <= 2 eta: (P_0, P_1, dP_0/dr, dP_1/dr)
+    float4* ndp;    // dP_q / dr (force pass with > 2 eta)
     float2* nfe;    // (f_c, element) (descriptor pass)
-    float* sg;      // g accumulators, 3 per neighbour (force)
+    int* sgh;       // g accumulators, 3 per neighbour, fixed point: hi words (force)
+    int* sgl;       //   and lo words
     unsigned short* queue;   // live pairs of the current block
     short* cmap;    // compact index of each list slot, -1 outside the cutoff (force)
 };
@@ -94,9 +95,43 @@ __host__ __device__ inline size_t sf_warp_bytes(int C)
 {
     return (size_t)C * (16 + 4 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2;
 }
-__host__ __device__ inline size_t force_warp_bytes(int C, int S)
+// PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).
+__host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack)
 {
-    return (size_t)C * (16 + 16 + 16 + 12) + PAIR_QUEUE * 2 + NNP_MAXG * 4 + (size_t)S * 2;
+    return (size_t)C * (16 + (pack ? 16 : 32) + 24) + PAIR_QUEUE * 2 + NNP_MAXG * 4 + (size_t)S * 2;
+}
+
+// Fixed-point accumulation of the force pass.  A contribution v, |v| < FX_LIMIT
+// eV/A, is split exactly into hi = round(v 2^10) and lo = round((v - hi 2^-10) 2^31)
+// (the remainder is a float difference of nearby values, so it is exact), and each
+// part is added into its own int32 word with a native shared-memory integer atomic.
+// Per add |hi|, |lo| <= 2^20, so the up to 1024 adds a neighbour receives (list
+// stride <= 1024) cannot overflow either word; the only rounding is 2^-32 eV/A
+// per add, and the sums do not depend on the order of the adds.
+#define FX_LIMIT 1024.0f
+__device__ __forceinline__ void fx_split(float v, int& hi, int& lo)
+{
+    hi = __float2int_rn(v * 1024.0f);
+    const float r = fmaf((float)hi, -1.0f / 1024.0f, v);
+    lo = __float2int_rn(r * 2147483648.0f);
+}
+__device__ __forceinline__ void fx_set(const WarpSmem& w, int idx, float v)
+{
+    int hi, lo;
+    fx_split(v, hi, lo);
+    w.sgh[idx] = hi;
+    w.sgl[idx] = lo;
+}
+__device__ __forceinline__ void fx_add(const WarpSmem& w, int idx, float v)
+{
+    int hi, lo;
+    fx_split(v, hi, lo);
+    atomicAdd(&w.sgh[idx], hi);
+    atomicAdd(&w.sgl[idx], lo);
+}
+__device__ __forceinline__ float fx_get(const WarpSmem& w, int idx)
+{
+    return fmaf((float)w.sgl[idx], 1.0f / 2147483648.0f, (float)w.sgh[idx] * (1.0f / 1024.0f));
 }
 
 // Stages the neighbours of atom i within the cutoff, compacted in list order.
@@ -146,14 +181,19 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                 pq[q] = ex * fc;
                 dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
             }
-            w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
             if (!FORCE) {
+                w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
                 w.nd[at] = make_float4(dx, dy, dz, r);
                 w.ninv[at] = ir;
                 w.nfe[at] = make_float2(fc, __int_as_float(ej));
             } else {
                 w.nd[at] = make_float4(dx, dy, dz, ir);
-                w.ndp[at] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+                if (NETA <= 2) {
+                    w.npf[at] = make_float4(pq[0], pq[1], dq[0], dq[1]);
+                } else {
+                    w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
+                    w.ndp[at] = make_float4(dq[0], dq[1], dq[2], dq[3]);
+                }
                 // radial part of g_ij: sum over radial descriptors of dE/dG * dG/dr * d / r
                 float gr = 0.f;
                 for (int rr = 0; rr < E.n_rad; ++rr) {
@@ -165,9 +205,10 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                     }
                 }
                 const float gs = gr * ir;
-                w.sg[3 * at + 0] = gs * dx;
-                w.sg[3 * at + 1] = gs * dy;
-                w.sg[3 * at + 2] = gs * dz;
+                if (!(fabsf(gs) * P.rc < FX_LIMIT)) atomicOr(&flags[FLAG_ERR], ERR_RANGE);
+                fx_set(w, 3 * at + 0, gs * dx);
+                fx_set(w, 3 * at + 1, gs * dy);
+                fx_set(w, 3 * at + 2, gs * dz);
             }
         }
         M += __popc(m);
@@ -269,7 +310,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     w.nfe = reinterpret_cast<float2*>(w.ninv + C);
     w.queue = reinterpret_cast<unsigned short*>(w.nfe + C);
     w.ndp = nullptr;
-    w.sg = nullptr;
+    w.sgh = nullptr;
+    w.sgl = nullptr;
     w.cmap = nullptr;
 
     unsigned long long c_list = 0, c_rc = 0, c_pairs = 0, c_trip = 0, c_max = 0, c_maxrc = 0, c_spill = 0;
@@ -443,13 +485,18 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     const Plan& P = *plan_g;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    unsigned char* base = smem + force_warp_bytes(C, nv.stride) * wib;
+    constexpr bool PACK = NETA <= 2;
+    unsigned char* base = smem + force_warp_bytes(C, nv.stride, PACK) * wib;
     WarpSmem w;
     w.nd = reinterpret_cast<float4*>(base);
     w.npf = w.nd + C;
-    w.ndp = w.npf + C;
-    w.sg = reinterpret_cast<float*>(w.ndp + C);
-    float* sW = w.sg + 3 * C;
+    w.ndp = PACK ? nullptr : w.npf + C;
+    w.sgh = reinterpret_cast<int*>(w.npf + (PACK ? C : 2 * C));
+    w.sgl = w.sgh + 3 * C;
+    float* sW = reinterpret_cast<float*>(w.sgl + 3 * C);
+    // |g| <= (|c_a| + |c_ab| + |c_b| + |c_d|) 2 r_c bounds every triplet contribution
+    const float fx_bound = 0.5f * FX_LIMIT / P.rc;
+    bool fx_bad = false;
     w.queue = reinterpret_cast<unsigned short*>(sW + NNP_MAXG);
     w.cmap = reinterpret_cast<short*>(w.queue + PAIR_QUEUE);
     w.ninv = nullptr;
@@ -506,9 +553,19 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             const int j = 32 * A + l, k = 32 * B + ((l + s) & 31);
                             const float4 a = w.nd[j], b = w.nd[k];
                             const float ia = a.w, ib = b.w;
-                            const float4 pa4 = w.npf[j], qa4 = w.ndp[j], pb4 = w.npf[k], qb4 = w.ndp[k];
-                            const float pav[4] = {pa4.x, pa4.y, pa4.z, pa4.w}, qav[4] = {qa4.x, qa4.y, qa4.z, qa4.w};
-                            const float pbv[4] = {pb4.x, pb4.y, pb4.z, pb4.w}, qbv[4] = {qb4.x, qb4.y, qb4.z, qb4.w};
+                            float pav[4], qav[4], pbv[4], qbv[4];
+                            if (PACK) {
+                                const float4 pa4 = w.npf[j], pb4 = w.npf[k];
+                                pav[0] = pa4.x; pav[1] = pa4.y; qav[0] = pa4.z; qav[1] = pa4.w;
+                                pbv[0] = pb4.x; pbv[1] = pb4.y; qbv[0] = pb4.z; qbv[1] = pb4.w;
+                                pav[2] = pav[3] = qav[2] = qav[3] = pbv[2] = pbv[3] = qbv[2] = qbv[3] = 0.f;
+                            } else {
+                                const float4 pa4 = w.npf[j], qa4 = w.ndp[j], pb4 = w.npf[k], qb4 = w.ndp[k];
+                                pav[0] = pa4.x; pav[1] = pa4.y; pav[2] = pa4.z; pav[3] = pa4.w;
+                                qav[0] = qa4.x; qav[1] = qa4.y; qav[2] = qa4.z; qav[3] = qa4.w;
+                                pbv[0] = pb4.x; pbv[1] = pb4.y; pbv[2] = pb4.z; pbv[3] = pb4.w;
+                                qbv[0] = qb4.x; qbv[1] = qb4.y; qbv[2] = qb4.z; qbv[3] = qb4.w;
+                            }
                             const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
                             const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * (ia * ib);
                             float fcd = 1.f, dfcd = 0.f, rd2 = 0.f, rd = 1.f, ird = 0.f;
@@ -568,12 +625,13 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             const float ca = phia * ia - phic * c * ia * ia;
                             const float cb = phib * ib - phic * c * ib * ib;
                             const float cd = NARROW ? phid * ird : 0.f;
-                            atomicAdd(&w.sg[3 * j + 0], ca * a.x + cab * b.x - cd * ex);
-                            atomicAdd(&w.sg[3 * j + 1], ca * a.y + cab * b.y - cd * ey);
-                            atomicAdd(&w.sg[3 * j + 2], ca * a.z + cab * b.z - cd * ez);
-                            atomicAdd(&w.sg[3 * k + 0], cb * b.x + cab * a.x + cd * ex);
-                            atomicAdd(&w.sg[3 * k + 1], cb * b.y + cab * a.y + cd * ey);
-                            atomicAdd(&w.sg[3 * k + 2], cb * b.z + cab * a.z + cd * ez);
+                            fx_bad |= !(fabsf(ca) + fabsf(cab) + fabsf(cb) + fabsf(cd) < fx_bound);
+                            fx_add(w, 3 * j + 0, ca * a.x + cab * b.x - cd * ex);
+                            fx_add(w, 3 * j + 1, ca * a.y + cab * b.y - cd * ey);
+                            fx_add(w, 3 * j + 2, ca * a.z + cab * b.z - cd * ez);
+                            fx_add(w, 3 * k + 0, cb * b.x + cab * a.x + cd * ex);
+                            fx_add(w, 3 * k + 1, cb * b.y + cab * a.y + cd * ey);
+                            fx_add(w, 3 * k + 2, cb * b.z + cab * a.z + cd * ez);
                         }
                     }
                     __syncwarp();
@@ -586,7 +644,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         float4* grow = gbuf + (size_t)i * nv.stride;
         for (int s = lane; s < cnt; s += 32) {
             const int c = w.cmap[s];
-            grow[s] = (c >= 0) ? make_float4(w.sg[3 * c], w.sg[3 * c + 1], w.sg[3 * c + 2], 0.f)
+            grow[s] = (c >= 0) ? make_float4(fx_get(w, 3 * c), fx_get(w, 3 * c + 1), fx_get(w, 3 * c + 2), 0.f)
                                : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         float fx = 0.f, fy = 0.f, fz = 0.f, v[9];
@@ -594,7 +652,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         for (int q = 0; q < 9; ++q) v[q] = 0.f;
         for (int m = lane; m < M; m += 32) {
             const float4 d = w.nd[m];
-            const float gx = w.sg[3 * m], gy = w.sg[3 * m + 1], gz = w.sg[3 * m + 2];
+            const float gx = fx_get(w, 3 * m), gy = fx_get(w, 3 * m + 1), gz = fx_get(w, 3 * m + 2);
             fx += gx; fy += gy; fz += gz;
             v[0] -= d.x * gx; v[1] -= d.x * gy; v[2] -= d.x * gz;
             v[3] -= d.y * gx; v[4] -= d.y * gy; v[5] -= d.y * gz;
@@ -606,6 +664,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         if (lane == 0) Fown[i] = make_float4(fx, fy, fz, 0.f);
         __syncwarp();
     }
+    if (__any_sync(FULL, fx_bad) && lane == 0) atomicOr(&flags[FLAG_ERR], ERR_RANGE);
     if (lane == 0) {
         const int gw = blockIdx.x * wpb + wib;
 #pragma unroll

@@ -324,7 +324,10 @@ static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
 }
 
 static size_t sf_smem_per_warp(int cap) { return sf_warp_bytes(cap); }
-static size_t force_smem_per_warp(int cap, int stride) { return force_warp_bytes(cap, stride); }
+static size_t force_smem_per_warp(const Plan& P, int cap, int stride)
+{
+    return force_warp_bytes(cap, stride, P.n_eta_max <= 2);   // the kernels' NETA is n_eta_max
+}
 
 // Shared-memory capacity C of the main descriptor, force and tangent launches:
 // warps per block (at most 4, the kernels' launch bounds), dynamic shared memory
@@ -336,7 +339,7 @@ static int set_capacity(nnp_handle* h, int C)
     ForceKernel kf;
     TangentKernel kt;
     pick_kernels(h->plan, ksf, kf, kt);
-    const size_t ps = sf_smem_per_warp(C), pf = force_smem_per_warp(C, h->stride), pt = tangent_warp_bytes(C);
+    const size_t ps = sf_smem_per_warp(C), pf = force_smem_per_warp(h->plan, C, h->stride), pt = tangent_warp_bytes(C);
     const size_t ms = (size_t)h->max_smem;
     if (ps > ms || pf > ms) return set_err(h, NNP_EINVAL, "shared-memory capacity %d does not fit one block", C);
     h->cap_rc = C;
@@ -546,6 +549,8 @@ static int read_status(nnp_handle* h, cudaStream_t st)
                            "an atom has more than max_neighbors = %d neighbours within cutoff + skin", h->stride);
         if (f & ERR_CELL_OVERFLOW) return set_err(h, NNP_ENEIGH_OVERFLOW, "a cell holds more than %d atoms", CELL_CAP);
         if (f & ERR_RC_OVERFLOW) return set_err(h, NNP_ECUDA, "internal error: wide-capacity pass overflowed");
+        if (f & ERR_RANGE)
+            return set_err(h, NNP_ENONFINITE, "a force contribution is non-finite or exceeds %g eV/A", (double)FX_LIMIT);
         if (f & ERR_CLOSE) return set_err(h, NNP_ENONFINITE, "two atoms are closer than 1e-4 A");
         if (f & ERR_NONFINITE) return set_err(h, NNP_ENONFINITE, "non-finite position/energy/force or invalid element type");
         if (f & ERR_REV) return set_err(h, NNP_ECUDA, "internal error: neighbour list not symmetric");
@@ -848,7 +853,7 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     pick_kernels(P, ksf, kf, kt);
     {
         // wide-capacity pass: capacity = list stride, as many warps as fit (<= 4)
-        const size_t ps = sf_smem_per_warp(h->stride), pf = force_smem_per_warp(h->stride, h->stride);
+        const size_t ps = sf_smem_per_warp(h->stride), pf = force_smem_per_warp(P, h->stride, h->stride);
         if (ps > (size_t)max_smem || pf > (size_t)max_smem) {
             set_err(h, NNP_EINVAL, "max_neighbors = %d needs more shared memory than one block has", h->stride);
             return fail(NNP_EINVAL);
@@ -1439,6 +1444,9 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
         return static_fail(eb, el, NNP_ENEIGH_OVERFLOW,
                            "an atom has more than max_neighbors = %d neighbours within cutoff + skin", S);
     if (hf & ERR_RC_OVERFLOW) return static_fail(eb, el, NNP_ECUDA, "internal error: wide-capacity pass overflowed");
+    if (hf & ERR_RANGE)
+        return static_fail(eb, el, NNP_ENONFINITE, "a force contribution is non-finite or exceeds %g eV/A",
+                           (double)FX_LIMIT);
     if (hf & ERR_CLOSE) return static_fail(eb, el, NNP_ENONFINITE, "two atoms are closer than 1e-4 A");
     if (hf & ERR_NONFINITE)
         return static_fail(eb, el, NNP_ENONFINITE, "non-finite position/energy/force or invalid element type");

@@ -64,7 +64,7 @@ def test_spilled_atoms_match_oracle_and_fresh_handle():
     o2 = fresh.compute(p, t, liq[2])
     assert fresh.stats()["spilled_atoms"] == 0
     assert torch.equal(out["Ei"], o2["Ei"])
-    assert (out["F"] - o2["F"]).abs().max().item() <= 1e-6
+    assert torch.equal(out["F"], o2["F"])   # integer force accumulators: order-independent sums
     # descriptors through the same two passes
     _shrink(nnp, low)
     G, _ = nnp.descriptors(p, t, liq[2])
