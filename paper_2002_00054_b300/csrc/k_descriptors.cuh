@@ -234,16 +234,37 @@ __device__ __forceinline__ unsigned valid_mask(int A, int B, int l, int M)
 }
 
 // Bitmask over s of the contributing partners of lane l's j in block (A, B).
+// A full partner block (32 present) is walked with a fixed, unrolled trip count
+// (s = 1..16 on the diagonal); a partial one by scanning its valid bits.
 template <bool NARROW>
 __device__ __forceinline__ unsigned live_mask(int A, int B, int l, int M, const float4 a, const float4* nd, float rc2)
 {
     unsigned v = valid_mask(A, B, l, M);
     if (!NARROW) return v;
+    const float4* blk = nd + 32 * B;
     unsigned mask = 0u;
+    if (32 * B + 32 <= M) {
+        if (A == B) {
+#pragma unroll
+            for (int s = 1; s <= 16; ++s) {
+                const float4 b = blk[(l + s) & 31];
+                const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+                if (ex * ex + ey * ey + ez * ez < rc2) mask |= 1u << s;
+            }
+        } else {
+#pragma unroll
+            for (int s = 0; s < 32; ++s) {
+                const float4 b = blk[(l + s) & 31];
+                const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
+                if (ex * ex + ey * ey + ez * ez < rc2) mask |= 1u << s;
+            }
+        }
+        return mask & v;
+    }
     while (v) {
         const int s = __ffs(v) - 1;
         v &= v - 1u;
-        const float4 b = nd[32 * B + ((l + s) & 31)];
+        const float4 b = blk[(l + s) & 31];
         const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
         if (ex * ex + ey * ey + ez * ez < rc2) mask |= 1u << s;
     }
