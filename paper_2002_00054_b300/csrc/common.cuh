@@ -59,6 +59,10 @@ struct ElemPlan {
     float rad_rs[NNP_MAXRAD];
     int rad_elem[NNP_MAXRAD];
     int rad_out[NNP_MAXRAD];
+    // radial descriptors are ordered by neighbour element: [0, rad_nall) take every
+    // element, [rad_beg[e], rad_end[e]) only element e
+    int rad_nall;
+    int rad_beg[NNP_MAXE], rad_end[NNP_MAXE];
     int n_eta;
     float ang_eta[NNP_MAXETA];
     float ang_khi[NNP_MAXETA], ang_klo[NNP_MAXETA];   // -eta log2(e) as hi + lo floats

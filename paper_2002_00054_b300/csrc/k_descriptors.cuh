@@ -89,7 +89,12 @@ struct WarpSmem {
     int* sgl;       //   and lo words
     unsigned short* queue;   // live pairs of the current block
     short* cmap;    // compact index of each list slot, -1 outside the cutoff (force)
+    // force pass, during staging only (they share the queue's space): per radial
+    // descriptor (eta log2 e as hi, lo; r_s; -2 eta) and dE/dG of the current atom
+    float4* rtab;
+    float* rw;
 };
+static_assert(NNP_MAXRAD * 20 <= PAIR_QUEUE * 2, "radial table must fit the queue space");
 
 __host__ __device__ inline size_t sf_warp_bytes(int C)
 {
@@ -194,16 +199,17 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                     w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
                     w.ndp[at] = make_float4(dq[0], dq[1], dq[2], dq[3]);
                 }
-                // radial part of g_ij: sum over radial descriptors of dE/dG * dG/dr * d / r
+                // radial part of g_ij: sum over the radial descriptors that take the
+                // neighbour's element of dE/dG * dG/dr * d / r
                 float gr = 0.f;
-                for (int rr = 0; rr < E.n_rad; ++rr) {
-                    const int el = E.rad_elem[rr];
-                    if (el < 0 || el == ej) {
-                        const float x = r - E.rad_rs[rr];
-                        const float ex = gauss2(E.rad_khi[rr], E.rad_klo[rr], x * x);
-                        gr += sW[E.rad_out[rr]] * ex * (dfc - 2.0f * E.rad_eta[rr] * x * fc);
-                    }
-                }
+                auto rad = [&](int rr) {
+                    const float4 t = w.rtab[rr];
+                    const float x = r - t.z;
+                    const float ex = gauss2(t.x, t.y, x * x);
+                    gr += w.rw[rr] * ex * fmaf(t.w * x, fc, dfc);
+                };
+                for (int rr = 0; rr < E.rad_nall; ++rr) rad(rr);
+                for (int rr = E.rad_beg[ej], re = E.rad_end[ej]; rr < re; ++rr) rad(rr);
                 const float gs = gr * ir;
                 if (!(fabsf(gs) * P.rc < FX_LIMIT)) atomicOr(&flags[FLAG_ERR], ERR_RANGE);
                 fx_set(w, 3 * at + 0, gs * dx);
@@ -334,6 +340,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     w.sgh = nullptr;
     w.sgl = nullptr;
     w.cmap = nullptr;
+    w.rtab = nullptr;
+    w.rw = nullptr;
 
     unsigned long long c_list = 0, c_rc = 0, c_pairs = 0, c_trip = 0, c_max = 0, c_maxrc = 0, c_spill = 0;
     const int nw = gridDim.x * wpb;
@@ -520,6 +528,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     bool fx_bad = false;
     w.queue = reinterpret_cast<unsigned short*>(sW + NNP_MAXG);
     w.cmap = reinterpret_cast<short*>(w.queue + PAIR_QUEUE);
+    w.rtab = reinterpret_cast<float4*>(w.queue);
+    w.rw = reinterpret_cast<float*>(w.rtab + NNP_MAXRAD);
     w.ninv = nullptr;
     w.nfe = nullptr;
 
@@ -535,6 +545,11 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         const int ti = __float_as_int(pi.w);
         const ElemPlan& E = P.e[ti];
         for (int s = lane; s < E.n_g; s += 32) sW[s] = dEdG[(size_t)i * P.gs + s];
+        __syncwarp();
+        for (int rr = lane; rr < E.n_rad; rr += 32) {
+            w.rtab[rr] = make_float4(E.rad_khi[rr], E.rad_klo[rr], E.rad_rs[rr], -2.0f * E.rad_eta[rr]);
+            w.rw[rr] = sW[E.rad_out[rr]];
+        }
         __syncwarp();
         float khi[4], klo[4], etav[4];
 #pragma unroll

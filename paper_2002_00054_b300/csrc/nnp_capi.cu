@@ -265,6 +265,33 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
         E.n_eta = (int)etas.size();
         neta_max = std::max(neta_max, E.n_eta);
         off += ns;
+        {
+            // order the radial descriptors by neighbour element (all-element ones
+            // first); each keeps its output slot rad_out
+            std::vector<int> ord(E.n_rad);
+            for (int r = 0; r < E.n_rad; ++r) ord[r] = r;
+            std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return E.rad_elem[a] < E.rad_elem[b]; });
+            ElemPlan T = E;
+            for (int r = 0; r < E.n_rad; ++r) {
+                const int o = ord[r];
+                E.rad_eta[r] = T.rad_eta[o];
+                E.rad_khi[r] = T.rad_khi[o];
+                E.rad_klo[r] = T.rad_klo[o];
+                E.rad_rs[r] = T.rad_rs[o];
+                E.rad_elem[r] = T.rad_elem[o];
+                E.rad_out[r] = T.rad_out[o];
+            }
+            E.rad_nall = 0;
+            while (E.rad_nall < E.n_rad && E.rad_elem[E.rad_nall] < 0) E.rad_nall++;
+            for (int x = 0; x < NNP_MAXE; ++x) {
+                int b = E.rad_nall;
+                while (b < E.n_rad && E.rad_elem[b] < x) b++;
+                int en = b;
+                while (en < E.n_rad && E.rad_elem[en] == x) en++;
+                E.rad_beg[x] = b;
+                E.rad_end[x] = en;
+            }
+        }
     }
     P.ang_kind = kind;
     P.n_eta_max = neta_max;
