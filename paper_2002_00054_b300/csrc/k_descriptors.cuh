@@ -107,18 +107,18 @@ __host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack)
 }
 
 // Fixed-point accumulation of the force pass.  A contribution v, |v| < FX_LIMIT
-// eV/A, is split exactly into hi = round(v 2^10) and lo = round((v - hi 2^-10) 2^31)
+// eV/A, is split exactly into hi = round(v 2^6) and lo = round((v - hi 2^-6) 2^27)
 // (the remainder is a float difference of nearby values, so it is exact), and each
 // part is added into its own int32 word with a native shared-memory integer atomic.
-// Per add |hi|, |lo| <= 2^20, so the up to 1024 adds a neighbour receives (list
-// stride <= 1024) cannot overflow either word; the only rounding is 2^-32 eV/A
-// per add, and the sums do not depend on the order of the adds.
-#define FX_LIMIT 1024.0f
+// Per add |hi| < 2^21 and |lo| <= 2^20, so the up to 1024 adds a neighbour receives
+// (list stride <= 1024) cannot overflow either word; the only rounding is 2^-28
+// eV/A per add, and the sums do not depend on the order of the adds.
+#define FX_LIMIT 32000.0f
 __device__ __forceinline__ void fx_split(float v, int& hi, int& lo)
 {
-    hi = __float2int_rn(v * 1024.0f);
-    const float r = fmaf((float)hi, -1.0f / 1024.0f, v);
-    lo = __float2int_rn(r * 2147483648.0f);
+    hi = __float2int_rn(v * 64.0f);
+    const float r = fmaf((float)hi, -1.0f / 64.0f, v);
+    lo = __float2int_rn(r * 134217728.0f);
 }
 __device__ __forceinline__ void fx_set(const WarpSmem& w, int idx, float v)
 {
@@ -136,7 +136,7 @@ __device__ __forceinline__ void fx_add(const WarpSmem& w, int idx, float v)
 }
 __device__ __forceinline__ float fx_get(const WarpSmem& w, int idx)
 {
-    return fmaf((float)w.sgl[idx], 1.0f / 2147483648.0f, (float)w.sgh[idx] * (1.0f / 1024.0f));
+    return fmaf((float)w.sgl[idx], 1.0f / 134217728.0f, (float)w.sgh[idx] * (1.0f / 64.0f));
 }
 
 // Stages the neighbours of atom i within the cutoff, compacted in list order.
@@ -523,9 +523,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     w.sgh = reinterpret_cast<int*>(w.npf + (PACK ? C : 2 * C));
     w.sgl = w.sgh + 3 * C;
     float* sW = reinterpret_cast<float*>(w.sgl + 3 * C);
-    // |g| <= (|c_a| + |c_ab| + |c_b| + |c_d|) 2 r_c bounds every triplet contribution
-    const float fx_bound = 0.5f * FX_LIMIT / P.rc;
-    bool fx_bad = false;
+    bool fx_bad = false;   // a contribution outside the fixed-point range (or not finite)
     w.queue = reinterpret_cast<unsigned short*>(sW + NNP_MAXG);
     w.cmap = reinterpret_cast<short*>(w.queue + PAIR_QUEUE);
     w.rtab = reinterpret_cast<float4*>(w.queue);
@@ -657,11 +655,16 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             }
                             // g_a = phic (b/(ra rb) - c a/ra^2) + phia a/ra - phid (b - a)/rd
                             // g_b = phic (a/(ra rb) - c b/rb^2) + phib b/rb + phid (b - a)/rd
-                            const float cab = phic * ia * ib;
-                            const float ca = phia * ia - phic * c * ia * ia;
-                            const float cb = phib * ib - phic * c * ib * ib;
+                            const float pc = phic * c;
+                            const float ua = fmaf(-pc, ia, phia), ub = fmaf(-pc, ib, phib);
+                            const float ta = phic * ia, tb = phic * ib;
+                            const float cab = ta * ib;
+                            const float ca = ua * ia, cb = ub * ib;
                             const float cd = NARROW ? phid * ird : 0.f;
-                            fx_bad |= !(fabsf(ca) + fabsf(cab) + fabsf(cb) + fabsf(cd) < fx_bound);
+                            // every component of g_a is at most |u_a| + |phic / ra| + |phid| (|a| = ra,
+                            // |e| = rd); likewise for g_b
+                            fx_bad |= !(fabsf(ua) + fabsf(ta) + fabsf(phid) < FX_LIMIT &&
+                                        fabsf(ub) + fabsf(tb) + fabsf(phid) < FX_LIMIT);
                             fx_add(w, 3 * j + 0, ca * a.x + cab * b.x - cd * ex);
                             fx_add(w, 3 * j + 1, ca * a.y + cab * b.y - cd * ey);
                             fx_add(w, 3 * j + 2, ca * a.z + cab * b.z - cd * ez);

@@ -120,3 +120,25 @@ def test_spilled_atoms_in_static_entry():
     ref = oracle.compute(m, *liq)
     check({"Ei": ei, "F": f, "energy": e}, ref, what="static entry with spilled atoms")
     assert np.abs(f.double().cpu().numpy() - ref["F"]).max() <= F_ABS
+
+
+def test_force_contribution_out_of_range_is_an_error():
+    """Force contributions are summed in fixed point (|v| < 32000 eV/A per
+    contribution); a model whose forces exceed that range fails the call with
+    NNP_ENONFINITE instead of returning wrapped sums."""
+    from paper_2002_00054_b300 import NNP
+    from paper_2002_00054_b300._capi import NNPError
+    m = workloads.water_model()
+    w = [x.copy() for x in m["weights"]]
+    for x in w:
+        x[-26:-1] *= 1e7   # output-layer weights (25 of them, then the bias)
+    big = dict(m, weights=w)
+    nnp = NNP(big)
+    pos, types, box = workloads.water_random()
+    p, t = to_dev(f32(pos), types)
+    with pytest.raises(NNPError, match="exceeds"):
+        nnp.compute(p, t, f32(box))
+    # the handle stays usable: the same system with the unscaled model's weights
+    nnp.set_weights(torch.tensor(np.concatenate(m["weights"]), dtype=torch.float32, device="cuda"))
+    out = nnp.compute(p, t, f32(box))
+    check(out, oracle.compute(m, f32(pos), types, f32(box)), what="after a range error")
