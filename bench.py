@@ -45,10 +45,14 @@ WORKLOADS = {
 # FP32 peak from unit counts and clock: 148 SMs x 128 FP32 lanes x 2 flops x 2032 MHz.
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2032e6 / 1e12
 MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
-# DRAM traffic per atom-evaluation of each kernel group from the ncu capture
-# summarised in profiles/ (filled in with the source hash it was taken at).
-TRAFFIC = {}
-TRAFFIC_SRC_SHA = None
+# DRAM bytes (read + write) per atom-evaluation of each kernel group, from the
+# ncu --set full capture on the 110,592-atom water box summarised in
+# profiles/k_force_k_sf_water_110k.md (a 2M-atom launch moves the same bytes per
+# atom: list rows, positions and the per-slot g buffer all scale with atoms).
+# Valid only for the kernel sources with this hash; otherwise traffic is null.
+TRAFFIC = {"force": (93.566976e6 + 200.399360e6) / 110592, "descriptors": (78.027264e6 + 3.976960e6) / 110592}
+TRAFFIC_SRC_SHA = "17653a9d6093"
+MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
 def src_sha():
@@ -433,8 +437,14 @@ def main():
     traffic = None
     if TRAFFIC_SRC_SHA == sha and dom in TRAFFIC:
         traffic = TRAFFIC[dom] * n
+    hbm = None
+    if traffic is not None and os.path.exists(MEASURED_PEAKS):
+        with open(MEASURED_PEAKS) as f:
+            peak_gbs = json.load(f)["hbm_gbs"]
+        gbs = traffic / (dom_ms / dom_launch * 1e-3) / 1e9
+        hbm = {"achieved_gbs": gbs, "peak_gbs": peak_gbs, "frac": gbs / peak_gbs, "peak_source": "measured"}
     roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic,
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "hbm": hbm,
             "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (unit counts and max clock)",
             "mufu_gops": mu / (dom_ms * 1e-3) / 1e9, "mufu_peak_gops": MUFU_PEAK_GOPS,
             "avg_launch_ms": dom_ms / dom_launch, "launches": dom_launch}
