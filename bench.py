@@ -3,13 +3,20 @@ energy and forces every step, on the 2,064,384-atom water-like workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload water_2m|water_110k|water_1m|fcc_1m] [--no-cpu-baseline]
+                  [--no-bf16] [--no-train] [--no-fcc] [--mode standard|combined]
 
 Prints one JSON line (rank 0).  The timed region is one nnp_step call of K steps
 (device-resident inputs; neighbour-list maintenance included), bracketed by a
 barrier and device synchronisation on both sides, max over ranks.  Each rank
 runs its own copy of the workload (weak scaling, no collective on the data
-path).  --impl reference times the FP64 CPU oracle on a bounded sample of the
-same workload (the reference arm of this build).
+path).  Further legs on the same line: end to end through host buffers (e2e),
+the roofline of the dominant kernel, the BF16 tensor-core network on the same
+workload (bf16_mlp), the force-matching training step (training_step), FP32 and
+BF16 on the 1,048,576-atom FCC crystal with errors against the oracle on the
+4,000-atom FCC box (fcc_precision), and the oracle timed on the host cores
+(cpu_baseline).  --mode combined runs the 1,048,320-atom BF16 autograd NVE run.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the reference arm of this build).
 """
 from __future__ import annotations
 
@@ -117,6 +124,68 @@ def sample_clocks_stop(p, path):
         pass
     return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
             "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline_fcc_box(model):
+    """The oracle (the CPU-baseline leg) on the independent 4,000-atom FCC box
+    (10x10x10 cells, same recipe): one energy + force evaluation timed on the host
+    cores, and its per-atom energies and forces, against which the GPU paths'
+    errors are stated."""
+    import oracle
+    pos, types, box = workloads.fcc((10, 10, 10))
+    pos = np.asarray(pos, np.float32).astype(np.float64)
+    box = np.asarray(box, np.float32).astype(np.float64)
+    types = np.asarray(types, np.int32)
+    cores = oracle.set_threads(0)
+    t0 = time.perf_counter()
+    ref = oracle.compute(model, pos, types, box)
+    el = time.perf_counter() - t0
+    base = {"value": len(pos) / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "4,000-atom FCC box, one E+F evaluation"}
+    return pos, types, box, ref, base
+
+
+def fcc_precision_leg(dev, steps, warmup, with_oracle):
+    """Precision form on the 1,048,576-atom FCC crystal: nnp_step with the FP32
+    network and with the BF16 tensor-core network, and (with the oracle) each
+    path's energy and force error on the 4,000-atom FCC box."""
+    import torch
+    from paper_2002_00054_b300 import NNP
+    model, pos_h, types_h, box, _desc, max_nb = make_workload("fcc_1m")
+    n = len(pos_h)
+    vel_h = workloads.maxwell_boltzmann(types_h, model["masses"]).astype(np.float32)
+    types = torch.from_numpy(types_h).to(dev)
+    res = {"workload": "fcc_1m", "atoms": n, "steps": steps, "warmup": warmup}
+    ref = None
+    if with_oracle:
+        sp, stp, sb, ref, base = cpu_baseline_fcc_box(model)
+        res["oracle_box"] = {"atoms": len(sp), "cpu_baseline": base}
+        sp_d = torch.tensor(sp, dtype=torch.float32, device=dev)
+        st_d = torch.tensor(stp, dtype=torch.int32, device=dev)
+    for prec in ("fp32", "bf16"):
+        h = NNP(model, device=dev.index, precision=prec, max_neighbors=max_nb)
+        p = torch.from_numpy(pos_h).to(dev)
+        v = torch.from_numpy(vel_h).to(dev)
+        h.step(p, v, types, box, DT_FS, warmup)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        h.step(p, v, types, box, DT_FS, steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        r = {"value": n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps}
+        if ref is not None:
+            o = h.compute(sp_d, st_d, sb)
+            dF = o["F"].double().cpu().numpy() - ref["F"]
+            dE = o["Ei"].double().cpu().numpy() - ref["Ei"]
+            r["vs_oracle_4000"] = {"force_rms_ev_per_A": float(np.sqrt(np.mean(dF ** 2))),
+                                   "force_max_ev_per_A": float(np.abs(dF).max()),
+                                   "energy_rms_ev_per_atom": float(np.sqrt(np.mean(dE ** 2))),
+                                   "total_energy_err_ev_per_atom": float(abs(o["energy"].item() - ref["energy"]) / len(sp))}
+        res[prec] = r
+        h.close()
+    return res
 
 
 def cpu_baseline(model_name, budget_s=12.0):
@@ -329,6 +398,7 @@ def main():
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-network leg")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
+    ap.add_argument("--no-fcc", action="store_true", help="skip the FCC precision-form leg")
     ap.add_argument("--mode", default="standard", choices=["standard", "combined"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -491,6 +561,9 @@ def main():
         bf.close()
     if not args.no_train:
         out["training_step"] = training_leg(dev, max(3, args.steps // 2), args.warmup)
+    if not args.no_fcc and args.workload != "fcc_1m":
+        out["fcc_precision"] = fcc_precision_leg(dev, args.steps, args.warmup,
+                                                 rank == 0 and world == 1 and not args.no_cpu_baseline)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model["name"])
     if rank == 0:
