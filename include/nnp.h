@@ -97,9 +97,12 @@ typedef struct {
                                  /* bias b_l [widths[l+1]]; elements back to back     */
     int mlp_precision;           /* nnp_precision                                     */
     int max_neighbors;           /* capacity of one atom's neighbour-list row (entries */
-                                 /* within cutoff + skin), 32..1024; entries within   */
-                                 /* the cutoff alone are limited to max_neighbors *   */
-                                 /* (cutoff / (cutoff + skin))^3 (at least 32)         */
+                                 /* within cutoff + skin), 32..1024; a row above it    */
+                                 /* fails the call (NNP_ENEIGH_OVERFLOW).  It sizes    */
+                                 /* memory only: how many neighbours inside the cutoff */
+                                 /* the kernels stage in shared memory follows the     */
+                                 /* counts seen (nnp_stats.rc_capacity), and atoms     */
+                                 /* above that take a second, wide-capacity pass       */
 } nnp_params;
 
 typedef struct nnp_handle nnp_handle;

@@ -37,7 +37,8 @@
 #define CNT_SPILL 6     // atoms handed to the wide-capacity pass
 #define CNT_PER_CALL 7  // counters [0, CNT_PER_CALL) restart with every API call
 #define CNT_REBUILDS 7
-#define CNT_N 8
+#define CNT_QTOP 8      // pair-queue pool entries claimed by the current evaluation
+#define CNT_N 10
 
 #define LOG2E 1.4426950408889634f
 

@@ -62,6 +62,29 @@ __device__ __forceinline__ int atom_at(int pass, int it, const int* spill)
 {
     return pass ? spill[1 + it] : it;
 }
+// Pair-queue records.  The descriptor pass stores each atom's live-pair queue
+// (every 32 x 32 block, in walk order) so that the force pass does not rebuild
+// it.  Record layout (u16): M, the staging fingerprint (2 words), 0, one total
+// per block pair, then from the next multiple of 8 the entries of each block,
+// each block padded to a multiple of 8 (16-byte vector stores).  Records are
+// 8-entry aligned and addressed by qoff[i] = offset / 8 (QOFF_NONE: not stored;
+// the force pass rebuilds the queue).  Each warp claims chunks of QCHUNK
+// entries of the pool with one atomic; the pool counter also records the
+// demand when the pool is too small.
+#define QOFF_NONE 0xffffffffu
+#define QCHUNK 65536ull
+#define QHDR 4
+__host__ __device__ inline int queue_entries_start(int nb)
+{
+    return (QHDR + nb * (nb + 1) / 2 + 7) & ~7;
+}
+__host__ __device__ inline unsigned long long queue_record_bound(int M)
+{
+    const int nb = (M + 31) / 32;
+    const unsigned long long nbp = (unsigned long long)nb * (nb + 1) / 2;
+    return (unsigned long long)queue_entries_start(nb) + (unsigned long long)M * (M - 1) / 2 + 7 * nbp;
+}
+
 // true when atom i must be skipped by this pass (M > C)
 __device__ __forceinline__ bool over_capacity(int M, int C, int pass, int i, int* spill, bool enqueue, int lane,
                                               int* flags, unsigned long long& c_spill)
@@ -145,10 +168,12 @@ template <int NETA, bool FORCE>
 __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box& bx, const NbView& nv,
                                                const float4* __restrict__ pos4, const Plan& P, const ElemPlan& E,
                                                const float* khi, const float* klo, const float* etav, int C,
-                                               const WarpSmem& w, const float* sW, int lane, int* flags, int& n_list)
+                                               const WarpSmem& w, const float* sW, int lane, int* flags, int& n_list,
+                                               unsigned& sig)
 {
     const int cnt = nv.ncount[i];
     n_list = cnt;
+    sig = 0u;
     const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
     float Lx, Ly, Lz;
     atom_box(nv, bx, i, Lx, Ly, Lz);
@@ -171,6 +196,7 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
             keep = r2 < P.rc2;
         }
         const unsigned m = __ballot_sync(FULL, keep);
+        sig = sig * 0x9e3779b1u + m;   // fingerprint of which list slots were kept
         const int at = M + __popc(m & ((1u << lane) - 1u));
         if (FORCE && s < cnt) w.cmap[s] = (keep && at < C) ? (short)at : (short)-1;
         if (keep && at < C) {
@@ -322,7 +348,8 @@ template <int NETA, bool NARROW, int KP, int KN>
 __global__ void __launch_bounds__(128, 6)
 k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g,
      int C, float* __restrict__ Gs, float* __restrict__ Graw, int* __restrict__ flags,
-     unsigned long long* __restrict__ counters, int* __restrict__ spill, int pass)
+     unsigned long long* __restrict__ counters, int* __restrict__ spill, int pass,
+     unsigned short* __restrict__ qpool, unsigned int* __restrict__ qoff, unsigned long long qcap)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -344,6 +371,9 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     w.rw = nullptr;
 
     unsigned long long c_list = 0, c_rc = 0, c_pairs = 0, c_trip = 0, c_max = 0, c_maxrc = 0, c_spill = 0;
+    // this warp's chunk [qcur, qend) of the queue pool (main pass, when forces follow)
+    unsigned long long qcur = 0, qend = 0;
+    bool qcan = (pass == 0) && (qpool != nullptr);
     const int nw = gridDim.x * wpb;
     const int n_items = atom_count(pass, n, spill);
     for (int it = blockIdx.x * wpb + wib; it < n_items; it += nw) {
@@ -359,9 +389,13 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             klo[q] = (q < E.n_eta) ? E.ang_klo[q] : 0.f;
         }
         int n_list;
+        unsigned sig;
         const int M = stage_neighbors<NETA, false>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, nullptr, lane,
-                                                   flags, n_list);
-        if (over_capacity(M, C, pass, i, spill, true, lane, flags, c_spill)) continue;
+                                                   flags, n_list, sig);
+        if (over_capacity(M, C, pass, i, spill, true, lane, flags, c_spill)) {
+            if (qoff && lane == 0) qoff[i] = QOFF_NONE;
+            continue;
+        }
         // radial: lane <-> descriptor (two neighbour halves when n_rad <= 16), loop over
         // neighbours with broadcast reads; Kahan-compensated sums (they feed
         // G~ = (G - mu)/s with |mu/s| up to ~20)
@@ -404,13 +438,48 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
 #pragma unroll
                     for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[q][l][kk] = 0.f;
             const int nb = (M + 31) >> 5;
+            // where this atom's queue record goes (nullptr: not stored)
+            unsigned short* rec = nullptr;
+            if (qcan) {
+                const unsigned long long need = queue_record_bound(M);
+                if (qend - qcur < need) {
+                    const unsigned long long sz = need > QCHUNK ? need : QCHUNK;
+                    unsigned long long old = 0;
+                    if (lane == 0) old = atomicAdd(&counters[CNT_QTOP], sz);
+                    old = __shfl_sync(FULL, old, 0);
+                    if (old + sz <= qcap) {
+                        qcur = old;
+                        qend = old + sz;
+                    } else {
+                        qcan = false;   // pool full: the remaining atoms are not stored
+                        qcur = qend = 0;
+                    }
+                }
+                if (qcan) rec = qpool + qcur;
+            }
+            if (qoff && lane == 0) qoff[i] = rec ? (unsigned)(qcur >> 3) : QOFF_NONE;
+            if (rec && lane == 0) {
+                rec[0] = (unsigned short)M;
+                rec[1] = (unsigned short)(sig & 0xffffu);
+                rec[2] = (unsigned short)(sig >> 16);
+                rec[3] = 0;
+            }
+            int bp = QHDR, qpos = queue_entries_start(nb);
             for (int A = 0; A < nb; ++A) {
                 const int jl = 32 * A + lane;
                 const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int B = A; B < nb; ++B) {
+                for (int B = A; B < nb; ++B, ++bp) {
                     const unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
                     c_trip += __popc(mask);
                     const int total = enqueue_block(mask, lane, w.queue);
+                    if (rec) {
+                        const int n8 = (total + 7) >> 3;   // 8 entries per 16-byte store
+                        const uint4* src = reinterpret_cast<const uint4*>(w.queue);
+                        uint4* dst = reinterpret_cast<uint4*>(rec + qpos);
+                        for (int v = lane; v < n8; v += 32) dst[v] = src[v];
+                        if (lane == 0) rec[bp] = (unsigned short)total;
+                        qpos += n8 * 8;
+                    }
                     for (int e0 = 0; e0 < total; e0 += 32) {
                         const int e = e0 + lane;
                         if (e < total) {
@@ -471,6 +540,9 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 }
             }
             if (lane == 0) c_pairs += (unsigned long long)M * (M - 1) / 2;
+            if (rec) qcur += (unsigned long long)qpos;   // a multiple of 8
+        } else if (qoff && lane == 0) {
+            qoff[i] = QOFF_NONE;
         }
         __syncwarp();
         for (int s = lane; s < E.n_g; s += 32) {
@@ -504,11 +576,15 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
 // ---------------------------------------------------------------- force pass
 // g[i, slot] = dE_i/dd_ij for each list slot (0 outside the cutoff), Fown[i] =
 // sum_j g_ij (the force on i from its own energy), per-warp virial partials.
-template <int NETA, bool NARROW, int KP, int KN>
+// STORED (main pass): the pair queues come from the descriptor pass's records;
+// an atom without a valid record is appended to the wide-capacity list, whose
+// pass (STORED = false) rebuilds the queue from the live masks.
+template <int NETA, bool NARROW, int KP, int KN, bool STORED>
 __global__ void __launch_bounds__(128, 5)
 k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
-        double* __restrict__ vir_part, int* __restrict__ flags, int* __restrict__ spill, int pass)
+        double* __restrict__ vir_part, int* __restrict__ flags, int* __restrict__ spill, int pass,
+        const unsigned short* __restrict__ qpool, const unsigned int* __restrict__ qoff)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -557,8 +633,9 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             klo[q] = (q < E.n_eta) ? E.ang_klo[q] : 0.f;
         }
         int n_list;
+        unsigned sig;
         const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
-                                                  n_list);
+                                                  n_list, sig);
         if (over_capacity(M, C, pass, i, spill, false, lane, flags, c_spill)) continue;
         if (NETA > 0) {
             // dense weights W[q][l][k] = dE/dG_o * 2^(1-zeta), zeta = 2^k
@@ -573,16 +650,43 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                         W[q][l][kk] = (o >= 0) ? sW[o] * exp2f((float)(1 - (1 << kk))) : 0.f;
                     }
             const int nb = (M + 31) >> 5;
+            // the descriptor pass's queue record, used when this staging reproduces it
+            const unsigned short* rec = nullptr;
+            if (STORED) {
+                const unsigned o = qoff[i];
+                if (o != QOFF_NONE) {
+                    const unsigned short* r = qpool + (size_t)o * 8;
+                    if (r[0] == (unsigned short)M && r[1] == (unsigned short)(sig & 0xffffu) &&
+                        r[2] == (unsigned short)(sig >> 16))
+                        rec = r;
+                }
+                if (!rec) {
+                    if (lane == 0) spill[1 + atomicAdd(spill, 1)] = i;
+                    continue;
+                }
+            }
+            int bp = QHDR, qpos = queue_entries_start(nb);
             for (int A = 0; A < nb; ++A) {
                 const int jl = 32 * A + lane;
                 const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
-                for (int B = A; B < nb; ++B) {
-                    const unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
-                    const int total = enqueue_block(mask, lane, w.queue);
+                for (int B = A; B < nb; ++B, ++bp) {
+                    int total;
+                    const unsigned short* qsrc;
+                    if (STORED) {
+                        total = rec[bp];
+                        qsrc = rec + qpos;
+                        qpos += (total + 7) & ~7;
+                    } else {
+                        const unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
+                        total = enqueue_block(mask, lane, w.queue);
+                        qsrc = w.queue;
+                    }
+                    int ent_next = (lane < total) ? qsrc[lane] : 0;
                     for (int e0 = 0; e0 < total; e0 += 32) {
                         const int e = e0 + lane;
+                        const int ent = ent_next;
+                        ent_next = (e + 32 < total) ? qsrc[e + 32] : 0;
                         if (e < total) {
-                            const int ent = w.queue[e];
                             const int l = ent & 31, s = ent >> 5;
                             const int j = 32 * A + l, k = 32 * B + ((l + s) & 31);
                             const float4 a = w.nd[j], b = w.nd[k];

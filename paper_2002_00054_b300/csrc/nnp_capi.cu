@@ -126,6 +126,11 @@ struct nnp_handle {
     // counters read back with the status; evaluations in the current call
     unsigned long long* h_cnt = nullptr;
     int evals = 0;
+    // pair-queue records written by the descriptor pass for the force pass
+    unsigned short* qpool = nullptr;
+    size_t cap_qpool = 0;      // entries allocated
+    size_t want_qpool = 0;     // entries the next evaluation should have (0: estimate)
+    unsigned int* qoff = nullptr;   // [cap_n] record offset / 8 per atom
 };
 
 static thread_local std::string g_create_err;
@@ -301,18 +306,19 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
 
 // --------------------------------------------------------------- dispatch
 typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, float*, float*, int*, unsigned long long*,
-                         int*, int);
+                         int*, int, unsigned short*, unsigned int*, unsigned long long);
 typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
-                            double*, int*, int*, int);
+                            double*, int*, int*, int, const unsigned short*, const unsigned int*);
 
 typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*, int*, int);
 
 template <int NETA, bool NARROW, int KP, int KN>
-static void pick(SfKernel& s, ForceKernel& f, TangentKernel& t)
+static void pick(SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs)
 {
     s = k_sf<NETA, NARROW, KP, KN>;
-    f = k_force<NETA, NARROW, KP, KN>;
+    f = k_force<NETA, NARROW, KP, KN, false>;
     t = k_tangent<NETA, NARROW, KP, KN>;
+    fs = k_force<NETA, NARROW, KP, KN, true>;
 }
 
 // Largest k (zeta = 2^k) used with lambda = +1 (l = 0) or -1 (l = 1), -1 if none.
@@ -330,19 +336,24 @@ static int kmax_of(const Plan& P, int l)
 // eta, lambda +1 up to zeta 16, lambda -1 up to zeta 4) and FCC-like (wide,
 // three eta, both lambda up to zeta 16) models; every other set runs the
 // generic instantiation with all powers up to zeta 16.
-static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t)
+static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs)
 {
     const bool nar = (P.ang_kind == NNP_SF_ANG_NARROW);
     const int kp = kmax_of(P, 0), kn = kmax_of(P, 1);
-    if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f, t); return; }
-    if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f, t); return; }
+    if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f, t, fs); return; }
+    if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f, t, fs); return; }
     switch (P.n_eta_max) {
-    case 0: pick<0, false, 4, 4>(s, f, t); break;
-    case 1: if (nar) pick<1, true, 4, 4>(s, f, t); else pick<1, false, 4, 4>(s, f, t); break;
-    case 2: if (nar) pick<2, true, 4, 4>(s, f, t); else pick<2, false, 4, 4>(s, f, t); break;
-    case 3: if (nar) pick<3, true, 4, 4>(s, f, t); else pick<3, false, 4, 4>(s, f, t); break;
-    default: if (nar) pick<4, true, 4, 4>(s, f, t); else pick<4, false, 4, 4>(s, f, t); break;
+    case 0: pick<0, false, 4, 4>(s, f, t, fs); break;
+    case 1: if (nar) pick<1, true, 4, 4>(s, f, t, fs); else pick<1, false, 4, 4>(s, f, t, fs); break;
+    case 2: if (nar) pick<2, true, 4, 4>(s, f, t, fs); else pick<2, false, 4, 4>(s, f, t, fs); break;
+    case 3: if (nar) pick<3, true, 4, 4>(s, f, t, fs); else pick<3, false, 4, 4>(s, f, t, fs); break;
+    default: if (nar) pick<4, true, 4, 4>(s, f, t, fs); else pick<4, false, 4, 4>(s, f, t, fs); break;
     }
+}
+static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t)
+{
+    ForceKernel fs;
+    pick_kernels(P, s, f, t, fs);
 }
 static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
 {
@@ -409,6 +420,10 @@ static void retune_capacity(nnp_handle* h)
         const int old = h->cap_rc;
         if (set_capacity(h, C) != NNP_OK) set_capacity(h, old);
     }
+    // queue pool: the last evaluation's demand (chunks claimed, including the
+    // claims that did not fit) plus a quarter
+    const size_t demand = (size_t)h->h_cnt[CNT_QTOP];
+    if (demand > h->cap_qpool) h->want_qpool = demand + demand / 4;
 }
 
 // ------------------------------------------------------------------ scratch
@@ -448,6 +463,7 @@ static int ensure_atoms(nnp_handle* h, int n)
     CK(h, regrow(h->sys_of, cap));
     CK(h, regrow(h->T, (size_t)cap * h->plan.gs));
     CK(h, regrow(h->spill, (size_t)cap + 1));
+    CK(h, regrow(h->qoff, cap));
     h->bt_start.clear();
     h->cap_n = cap;
     h->list_valid = false;
@@ -475,6 +491,21 @@ static int ensure_red(nnp_handle* h, int ne, int nv)
         CK(h, regrow(h->vpart, (size_t)nv * 9));
         h->cap_vpart = nv;
     }
+    return NNP_OK;
+}
+
+// Queue pool for an evaluation of n atoms: the size the last call asked for, or
+// on first use half the records' upper bound at the current capacity.
+static int ensure_qpool(nnp_handle* h, int n)
+{
+    size_t want = h->want_qpool;
+    if (want == 0) want = (size_t)n * (queue_record_bound(h->cap_rc) / 2);
+    if (want <= h->cap_qpool) return NNP_OK;
+    if (h->qpool) cudaFree(h->qpool);
+    h->qpool = nullptr;
+    h->cap_qpool = 0;
+    CK(h, cudaMalloc((void**)&h->qpool, want * sizeof(unsigned short)));
+    h->cap_qpool = want;
     return NNP_OK;
 }
 
@@ -713,16 +744,27 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     }
     SfKernel ksf;
     ForceKernel kf;
-    pick_kernels(P, ksf, kf);
+    TangentKernel kt_unused;
+    ForceKernel kfs;
+    pick_kernels(P, ksf, kf, kt_unused, kfs);
     h->evals++;
     {
+        // the force pass follows: store the pair queues for it
+        const bool store = (stop_after == 0) && P.n_eta_max > 0;
+        if (store) {
+            rc = ensure_qpool(h, n);
+            if (rc) return rc;
+            CK(h, cudaMemsetAsync(h->counters + CNT_QTOP, 0, sizeof(unsigned long long), st));
+        }
         KScope ks(h, KG_SF, st, 2);
         CK(h, cudaMemsetAsync(h->spill, 0, sizeof(int), st));
         const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
         ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->G, G_out, h->flags,
-                                                     h->counters, h->spill, 0);
+                                                     h->counters, h->spill, 0, store ? h->qpool : nullptr,
+                                                     store ? h->qoff : nullptr, (unsigned long long)h->cap_qpool);
         ksf<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride, h->G, G_out,
-                                                                 h->flags, h->counters, h->spill, 1);
+                                                                 h->flags, h->counters, h->spill, 1, nullptr, nullptr,
+                                                                 0ull);
     }
     if (stop_after == 1 && !dEdG_out) return read_status(h, st);
     if (h->precision == NNP_BF16) {
@@ -751,12 +793,15 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     if (rc) return rc;
     {
         KScope ks(h, KG_FORCE, st, 2);
-        kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf,
-                                                         h->Fown, h->vpart, h->flags, h->spill, 0);
+        // main pass over the stored queues (atoms without one join the wide pass)
+        const bool stored = P.n_eta_max > 0 && h->qpool;
+        (stored ? kfs : kf)<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
+            n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, h->vpart, h->flags, h->spill, 0,
+            stored ? h->qpool : nullptr, stored ? h->qoff : nullptr);
         kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride,
                                                                        h->dEdG, h->gbuf, h->Fown,
                                                                        h->vpart + (size_t)nvp_main * 9, h->flags,
-                                                                       h->spill, 1);
+                                                                       h->spill, 1, nullptr, nullptr);
     }
     {
         KScope ks(h, KG_GATHER, st);
@@ -900,6 +945,13 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     // raise it to the device maximum (never lower it to this handle's need).
     CKC(cudaFuncSetAttribute((const void*)ksf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     CKC(cudaFuncSetAttribute((const void*)kf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    {
+        SfKernel s3;
+        ForceKernel f3, fs3;
+        TangentKernel t3;
+        pick_kernels(P, s3, f3, t3, fs3);
+        CKC(cudaFuncSetAttribute((const void*)fs3, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    }
     CKC(cudaFuncSetAttribute((const void*)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     CKC(cudaFuncSetAttribute((const void*)k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     if (h->precision == NNP_BF16) {
@@ -958,7 +1010,8 @@ int nnp_destroy(nnp_handle* h)
                    h->epart, h->vpart, h->d_energy, h->d_log, h->flags, h->counters, h->sys_box};
     for (void* p : dev)
         if (p) cudaFree(p);
-    for (void* p2 : {(void*)h->sys_of, (void*)h->sys_start_d, (void*)h->T, (void*)h->gpart, (void*)h->spill})
+    for (void* p2 : {(void*)h->sys_of, (void*)h->sys_start_d, (void*)h->T, (void*)h->gpart, (void*)h->spill,
+                     (void*)h->qpool, (void*)h->qoff})
         if (p2) cudaFree(p2);
     if (h->pos_cache) cudaFree(h->pos_cache);
     if (h->types_cache) cudaFree(h->types_cache);
@@ -1449,15 +1502,15 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     pick_kernels(P, ksf, kf);
     const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
     ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, G, nullptr, flags, counters,
-                                                 spill, 0);
+                                                 spill, 0, nullptr, nullptr, 0ull);
     ksf<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, G, nullptr, flags, counters,
-                                                             spill, 1);
+                                                             spill, 1, nullptr, nullptr, 0ull);
     const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
     k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
     kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, vpart,
-                                                     flags, spill, 0);
+                                                     flags, spill, 0, nullptr, nullptr);
     kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, dEdG, gbuf, Fown,
-                                                                   vpart + (size_t)nvp_main * 9, flags, spill, 1);
+                                                                   vpart + (size_t)nvp_main * 9, flags, spill, 1, nullptr, nullptr);
     k_gather<<<rows_grid, 256, 0, st>>>(n, nv, rev, gbuf, Fown, forces ? forces : Fs, flags);
     k_sum_partial<<<gred, T, 0, st>>>(n, Ei, epart, flags);
     k_finalize<<<1, 256, 0, st>>>(gred, epart, energy, nvp, vpart, nullptr);
