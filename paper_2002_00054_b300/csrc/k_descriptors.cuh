@@ -370,10 +370,14 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     w.rtab = nullptr;
     w.rw = nullptr;
 
-    unsigned long long c_list = 0, c_rc = 0, c_pairs = 0, c_trip = 0, c_max = 0, c_maxrc = 0, c_spill = 0;
-    // this warp's chunk [qcur, qend) of the queue pool (main pass, when forces follow)
-    unsigned long long qcur = 0, qend = 0;
-    bool qcan = (pass == 0) && (qpool != nullptr);
+    // work counters, one per lane: lane 0 list entries, 1 cutoff entries, 2 pairs,
+    // 3 largest row, 4 largest cutoff row; triplets per lane, spills in lane 0
+    unsigned long long cnt = 0, c_spill = 0;
+    unsigned c_trip = 0;
+    // this warp's chunk [qcur, qend) of the queue pool, in units of 8 entries
+    // (main pass, when forces follow)
+    unsigned qcur = 0, qend = 0;
+    bool qcan = NARROW && (pass == 0) && (qpool != nullptr);   // wide queues are not stored
     const int nw = gridDim.x * wpb;
     const int n_items = atom_count(pass, n, spill);
     for (int it = blockIdx.x * wpb + wib; it < n_items; it += nw) {
@@ -440,24 +444,24 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             const int nb = (M + 31) >> 5;
             // where this atom's queue record goes (nullptr: not stored)
             unsigned short* rec = nullptr;
-            if (qcan) {
-                const unsigned long long need = queue_record_bound(M);
-                if (qend - qcur < need) {
-                    const unsigned long long sz = need > QCHUNK ? need : QCHUNK;
+            if (NARROW && qcan) {
+                const unsigned need8 = (unsigned)((queue_record_bound(M) + 7) >> 3);
+                if (qend - qcur < need8) {
+                    const unsigned long long sz = (need8 > QCHUNK / 8 ? need8 : QCHUNK / 8) * 8ull;
                     unsigned long long old = 0;
                     if (lane == 0) old = atomicAdd(&counters[CNT_QTOP], sz);
                     old = __shfl_sync(FULL, old, 0);
-                    if (old + sz <= qcap) {
-                        qcur = old;
-                        qend = old + sz;
+                    if (old + sz <= qcap && old + sz < (8ull << 32)) {
+                        qcur = (unsigned)(old >> 3);
+                        qend = (unsigned)((old + sz) >> 3);
                     } else {
                         qcan = false;   // pool full: the remaining atoms are not stored
                         qcur = qend = 0;
                     }
                 }
-                if (qcan) rec = qpool + qcur;
+                if (qcan) rec = qpool + (size_t)qcur * 8;
             }
-            if (qoff && lane == 0) qoff[i] = rec ? (unsigned)(qcur >> 3) : QOFF_NONE;
+            if (qoff && lane == 0) qoff[i] = rec ? qcur : QOFF_NONE;
             if (rec && lane == 0) {
                 rec[0] = (unsigned short)M;
                 rec[1] = (unsigned short)(sig & 0xffffu);
@@ -539,8 +543,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                     if (o >= 0) sG[o] = tot * (double)exp2f((float)(1 - (1 << kk)));
                 }
             }
-            if (lane == 0) c_pairs += (unsigned long long)M * (M - 1) / 2;
-            if (rec) qcur += (unsigned long long)qpos;   // a multiple of 8
+            if (lane == 2) cnt += (unsigned long long)M * (M - 1) / 2;
+            if (rec) qcur += (unsigned)(qpos >> 3);   // qpos is a multiple of 8
         } else if (qoff && lane == 0) {
             qoff[i] = QOFF_NONE;
         }
@@ -551,24 +555,22 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             if (Graw) Graw[(size_t)i * E.n_g + s] = (float)g;
         }
         __syncwarp();
-        if (lane == 0) {
-            c_list += (unsigned long long)n_list;
-            c_max = max(c_max, (unsigned long long)n_list);
-            c_maxrc = max(c_maxrc, (unsigned long long)M);
-            c_rc += (unsigned long long)M;
-        }
+        if (lane == 0) cnt += (unsigned long long)n_list;
+        if (lane == 1) cnt += (unsigned long long)M;
+        if (lane == 3) cnt = max(cnt, (unsigned long long)n_list);
+        if (lane == 4) cnt = max(cnt, (unsigned long long)M);
     }
-    // counters: one atomic per warp
+    // counters: one atomic per counter and warp
     unsigned long long t = c_trip;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+    if (lane == 0) atomicAdd(&counters[CNT_LIST], cnt);
+    if (lane == 1) atomicAdd(&counters[CNT_RC], cnt);
+    if (lane == 2) atomicAdd(&counters[CNT_PAIRS], cnt);
+    if (lane == 3) atomicMax(&counters[CNT_MAXLIST], cnt);
+    if (lane == 4) atomicMax(&counters[CNT_MAXRC], cnt);
     if (lane == 0) {
-        atomicAdd(&counters[CNT_LIST], c_list);
-        atomicAdd(&counters[CNT_RC], c_rc);
-        atomicAdd(&counters[CNT_PAIRS], c_pairs);
         atomicAdd(&counters[CNT_TRIPLETS], t);
-        atomicMax(&counters[CNT_MAXLIST], c_max);
-        atomicMax(&counters[CNT_MAXRC], c_maxrc);
         if (c_spill) atomicAdd(&counters[CNT_SPILL], c_spill);
     }
 }
@@ -681,12 +683,17 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                         total = enqueue_block(mask, lane, w.queue);
                         qsrc = w.queue;
                     }
-                    int ent_next = (lane < total) ? qsrc[lane] : 0;
+                    // stored queues come from global memory: load one round ahead
+                    int ent_next = (STORED && lane < total) ? qsrc[lane] : 0;
                     for (int e0 = 0; e0 < total; e0 += 32) {
                         const int e = e0 + lane;
-                        const int ent = ent_next;
-                        ent_next = (e + 32 < total) ? qsrc[e + 32] : 0;
+                        int ent;
+                        if (STORED) {
+                            ent = ent_next;
+                            ent_next = (e + 32 < total) ? qsrc[e + 32] : 0;
+                        }
                         if (e < total) {
+                            if (!STORED) ent = qsrc[e];
                             const int l = ent & 31, s = ent >> 5;
                             const int j = 32 * A + l, k = 32 * B + ((l + s) & 31);
                             const float4 a = w.nd[j], b = w.nd[k];

@@ -749,8 +749,10 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     pick_kernels(P, ksf, kf, kt_unused, kfs);
     h->evals++;
     {
-        // the force pass follows: store the pair queues for it
-        const bool store = (stop_after == 0) && P.n_eta_max > 0;
+        // the force pass follows: store the pair queues for it (narrow kind only:
+        // there the live masks cost a distance test per pair; wide queues follow
+        // from the index arithmetic alone and are cheaper to rebuild than to store)
+        const bool store = (stop_after == 0) && P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW;
         if (store) {
             rc = ensure_qpool(h, n);
             if (rc) return rc;
@@ -794,7 +796,7 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     {
         KScope ks(h, KG_FORCE, st, 2);
         // main pass over the stored queues (atoms without one join the wide pass)
-        const bool stored = P.n_eta_max > 0 && h->qpool;
+        const bool stored = P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW && h->qpool;
         (stored ? kfs : kf)<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
             n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, h->vpart, h->flags, h->spill, 0,
             stored ? h->qpool : nullptr, stored ? h->qoff : nullptr);
