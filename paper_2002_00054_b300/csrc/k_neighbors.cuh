@@ -152,10 +152,13 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start, int* 
 
 // Row of atom i from the 27-cell stencil (cells of edge >= cutoff + skin, >= 3 per side).
 // Entry order: stencil order (z, y, x from -1 to 1), then ascending atom index.
+// seg[i][t] (t = 0..26, stencil cell t = (dz+1)*9 + (dy+1)*3 + (dx+1)) is the
+// first slot of row i that came from stencil cell t; seg[i][27] = the row length.
+#define NB_SEG 28
 __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int ncx, int ncy, int ncz,
                             const int* __restrict__ cell_start, const int* __restrict__ cell_atoms,
                             float rcut2, int stride, uint32_t* __restrict__ nbr, int* __restrict__ ncount,
-                            int* __restrict__ flags)
+                            unsigned short* __restrict__ seg, int* __restrict__ flags)
 {
     if (!flags[FLAG_REBUILD]) return;
     const int lane = threadIdx.x & 31;
@@ -173,6 +176,8 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
                     if (y < 0) { y += ncy; sy = -1; } else if (y >= ncy) { y -= ncy; sy = 1; }
                     if (z < 0) { z += ncz; sz = -1; } else if (z >= ncz) { z -= ncz; sz = 1; }
                     const int c = (z * ncy + y) * ncx + x;
+                    if (lane == 0) seg[(size_t)i * NB_SEG + (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] =
+                        (unsigned short)min(cnt, stride);
                     const float ox = (float)sx * box.L[0], oy = (float)sy * box.L[1], oz = (float)sz * box.L[2];
                     const int b0 = cell_start[c], b1 = cell_start[c + 1];
                     for (int base = b0; base < b1; base += 32) {
@@ -196,6 +201,45 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
         if (lane == 0) {
             if (cnt > stride) atomicOr(&flags[FLAG_ERR], ERR_NEIGH_OVERFLOW);
             ncount[i] = min(cnt, stride);
+            seg[(size_t)i * NB_SEG + 27] = (unsigned short)min(cnt, stride);
+        }
+    }
+}
+
+// Reverse index of cell-built rows: if j came from stencil cell t of i's row,
+// i is in stencil cell 26 - t of j's row (with the opposite image), among the
+// few entries of that segment.  One lane per entry.
+__global__ void k_rev_cell(int n, const uint32_t* __restrict__ nbr, const int* __restrict__ ncount, int stride,
+                           const unsigned short* __restrict__ seg, int* __restrict__ rev, int* __restrict__ flags)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+        const int cnt = ncount[i];
+        const uint32_t* row = nbr + (size_t)i * stride;
+        const unsigned short* si = seg + (size_t)i * NB_SEG;
+        const int my_seg = (lane < NB_SEG) ? (int)si[lane] : 0x7fffffff;
+        for (int s0 = 0; s0 < cnt; s0 += 32) {
+            const int s = s0 + lane;
+            // stencil cell of slot s: the last t in 0..26 whose segment starts at or before s
+            int t = 0;
+#pragma unroll
+            for (int u = 1; u < 27; ++u)
+                if (__shfl_sync(FULL, my_seg, u) <= s) t = u;
+            if (s < cnt) {
+                const uint32_t e = row[s];
+                const int j = (int)(e & NB_INDEX_MASK);
+                const uint32_t target = nb_reverse(e, i);
+                const unsigned short* sj = seg + (size_t)j * NB_SEG + (26 - t);
+                const int lo = sj[0], hi = sj[1];
+                const uint32_t* rj = nbr + (size_t)j * stride;
+                int f = -1;
+                for (int r = lo; r < hi; ++r)
+                    if (rj[r] == target) { f = r; break; }
+                if (f < 0) atomicOr(&flags[FLAG_ERR], ERR_REV);
+                rev[(size_t)i * stride + s] = f < 0 ? 0 : f;
+            }
         }
     }
 }

@@ -131,6 +131,7 @@ struct nnp_handle {
     size_t cap_qpool = 0;      // entries allocated
     size_t want_qpool = 0;     // entries the next evaluation should have (0: estimate)
     unsigned int* qoff = nullptr;   // [cap_n] record offset / 8 per atom
+    unsigned short* seg = nullptr;  // [cap_n][NB_SEG] stencil segments of cell-built rows
 };
 
 static thread_local std::string g_create_err;
@@ -453,6 +454,7 @@ static int ensure_atoms(nnp_handle* h, int n)
     CK(h, regrow(h->nbr, rows));
     CK(h, regrow(h->ncount, cap));
     CK(h, regrow(h->rev, rows));
+    CK(h, regrow(h->seg, (size_t)cap * NB_SEG));
     CK(h, regrow(h->gbuf, rows));
     CK(h, regrow(h->cell_of, cap));
     CK(h, regrow(h->cell_atoms, cap));
@@ -723,15 +725,16 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
             k_cell_sort<<<std::min(blocks_for(ncell, 8), h->num_sms * 8), 256, 0, st>>>(ncell, h->cell_start,
                                                                                         h->cell_atoms, h->flags);
             k_rows_cell<<<rows_grid, 256, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_start,
-                                                   h->cell_atoms, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
-            h->launches += 5;
+                                                   h->cell_atoms, P.rcut2, h->stride, h->nbr, h->ncount, h->seg,
+                                                   h->flags);
+            k_rev_cell<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->seg, h->rev, h->flags);
+            h->launches += 6;
         } else {
             k_rows_brute<<<rows_grid, 256, 0, st>>>(n, h->pos4, bt ? h->sys_of : nullptr, bt ? h->sys_start_d : nullptr,
                                                     h->sys_box, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
-            h->launches++;
+            k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
+            h->launches += 2;
         }
-        k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
-        h->launches++;
     }
     h->list_valid = true;
     h->list_n = n;
@@ -1013,7 +1016,7 @@ int nnp_destroy(nnp_handle* h)
     for (void* p : dev)
         if (p) cudaFree(p);
     for (void* p2 : {(void*)h->sys_of, (void*)h->sys_start_d, (void*)h->T, (void*)h->gpart, (void*)h->spill,
-                     (void*)h->qpool, (void*)h->qoff})
+                     (void*)h->qpool, (void*)h->qoff, (void*)h->seg})
         if (p2) cudaFree(p2);
     if (h->pos_cache) cudaFree(h->pos_cache);
     if (h->types_cache) cudaFree(h->types_cache);
