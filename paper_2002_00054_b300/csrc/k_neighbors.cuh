@@ -167,37 +167,60 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
         const float4 pi = pos4[i];
         const int cx = cell_coord(pi.x, box.L[0], ncx), cy = cell_coord(pi.y, box.L[1], ncy),
                   cz = cell_coord(pi.z, box.L[2], ncz);
-        int cnt = 0;
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int x = cx + dx, y = cy + dy, z = cz + dz, sx = 0, sy = 0, sz = 0;
-                    if (x < 0) { x += ncx; sx = -1; } else if (x >= ncx) { x -= ncx; sx = 1; }
-                    if (y < 0) { y += ncy; sy = -1; } else if (y >= ncy) { y -= ncy; sy = 1; }
-                    if (z < 0) { z += ncz; sz = -1; } else if (z >= ncz) { z -= ncz; sz = 1; }
-                    const int c = (z * ncy + y) * ncx + x;
-                    if (lane == 0) seg[(size_t)i * NB_SEG + (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)] =
-                        (unsigned short)min(cnt, stride);
-                    const float ox = (float)sx * box.L[0], oy = (float)sy * box.L[1], oz = (float)sz * box.L[2];
-                    const int b0 = cell_start[c], b1 = cell_start[c + 1];
-                    for (int base = b0; base < b1; base += 32) {
-                        const int p = base + lane;
-                        bool keep = false;
-                        int j = 0;
-                        if (p < b1) {
-                            j = cell_atoms[p];
-                            const float4 pj = pos4[j];
-                            const float ddx = pair_disp(pj.x, pi.x, ox), ddy = pair_disp(pj.y, pi.y, oy),
-                                        ddz = pair_disp(pj.z, pi.z, oz);
-                            const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                            keep = (r2 < rcut2) && !(j == i && sx == 0 && sy == 0 && sz == 0);
-                        }
-                        const unsigned m = __ballot_sync(FULL, keep);
-                        const int at = cnt + __popc(m & ((1u << lane) - 1u));
-                        if (keep && at < stride) nbr[(size_t)i * stride + at] = nb_pack(j, sx, sy, sz);
-                        cnt += __popc(m);
-                    }
-                }
+        // lane t < 27: stencil cell t = (dz+1)*9 + (dy+1)*3 + (dx+1), its atom range
+        // and periodic shift; then an exclusive scan of the cell sizes
+        int b0 = 0, len = 0, code = 62;   // code of shift (0, 0, 0)
+        if (lane < 27) {
+            const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+            int x = cx + dx, y = cy + dy, z = cz + dz, sx = 0, sy = 0, sz = 0;
+            if (x < 0) { x += ncx; sx = -1; } else if (x >= ncx) { x -= ncx; sx = 1; }
+            if (y < 0) { y += ncy; sy = -1; } else if (y >= ncy) { y -= ncy; sy = 1; }
+            if (z < 0) { z += ncz; sz = -1; } else if (z >= ncz) { z -= ncz; sz = 1; }
+            const int c = (z * ncy + y) * ncx + x;
+            b0 = cell_start[c];
+            len = cell_start[c + 1] - b0;
+            code = (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2);
+        }
+        int pre = len;   // inclusive scan over lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, pre, o);
+            if (lane >= o) pre += t;
+        }
+        const int total = __shfl_sync(FULL, pre, 31);
+        pre -= len;   // first flat candidate index of cell `lane`
+        // candidates of all 27 cells in stencil order, 32 per round
+        int cnt = 0, my_seg = 0;
+        for (int f0 = 0; f0 < total; f0 += 32) {
+            const int f = f0 + lane;
+            // cell of candidate f: the last t whose first index is <= f
+            int t = 0;
+#pragma unroll
+            for (int u = 1; u < 27; ++u)
+                if (__shfl_sync(FULL, pre, u) <= f) t = u;
+            const int tb0 = __shfl_sync(FULL, b0, t), tpre = __shfl_sync(FULL, pre, t);
+            const int tcode = __shfl_sync(FULL, code, t);
+            bool keep = false;
+            int j = 0;
+            if (f < total) {
+                j = cell_atoms[tb0 + (f - tpre)];
+                const float4 pj = pos4[j];
+                const int sx = tcode / 25 - 2, sy = (tcode / 5) % 5 - 2, sz = tcode % 5 - 2;
+                const float ox = (float)sx * box.L[0], oy = (float)sy * box.L[1], oz = (float)sz * box.L[2];
+                const float ddx = pair_disp(pj.x, pi.x, ox), ddy = pair_disp(pj.y, pi.y, oy),
+                            ddz = pair_disp(pj.z, pi.z, oz);
+                const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                keep = (r2 < rcut2) && !(j == i && tcode == 62);
+            }
+            const unsigned m = __ballot_sync(FULL, keep);
+            // segment start of cell `lane` (its first candidate falls in this round)
+            if (lane < 27 && pre >= f0 && pre < f0 + 32) my_seg = cnt + __popc(m & ((1u << (pre - f0)) - 1u));
+            const int at = cnt + __popc(m & ((1u << lane) - 1u));
+            if (keep && at < stride) nbr[(size_t)i * stride + at] = (uint32_t)j | ((uint32_t)tcode << 24);
+            cnt += __popc(m);
+        }
+        if (lane < 27 && pre >= total) my_seg = cnt;   // empty trailing cells
+        if (lane < 27) seg[(size_t)i * NB_SEG + lane] = (unsigned short)min(my_seg, stride);
         if (lane == 0) {
             if (cnt > stride) atomicOr(&flags[FLAG_ERR], ERR_NEIGH_OVERFLOW);
             ncount[i] = min(cnt, stride);
@@ -235,8 +258,14 @@ __global__ void k_rev_cell(int n, const uint32_t* __restrict__ nbr, const int* _
                 const int lo = sj[0], hi = sj[1];
                 const uint32_t* rj = nbr + (size_t)j * stride;
                 int f = -1;
-                for (int r = lo; r < hi; ++r)
-                    if (rj[r] == target) { f = r; break; }
+                for (int r0 = lo; r0 < hi && f < 0; r0 += 8) {
+                    uint32_t v[8];   // independent loads (no entry equals 0xffffffff)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) v[u] = (r0 + u < hi) ? rj[r0 + u] : 0xffffffffu;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (f < 0 && v[u] == target) f = r0 + u;
+                }
                 if (f < 0) atomicOr(&flags[FLAG_ERR], ERR_REV);
                 rev[(size_t)i * stride + s] = f < 0 ? 0 : f;
             }
