@@ -55,10 +55,11 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # DRAM bytes (read + write) per atom-evaluation of each kernel group, from the
 # ncu --set full capture on the 110,592-atom water box summarised in
 # profiles/k_force_k_sf_water_110k.md (a 2M-atom launch moves the same bytes per
-# atom: list rows, positions and the per-slot g buffer all scale with atoms).
-# Valid only for the kernel sources with this hash; otherwise traffic is null.
-TRAFFIC = {"force": (93.566976e6 + 200.399360e6) / 110592, "descriptors": (78.027264e6 + 3.976960e6) / 110592}
-TRAFFIC_SRC_SHA = "17653a9d6093"
+# atom: list rows, positions, pair-queue records and the per-slot g buffer all
+# scale with atoms).  Valid only for the kernel sources with this hash;
+# otherwise traffic is null.
+TRAFFIC = {"force": (470.244608e6 + 227.742720e6) / 110592, "descriptors": (84.150016e6 + 328.985088e6) / 110592}
+TRAFFIC_SRC_SHA = "428773ee8c0f"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
