@@ -49,6 +49,7 @@ def main():
                for k, (sg, a) in enumerate((sg, a) for sg in (0.05, 0.1, 0.2) for a in (3.45, 3.52, 3.59))]
     jobs = [
         ("water", workloads.water_model, [workloads.water_random()]),
+        ("water_resolved", lambda: workloads.water_model(resolved=True), [workloads.water_random()]),
         ("fcc", workloads.fcc_model, fcc_set),
     ]
     for name, mk, configs in jobs:

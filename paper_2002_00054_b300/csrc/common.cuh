@@ -9,6 +9,7 @@
 #define NNP_MAXRAD 64   // radial descriptors per element
 #define NNP_MAXETA 4    // distinct angular eta per element
 #define NNP_KMAX 4      // angular zeta = 2^k, k <= NNP_KMAX
+#define NNP_MAXCLS 10   // neighbour-element pair classes of angular descriptors per element
 #define NNP_MAXL 6      // weight layers
 #define NNP_MAXH 32     // hidden width
 
@@ -50,8 +51,10 @@ __device__ __forceinline__ float gauss2(float khi, float klo, float x2)
 }
 
 // Per-element descriptor plan.  Angular functions of one element share one kind
-// and are grouped by eta: ang_out[q][l][k] is the descriptor index of
-// (eta_q, lambda = (l == 0 ? +1 : -1), zeta = 2^k), or -1.
+// and are grouped by neighbour-element pair class c and eta: ang_out[c][q][l][k]
+// is the descriptor index of (class c, eta_q, lambda = (l == 0 ? +1 : -1),
+// zeta = 2^k), or -1.  Class c takes the pairs (j, k) whose elements are
+// {cls_e1[c], cls_e2[c]}; cls_e1[c] = -1 takes every pair.
 struct ElemPlan {
     int n_g;
     int n_rad;
@@ -67,7 +70,9 @@ struct ElemPlan {
     int n_eta;
     float ang_eta[NNP_MAXETA];
     float ang_khi[NNP_MAXETA], ang_klo[NNP_MAXETA];   // -eta log2(e) as hi + lo floats
-    int ang_out[NNP_MAXETA][2][NNP_KMAX + 1];
+    int n_cls;
+    int cls_e1[NNP_MAXCLS], cls_e2[NNP_MAXCLS];
+    int ang_out[NNP_MAXCLS][NNP_MAXETA][2][NNP_KMAX + 1];
     float mu[NNP_MAXG];
     float inv_s[NNP_MAXG];
 };
@@ -76,6 +81,7 @@ struct Plan {
     int n_elem;
     int ang_kind;        // 0 none, 3 narrow, 4 wide (same for every element)
     int n_eta_max;
+    int resolved;        // some angular class is restricted to an element pair
     float rc, rc2, hpi_rc;   // cutoff, cutoff^2, pi / (2 rc)
     float inv_2rc, inv_2rc_lo;   // 1 / (2 rc) as hi + lo floats
     float rcut2;             // (cutoff + skin)^2

@@ -108,6 +108,7 @@ struct WarpSmem {
     float4* npf;    // P_q; force pass with <= 2 eta: (P_0, P_1, dP_0/dr, dP_1/dr)
     float4* ndp;    // dP_q / dr (force pass with > 2 eta)
     float2* nfe;    // (f_c, element) (descriptor pass)
+    unsigned char* nel;   // element of each staged neighbour (force pass, resolved angular)
     int* sgh;       // g accumulators, 3 per neighbour, fixed point: hi words (force)
     int* sgl;       //   and lo words
     unsigned short* queue;   // live pairs of the current block
@@ -124,9 +125,10 @@ __host__ __device__ inline size_t sf_warp_bytes(int C)
     return (size_t)C * (16 + 4 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2;
 }
 // PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).
-__host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack)
+__host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool res)
 {
-    return (size_t)C * (16 + (pack ? 16 : 32) + 24) + PAIR_QUEUE * 2 + NNP_MAXG * 4 + (size_t)S * 2;
+    return (size_t)C * (16 + (pack ? 16 : 32) + 24) + PAIR_QUEUE * 2 + NNP_MAXG * 4 + (size_t)S * 2 +
+           (res ? (size_t)((C + 15) & ~15) : 0);
 }
 
 // Fixed-point accumulation of the force pass.  A contribution v, |v| < FX_LIMIT
@@ -225,6 +227,7 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                     w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
                     w.ndp[at] = make_float4(dq[0], dq[1], dq[2], dq[3]);
                 }
+                if (w.nel) w.nel[at] = (unsigned char)ej;
                 // radial part of g_ij: sum over the radial descriptors that take the
                 // neighbour's element of dE/dG * dG/dr * d / r
                 float gr = 0.f;
@@ -303,6 +306,18 @@ __device__ __forceinline__ unsigned live_mask(int A, int B, int l, int M, const 
     return mask;
 }
 
+// Element-pair class filter: the partners k = 32B + (l + s) mod 32 (bit s) of
+// lane l's j (element ej) whose elements make {e1, e2} with ej.  el_k is the
+// element at this lane's position of block B (-1 past the staged neighbours).
+__device__ __forceinline__ unsigned class_mask(int ej, int el_k, int e1, int e2, int lane)
+{
+    const unsigned m1 = __ballot_sync(FULL, el_k == e1), m2 = __ballot_sync(FULL, el_k == e2);
+    unsigned r = 0u;
+    if (ej == e1) r |= __funnelshift_r(m2, m2, lane);
+    if (ej == e2) r |= __funnelshift_r(m1, m1, lane);
+    return r;
+}
+
 // Transposes the warp's 32 x 32 bit matrix (row = lane): lane s returns column s.
 __device__ __forceinline__ unsigned transpose32(unsigned m, int lane)
 {
@@ -344,7 +359,9 @@ __device__ __forceinline__ int enqueue_block(unsigned mask, int lane, unsigned s
 // ---------------------------------------------------------------- value pass
 // KP / KN: largest k (zeta = 2^k) among the lambda = +1 / -1 functions; powers and
 // terms beyond them are compiled out.
-template <int NETA, bool NARROW, int KP, int KN>
+// RES: angular descriptors resolved by neighbour-element pair (one pass over
+// the pairs per class).
+template <int NETA, bool NARROW, int KP, int KN, bool RES>
 __global__ void __launch_bounds__(128, 6)
 k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g,
      int C, float* __restrict__ Gs, float* __restrict__ Graw, int* __restrict__ flags,
@@ -367,6 +384,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     w.sgh = nullptr;
     w.sgl = nullptr;
     w.cmap = nullptr;
+    w.nel = nullptr;
     w.rtab = nullptr;
     w.rw = nullptr;
 
@@ -430,8 +448,9 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 if (act && hf == 0) sG[E.rad_out[rr]] = tot;
             }
         }
-        // angular
-        if (NETA > 0) {
+        // angular (one pass per neighbour-element pair class)
+        const int ncls = RES ? E.n_cls : 1;
+        for (int cls = 0; NETA > 0 && cls < ncls; ++cls) {
             constexpr int NQ = NETA > 0 ? NETA : 1;
             constexpr int NA = NQ * 2 * (NNP_KMAX + 1);   // dense accumulators, index (q*2 + l)*(KMAX+1) + k
             float acc[NQ][2][NNP_KMAX + 1];
@@ -442,9 +461,10 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
 #pragma unroll
                     for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[q][l][kk] = 0.f;
             const int nb = (M + 31) >> 5;
+            const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             // where this atom's queue record goes (nullptr: not stored)
             unsigned short* rec = nullptr;
-            if (NARROW && qcan) {
+            if (!RES && NARROW && qcan) {
                 const unsigned need8 = (unsigned)((queue_record_bound(M) + 7) >> 3);
                 if (qend - qcur < need8) {
                     const unsigned long long sz = (need8 > QCHUNK / 8 ? need8 : QCHUNK / 8) * 8ull;
@@ -472,9 +492,14 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             for (int A = 0; A < nb; ++A) {
                 const int jl = 32 * A + lane;
                 const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int ej = (RES && jl < M) ? __float_as_int(w.nfe[jl].y) : -1;
                 for (int B = A; B < nb; ++B, ++bp) {
-                    const unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
-                    c_trip += __popc(mask);
+                    unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
+                    if (cls == 0) c_trip += __popc(mask);
+                    if (RES && ce1 >= 0) {
+                        const int kl = 32 * B + lane;
+                        mask &= class_mask(ej, kl < M ? __float_as_int(w.nfe[kl].y) : -1, ce1, ce2, lane);
+                    }
                     const int total = enqueue_block(mask, lane, w.queue);
                     if (rec) {
                         const int n8 = (total + 7) >> 3;   // 8 entries per 16-byte store
@@ -539,15 +564,14 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 const int idx = c0 + lane;
                 if (idx < NA) {
                     const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
-                    const int o = (q < E.n_eta) ? E.ang_out[q][l][kk] : -1;
+                    const int o = (q < E.n_eta) ? E.ang_out[cls][q][l][kk] : -1;
                     if (o >= 0) sG[o] = tot * (double)exp2f((float)(1 - (1 << kk)));
                 }
             }
-            if (lane == 2) cnt += (unsigned long long)M * (M - 1) / 2;
+            if (cls == 0 && lane == 2) cnt += (unsigned long long)M * (M - 1) / 2;
             if (rec) qcur += (unsigned)(qpos >> 3);   // qpos is a multiple of 8
-        } else if (qoff && lane == 0) {
-            qoff[i] = QOFF_NONE;
         }
+        if (NETA == 0 && qoff && lane == 0) qoff[i] = QOFF_NONE;
         __syncwarp();
         for (int s = lane; s < E.n_g; s += 32) {
             const double g = sG[s];
@@ -581,7 +605,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
 // STORED (main pass): the pair queues come from the descriptor pass's records;
 // an atom without a valid record is appended to the wide-capacity list, whose
 // pass (STORED = false) rebuilds the queue from the live masks.
-template <int NETA, bool NARROW, int KP, int KN, bool STORED>
+template <int NETA, bool NARROW, int KP, int KN, bool STORED, bool RES>
 __global__ void __launch_bounds__(128, 5)
 k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
@@ -593,7 +617,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     constexpr bool PACK = NETA <= 2;
-    unsigned char* base = smem + force_warp_bytes(C, nv.stride, PACK) * wib;
+    unsigned char* base = smem + force_warp_bytes(C, nv.stride, PACK, RES) * wib;
     WarpSmem w;
     w.nd = reinterpret_cast<float4*>(base);
     w.npf = w.nd + C;
@@ -604,6 +628,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     bool fx_bad = false;   // a contribution outside the fixed-point range (or not finite)
     w.queue = reinterpret_cast<unsigned short*>(sW + NNP_MAXG);
     w.cmap = reinterpret_cast<short*>(w.queue + PAIR_QUEUE);
+    w.nel = RES ? reinterpret_cast<unsigned char*>(w.cmap + nv.stride) : nullptr;
     w.rtab = reinterpret_cast<float4*>(w.queue);
     w.rw = reinterpret_cast<float*>(w.rtab + NNP_MAXRAD);
     w.ninv = nullptr;
@@ -639,7 +664,24 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
                                                   n_list, sig);
         if (over_capacity(M, C, pass, i, spill, false, lane, flags, c_spill)) continue;
-        if (NETA > 0) {
+        const int nb = (M + 31) >> 5;
+        // the descriptor pass's queue record, used when this staging reproduces it
+        const unsigned short* rec = nullptr;
+        if (STORED && NETA > 0) {
+            const unsigned o = qoff[i];
+            if (o != QOFF_NONE) {
+                const unsigned short* r = qpool + (size_t)o * 8;
+                if (r[0] == (unsigned short)M && r[1] == (unsigned short)(sig & 0xffffu) &&
+                    r[2] == (unsigned short)(sig >> 16))
+                    rec = r;
+            }
+            if (!rec) {
+                if (lane == 0) spill[1 + atomicAdd(spill, 1)] = i;
+                continue;
+            }
+        }
+        const int ncls = RES ? E.n_cls : 1;
+        for (int cls = 0; NETA > 0 && cls < ncls; ++cls) {
             // dense weights W[q][l][k] = dE/dG_o * 2^(1-zeta), zeta = 2^k
             float W[NETA > 0 ? NETA : 1][2][NNP_KMAX + 1];
 #pragma unroll
@@ -648,29 +690,15 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 for (int l = 0; l < 2; ++l)
 #pragma unroll
                     for (int kk = 0; kk <= NNP_KMAX; ++kk) {
-                        const int o = (q < E.n_eta) ? E.ang_out[q][l][kk] : -1;
+                        const int o = (q < E.n_eta) ? E.ang_out[cls][q][l][kk] : -1;
                         W[q][l][kk] = (o >= 0) ? sW[o] * exp2f((float)(1 - (1 << kk))) : 0.f;
                     }
-            const int nb = (M + 31) >> 5;
-            // the descriptor pass's queue record, used when this staging reproduces it
-            const unsigned short* rec = nullptr;
-            if (STORED) {
-                const unsigned o = qoff[i];
-                if (o != QOFF_NONE) {
-                    const unsigned short* r = qpool + (size_t)o * 8;
-                    if (r[0] == (unsigned short)M && r[1] == (unsigned short)(sig & 0xffffu) &&
-                        r[2] == (unsigned short)(sig >> 16))
-                        rec = r;
-                }
-                if (!rec) {
-                    if (lane == 0) spill[1 + atomicAdd(spill, 1)] = i;
-                    continue;
-                }
-            }
+            const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             int bp = QHDR, qpos = queue_entries_start(nb);
             for (int A = 0; A < nb; ++A) {
                 const int jl = 32 * A + lane;
                 const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int ej = (RES && jl < M) ? (int)w.nel[jl] : -1;
                 for (int B = A; B < nb; ++B, ++bp) {
                     int total;
                     const unsigned short* qsrc;
@@ -679,7 +707,11 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                         qsrc = rec + qpos;
                         qpos += (total + 7) & ~7;
                     } else {
-                        const unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
+                        unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
+                        if (RES && ce1 >= 0) {
+                            const int kl = 32 * B + lane;
+                            mask &= class_mask(ej, kl < M ? (int)w.nel[kl] : -1, ce1, ce2, lane);
+                        }
                         total = enqueue_block(mask, lane, w.queue);
                         qsrc = w.queue;
                     }

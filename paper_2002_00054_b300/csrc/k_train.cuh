@@ -20,7 +20,7 @@ __host__ __device__ inline size_t tangent_warp_bytes(int C)
 }
 
 // t~_i = (dG_i/dr . u) / s for every atom (scaled descriptor tangent).
-template <int NETA, bool NARROW, int KP, int KN>
+template <int NETA, bool NARROW, int KP, int KN, bool RES>
 __global__ void __launch_bounds__(128, 4)
 k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
           const float* __restrict__ u, float* __restrict__ T, int* __restrict__ flags, int* __restrict__ spill,
@@ -120,7 +120,9 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
             }
             sT[E.rad_out[rr]] = acc;
         }
-        if (NETA > 0) {
+        // angular (one pass per neighbour-element pair class)
+        const int ncls = RES ? E.n_cls : 1;
+        for (int cls = 0; NETA > 0 && cls < ncls; ++cls) {
             constexpr int NQ = NETA > 0 ? NETA : 1;
             constexpr int NA = NQ * 2 * (NNP_KMAX + 1);
             float acc[NQ][2][NNP_KMAX + 1];
@@ -131,11 +133,17 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
 #pragma unroll
                     for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[q][l][kk] = 0.f;
             const int nb = (M + 31) >> 5;
+            const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             for (int A = 0; A < nb; ++A) {
                 const int jl = 32 * A + lane;
                 const float4 al = (jl < M) ? nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
+                const int ej = (RES && jl < M) ? __float_as_int(nfe[jl].z) : -1;
                 for (int B = A; B < nb; ++B) {
-                    const unsigned mask = live_mask<NARROW>(A, B, lane, M, al, nd, P.rc2);
+                    unsigned mask = live_mask<NARROW>(A, B, lane, M, al, nd, P.rc2);
+                    if (RES && ce1 >= 0) {
+                        const int kl = 32 * B + lane;
+                        mask &= class_mask(ej, kl < M ? __float_as_int(nfe[kl].z) : -1, ce1, ce2, lane);
+                    }
                     const int total = enqueue_block(mask, lane, queue);
                     for (int e0 = 0; e0 < total; e0 += 32) {
                         const int e = e0 + lane;
@@ -212,7 +220,7 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
                 const int idx = c0 + lane;
                 if (idx < NA) {
                     const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
-                    const int o = (q < E.n_eta) ? E.ang_out[q][l][kk] : -1;
+                    const int o = (q < E.n_eta) ? E.ang_out[cls][q][l][kk] : -1;
                     if (o >= 0) sT[o] = tot * (double)exp2f((float)(1 - (1 << kk)));
                 }
             }

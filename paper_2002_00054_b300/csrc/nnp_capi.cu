@@ -220,7 +220,9 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
         E.n_g = ns;
         for (int q = 0; q < NNP_MAXETA; ++q)
             for (int l = 0; l < 2; ++l)
-                for (int k = 0; k <= NNP_KMAX; ++k) E.ang_out[q][l][k] = -1;
+                for (int k = 0; k <= NNP_KMAX; ++k)
+                    for (int c = 0; c < NNP_MAXCLS; ++c) E.ang_out[c][q][l][k] = -1;
+        E.n_cls = 0;
         std::vector<double> etas;
         for (int s = 0; s < ns; ++s) {
             const nnp_sf_desc& d = p->sf[off + s];
@@ -240,8 +242,25 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
                 E.rad_out[E.n_rad] = s;
                 E.n_rad++;
             } else if (d.type == NNP_SF_ANG_NARROW || d.type == NNP_SF_ANG_WIDE) {
-                if (d.elem_a != -1 || d.elem_b != -1) { why = "element-resolved angular descriptors are not implemented"; return NNP_EUNSUPPORTED; }
+                if (d.elem_a < -1 || d.elem_a >= p->n_elements || d.elem_b < -1 || d.elem_b >= p->n_elements)
+                    return fail("angular elem_a / elem_b out of range");
                 if (d.rs != 0.0) return fail("angular rs must be 0");
+                // neighbour-element pair class (either element -1: every pair)
+                int ce1 = -1, ce2 = -1;
+                if (d.elem_a >= 0 && d.elem_b >= 0) {
+                    ce1 = std::min(d.elem_a, d.elem_b);
+                    ce2 = std::max(d.elem_a, d.elem_b);
+                }
+                int c = -1;
+                for (int t = 0; t < E.n_cls; ++t)
+                    if (E.cls_e1[t] == ce1 && E.cls_e2[t] == ce2) c = t;
+                if (c < 0) {
+                    if (E.n_cls >= NNP_MAXCLS) { why = "more than 10 neighbour-element pair classes of angular descriptors"; return NNP_EUNSUPPORTED; }
+                    c = E.n_cls++;
+                    E.cls_e1[c] = ce1;
+                    E.cls_e2[c] = ce2;
+                    if (ce1 >= 0) P.resolved = 1;
+                }
                 if (kind == 0) kind = d.type;
                 else if (kind != d.type) { why = "narrow and wide angular descriptors in one model are not implemented"; return NNP_EUNSUPPORTED; }
                 int q = -1;
@@ -260,8 +279,8 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
                 int k = -1;
                 for (int t = 0; t <= NNP_KMAX; ++t) if (d.zeta == (double)(1 << t)) k = t;
                 if (k < 0) { why = "angular zeta must be 1, 2, 4, 8 or 16"; return NNP_EUNSUPPORTED; }
-                if (E.ang_out[q][l][k] >= 0) return fail("duplicate angular descriptor");
-                E.ang_out[q][l][k] = s;
+                if (E.ang_out[c][q][l][k] >= 0) return fail("duplicate angular descriptor");
+                E.ang_out[c][q][l][k] = s;
             } else {
                 snprintf(buf, sizeof buf, "unknown descriptor type %d", d.type);
                 why = buf;
@@ -313,13 +332,14 @@ typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, c
 
 typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*, int*, int);
 
-template <int NETA, bool NARROW, int KP, int KN>
+template <int NETA, bool NARROW, int KP, int KN, bool RES = false>
 static void pick(SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs)
 {
-    s = k_sf<NETA, NARROW, KP, KN>;
-    f = k_force<NETA, NARROW, KP, KN, false>;
-    t = k_tangent<NETA, NARROW, KP, KN>;
-    fs = k_force<NETA, NARROW, KP, KN, true>;
+    s = k_sf<NETA, NARROW, KP, KN, RES>;
+    f = k_force<NETA, NARROW, KP, KN, false, RES>;
+    t = k_tangent<NETA, NARROW, KP, KN, RES>;
+    if constexpr (RES) fs = f;   // resolved models do not store pair queues
+    else fs = k_force<NETA, NARROW, KP, KN, true, false>;
 }
 
 // Largest k (zeta = 2^k) used with lambda = +1 (l = 0) or -1 (l = 1), -1 if none.
@@ -327,9 +347,10 @@ static int kmax_of(const Plan& P, int l)
 {
     int km = -1;
     for (int e = 0; e < P.n_elem; ++e)
-        for (int q = 0; q < NNP_MAXETA; ++q)
-            for (int k = 0; k <= NNP_KMAX; ++k)
-                if (P.e[e].ang_out[q][l][k] >= 0) km = std::max(km, k);
+        for (int c = 0; c < P.e[e].n_cls; ++c)
+            for (int q = 0; q < NNP_MAXETA; ++q)
+                for (int k = 0; k <= NNP_KMAX; ++k)
+                    if (P.e[e].ang_out[c][q][l][k] >= 0) km = std::max(km, k);
     return km;
 }
 
@@ -341,6 +362,16 @@ static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKern
 {
     const bool nar = (P.ang_kind == NNP_SF_ANG_NARROW);
     const int kp = kmax_of(P, 0), kn = kmax_of(P, 1);
+    if (P.resolved) {
+        // angular descriptors resolved by neighbour-element pair: generic terms
+        switch (P.n_eta_max) {
+        case 1: if (nar) pick<1, true, 4, 4, true>(s, f, t, fs); else pick<1, false, 4, 4, true>(s, f, t, fs); break;
+        case 2: if (nar) pick<2, true, 4, 4, true>(s, f, t, fs); else pick<2, false, 4, 4, true>(s, f, t, fs); break;
+        case 3: if (nar) pick<3, true, 4, 4, true>(s, f, t, fs); else pick<3, false, 4, 4, true>(s, f, t, fs); break;
+        default: if (nar) pick<4, true, 4, 4, true>(s, f, t, fs); else pick<4, false, 4, 4, true>(s, f, t, fs); break;
+        }
+        return;
+    }
     if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f, t, fs); return; }
     if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f, t, fs); return; }
     switch (P.n_eta_max) {
@@ -365,7 +396,8 @@ static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
 static size_t sf_smem_per_warp(int cap) { return sf_warp_bytes(cap); }
 static size_t force_smem_per_warp(const Plan& P, int cap, int stride)
 {
-    return force_warp_bytes(cap, stride, P.n_eta_max <= 2);   // the kernels' NETA is n_eta_max
+    // the kernels' NETA is n_eta_max; resolved models keep each neighbour's element
+    return force_warp_bytes(cap, stride, P.n_eta_max <= 2, P.resolved != 0);
 }
 
 // Shared-memory capacity C of the main descriptor, force and tangent launches:
@@ -755,7 +787,7 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         // the force pass follows: store the pair queues for it (narrow kind only:
         // there the live masks cost a distance test per pair; wide queues follow
         // from the index arithmetic alone and are cheaper to rebuild than to store)
-        const bool store = (stop_after == 0) && P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW;
+        const bool store = (stop_after == 0) && P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW && !P.resolved;
         if (store) {
             rc = ensure_qpool(h, n);
             if (rc) return rc;
@@ -799,7 +831,7 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     {
         KScope ks(h, KG_FORCE, st, 2);
         // main pass over the stored queues (atoms without one join the wide pass)
-        const bool stored = P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW && h->qpool;
+        const bool stored = P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW && !P.resolved && h->qpool;
         (stored ? kfs : kf)<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
             n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, h->vpart, h->flags, h->spill, 0,
             stored ? h->qpool : nullptr, stored ? h->qoff : nullptr);

@@ -100,9 +100,13 @@ def test_create_rejects_bad_descriptors(lib):
     rc, h, msg = _create(lib, _P(m))
     assert rc == _capi.NNP_EUNSUPPORTED and "zeta" in msg
     m = workloads.water_model()
-    m["sf"][1][18] = dict(m["sf"][1][18], e1=0, e2=1)
+    m["sf"][1][18] = dict(m["sf"][1][18], e1=0, e2=2)   # element 2 does not exist
     rc, h, msg = _create(lib, _P(m))
-    assert rc == _capi.NNP_EUNSUPPORTED and "element-resolved" in msg
+    assert rc == _capi.NNP_EINVAL and "out of range" in msg
+    m = workloads.water_model()
+    m["sf"][1][18] = dict(m["sf"][1][18], type="wide")   # narrow and wide in one model
+    rc, h, msg = _create(lib, _P(m))
+    assert rc == _capi.NNP_EUNSUPPORTED and "narrow and wide" in msg
     m = workloads.water_model()
     m["sf_s"][0] = np.array(m["sf_s"][0]); m["sf_s"][0][3] = 0.0
     rc, h, msg = _create(lib, _P(m))

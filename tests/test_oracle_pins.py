@@ -114,6 +114,37 @@ def test_angular_lambda_identity():
         assert res["G"][i, 0] - res["G"][i, 1] == pytest.approx(2 * (c * xf).sum(), rel=1e-9, abs=1e-12)
 
 
+def test_element_resolved_angular_classes():
+    """Angular descriptors resolved by neighbour-element pair: on a trimer whose
+    centre sees two neighbours of element 1, the (1, 1) class holds the whole
+    unresolved value and the (0, 0) and (0, 1) classes are zero; on the water box
+    the three classes of a two-element system partition the pair sum, so they add
+    up to the unresolved descriptor (for every eta, lambda, zeta, and both kinds)."""
+    rc, a = 6.0, 2.5
+    th = math.radians(100.0)
+    pos = np.array([[0, 0, 0], [a, 0, 0], [a * math.cos(th), a * math.sin(th), 0]], float)
+    terms = [(eta, z, l) for eta in (0.001, 0.02) for z in (1, 2, 4, 16) for l in (1.0, -1.0)]
+    for kind in ("narrow", "wide"):
+        rows = [angular(kind, e, z, l) for e, z, l in terms]
+        for e1, e2 in ((0, 0), (0, 1), (1, 1)):
+            rows += [angular(kind, e, z, l, e1=e1, e2=e2) for e, z, l in terms]
+        m = model_from_rows([rows, rows], rc)
+        res = oracle.compute(m, pos, np.array([0, 1, 1], np.int32), np.array([50.0, 50.0, 50.0]))
+        nt = len(terms)
+        g = res["G"][0]
+        assert np.all(np.abs(g[:nt]) > 0)
+        np.testing.assert_array_equal(g[nt:2 * nt], 0.0)        # (0, 0)
+        np.testing.assert_array_equal(g[2 * nt:3 * nt], 0.0)    # (0, 1)
+        np.testing.assert_allclose(g[3 * nt:], g[:nt], rtol=1e-14)   # (1, 1)
+        wpos, wtypes, wbox = workloads.water_random()
+        res = oracle.compute(m, wpos, wtypes, wbox)
+        G = res["G"]
+        parts = G[:, nt:2 * nt] + G[:, 2 * nt:3 * nt] + G[:, 3 * nt:]
+        np.testing.assert_allclose(parts, G[:, :nt], rtol=1e-12, atol=1e-300)
+        # both classes with one O neighbour are populated in the water box
+        assert np.all(np.abs(G[:, 2 * nt:3 * nt]).max(0) > 0)
+
+
 # ---------------------------------------------------------------- neighbours
 def test_neighbors_cell_equals_brute():
     pos, _t, box = workloads.fcc((4, 4, 4))

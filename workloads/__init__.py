@@ -40,22 +40,27 @@ def radial_etas(n, lo=0.001, hi=0.5):
     return [lo * (hi / lo) ** (m / (n - 1)) for m in range(n)]
 
 
-def water_sf_set():
+def water_sf_set(resolved=False):
     """Per element (O=0, H=1): 8 radial G2 per neighbour element + 14 narrow angular.
 
     Angular: for eta in {0.001, 0.01}: lambda=+1 with zeta in {1,2,4,16} and
-    lambda=-1 with zeta in {1,2,4}; not resolved by neighbour element.  n_G = 30.
+    lambda=-1 with zeta in {1,2,4}; not resolved by neighbour element: n_G = 30.
+    resolved=True: the same 14 for each neighbour-element pair (O,O), (O,H),
+    (H,H): n_G = 16 + 42 = 58.
     """
+    pairs = ((0, 0), (0, 1), (1, 1)) if resolved else ((-1, -1),)
     per = []
     for _centre in range(2):
         rows = []
         for nb in range(2):
             for eta in radial_etas(8):
                 rows.append({"type": "radial", "e1": nb, "e2": -1, "eta": eta, "rs": 0.0})
-        for eta in (0.001, 0.01):
-            for lam, zetas in ((1.0, (1, 2, 4, 16)), (-1.0, (1, 2, 4))):
-                for z in zetas:
-                    rows.append({"type": "narrow", "e1": -1, "e2": -1, "eta": eta, "zeta": float(z), "lambda": lam})
+        for e1, e2 in pairs:
+            for eta in (0.001, 0.01):
+                for lam, zetas in ((1.0, (1, 2, 4, 16)), (-1.0, (1, 2, 4))):
+                    for z in zetas:
+                        rows.append({"type": "narrow", "e1": e1, "e2": e2, "eta": eta, "zeta": float(z),
+                                     "lambda": lam})
         per.append(rows)
     return per
 
@@ -102,11 +107,13 @@ def _scaling(name, sf):
     return [np.zeros(len(r)) for r in sf], [np.ones(len(r)) for r in sf]
 
 
-def water_model(seed=SEED_WATER_MODEL, hidden=(25, 25)):
-    sf = water_sf_set()
-    mu, s = _scaling("water", sf)
-    widths = [30, *hidden, 1]
-    return {"name": "water", "elements": ["O", "H"], "masses": [MASS["O"], MASS["H"]], "cutoff": 6.0,
+def water_model(seed=SEED_WATER_MODEL, hidden=(25, 25), resolved=False):
+    """Water-like model; resolved=True takes the element-pair-resolved angular set (n_G = 58)."""
+    sf = water_sf_set(resolved)
+    name = "water_resolved" if resolved else "water"
+    mu, s = _scaling(name, sf)
+    widths = [len(sf[0]), *hidden, 1]
+    return {"name": name, "elements": ["O", "H"], "masses": [MASS["O"], MASS["H"]], "cutoff": 6.0,
             "sf": sf, "sf_mu": mu, "sf_s": s, "widths": widths, "weights": random_weights(widths, 2, seed)}
 
 
