@@ -388,6 +388,56 @@ def combined_run(args, dev):
                               "energy_log_every_100_steps": [float(e) for e in et[100::100]]}}
 
 
+def domains_run(args, dev):
+    """Slab domain decomposition of the workload (2 r_c halo, no reverse exchange),
+    the domains evaluated one after another on one GPU, each with its own handle
+    and device-resident inputs: energy + forces per evaluation against the
+    undivided box."""
+    import torch
+    from paper_2002_00054_b300 import NNP, domain
+    model, pos_h, types_h, box, desc, max_nb = make_workload(args.workload)
+    n = len(pos_h)
+
+    def timed(handles, inputs):
+        for _ in range(2):
+            for h, (p, t, b) in zip(handles, inputs):
+                h.compute(p, t, b)
+        torch.cuda.synchronize()
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            for h, (p, t, b) in zip(handles, inputs):
+                h.compute(p, t, b)
+        c.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(c) / args.steps
+
+    p0 = torch.from_numpy(pos_h).to(dev)
+    t0 = torch.from_numpy(types_h).to(dev)
+    full = NNP(model, device=dev.index, max_neighbors=max_nb)
+    ms_full = timed([full], [(p0, t0, box)])
+    full.close()
+    out = {"metric": "energy + force evaluations, atoms/s", "mode": "domains", "workload": args.workload,
+           "atoms": n, "steps": args.steps, "undivided_ms": ms_full, "undivided_atoms_per_s": n / (ms_full * 1e-3),
+           "decomposed": []}
+    for nd in (2, 4):
+        doms = domain.decompose(pos_h, box, nd, model["cutoff"])
+        handles, inputs, local = [], [], 0
+        for d in doms:
+            lp, lt = d.local(pos_h, types_h)
+            local += len(lp)
+            handles.append(NNP(model, device=dev.index, max_neighbors=max_nb))
+            inputs.append((torch.tensor(lp, dtype=torch.float32, device=dev),
+                           torch.tensor(lt, dtype=torch.int32, device=dev), d.box))
+        ms = timed(handles, inputs)
+        for h in handles:
+            h.close()
+        out["decomposed"].append({"domains": nd, "ms": ms, "atoms_per_s": n / (ms * 1e-3),
+                                  "local_atoms_over_owned": local / n,
+                                  "per_domain_ms_if_concurrent": ms / nd})
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -400,7 +450,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
     ap.add_argument("--no-fcc", action="store_true", help="skip the FCC precision-form leg")
-    ap.add_argument("--mode", default="standard", choices=["standard", "combined"])
+    ap.add_argument("--mode", default="standard", choices=["standard", "combined", "domains"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -422,6 +472,10 @@ def main():
     if args.mode == "combined":
         if rank == 0:
             print(json.dumps(combined_run(args, dev)), flush=True)
+        return
+    if args.mode == "domains":
+        if rank == 0:
+            print(json.dumps(domains_run(args, dev)), flush=True)
         return
 
     model, pos_h, types_h, box, desc, max_nb = make_workload(args.workload)
