@@ -438,6 +438,40 @@ def domains_run(args, dev):
     return out
 
 
+def ablation_run(args, dev):
+    """Force assembly, both forms on the same workload and steps: the per-slot g
+    buffer with the reverse-index gather (deterministic, the default) and the
+    scatter form with global float atomics (NNP_FORCE_SCATTER=1, no reverse
+    index, order-dependent sums)."""
+    import torch
+    from paper_2002_00054_b300 import NNP
+    model, pos_h, types_h, box, desc, max_nb = make_workload(args.workload)
+    n = len(pos_h)
+    vel_h = workloads.maxwell_boltzmann(types_h, model["masses"]).astype(np.float32)
+    t = torch.from_numpy(types_h).to(dev)
+    out = {"metric": METRIC, "mode": "ablation", "workload": args.workload, "atoms": n, "steps": args.steps}
+    for form, env in (("gather", "0"), ("scatter", "1")):
+        os.environ["NNP_FORCE_SCATTER"] = env
+        h = NNP(model, device=dev.index, max_neighbors=max_nb)
+        p = torch.from_numpy(pos_h).to(dev)
+        v = torch.from_numpy(vel_h).to(dev)
+        h.step(p, v, t, box, DT_FS, args.warmup)
+        h.profile(True)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        h.step(p, v, t, box, DT_FS, args.steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        kt = h.kernel_times()
+        out[form] = {"value": n * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
+                     "kernels_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1] > 0}}
+        h.close()
+    os.environ.pop("NNP_FORCE_SCATTER", None)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -450,7 +484,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
     ap.add_argument("--no-fcc", action="store_true", help="skip the FCC precision-form leg")
-    ap.add_argument("--mode", default="standard", choices=["standard", "combined", "domains"])
+    ap.add_argument("--mode", default="standard", choices=["standard", "combined", "domains", "ablation"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -476,6 +510,10 @@ def main():
     if args.mode == "domains":
         if rank == 0:
             print(json.dumps(domains_run(args, dev)), flush=True)
+        return
+    if args.mode == "ablation":
+        if rank == 0:
+            print(json.dumps(ablation_run(args, dev)), flush=True)
         return
 
     model, pos_h, types_h, box, desc, max_nb = make_workload(args.workload)

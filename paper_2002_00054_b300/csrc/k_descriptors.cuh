@@ -610,7 +610,8 @@ __global__ void __launch_bounds__(128, 5)
 k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
         double* __restrict__ vir_part, int* __restrict__ flags, int* __restrict__ spill, int pass,
-        const unsigned short* __restrict__ qpool, const unsigned int* __restrict__ qoff)
+        const unsigned short* __restrict__ qpool, const unsigned int* __restrict__ qoff,
+        float* __restrict__ Fscat)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -821,13 +822,27 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             }
         }
         __syncwarp();
-        // write g per list slot, own force and virial
+        // write g per list slot (or, with Fscat, add -g_ij to F_j with global
+        // atomics: the scatter form), own force and virial
         const int cnt = n_list;
-        float4* grow = gbuf + (size_t)i * nv.stride;
-        for (int s = lane; s < cnt; s += 32) {
-            const int c = w.cmap[s];
-            grow[s] = (c >= 0) ? make_float4(fx_get(w, 3 * c), fx_get(w, 3 * c + 1), fx_get(w, 3 * c + 2), 0.f)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (Fscat) {
+            const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
+            for (int s = lane; s < cnt; s += 32) {
+                const int c = w.cmap[s];
+                if (c >= 0) {
+                    float* fj = Fscat + 3 * (size_t)(row[s] & NB_INDEX_MASK);
+                    atomicAdd(fj + 0, -fx_get(w, 3 * c));
+                    atomicAdd(fj + 1, -fx_get(w, 3 * c + 1));
+                    atomicAdd(fj + 2, -fx_get(w, 3 * c + 2));
+                }
+            }
+        } else {
+            float4* grow = gbuf + (size_t)i * nv.stride;
+            for (int s = lane; s < cnt; s += 32) {
+                const int c = w.cmap[s];
+                grow[s] = (c >= 0) ? make_float4(fx_get(w, 3 * c), fx_get(w, 3 * c + 1), fx_get(w, 3 * c + 2), 0.f)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
         float fx = 0.f, fy = 0.f, fz = 0.f, v[9];
 #pragma unroll
@@ -843,7 +858,15 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
 #pragma unroll
         for (int q = 0; q < 9; ++q) vir[q] += (double)warp_sum(v[q]);
-        if (lane == 0) Fown[i] = make_float4(fx, fy, fz, 0.f);
+        if (lane == 0) {
+            if (Fscat) {
+                atomicAdd(Fscat + 3 * (size_t)i + 0, fx);
+                atomicAdd(Fscat + 3 * (size_t)i + 1, fy);
+                atomicAdd(Fscat + 3 * (size_t)i + 2, fz);
+            } else {
+                Fown[i] = make_float4(fx, fy, fz, 0.f);
+            }
+        }
         __syncwarp();
     }
     if (__any_sync(FULL, fx_bad) && lane == 0) atomicOr(&flags[FLAG_ERR], ERR_RANGE);

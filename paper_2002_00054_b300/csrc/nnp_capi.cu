@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -132,6 +133,7 @@ struct nnp_handle {
     size_t want_qpool = 0;     // entries the next evaluation should have (0: estimate)
     unsigned int* qoff = nullptr;   // [cap_n] record offset / 8 per atom
     unsigned short* seg = nullptr;  // [cap_n][NB_SEG] stencil segments of cell-built rows
+    bool scatter = false;           // forces by global atomics instead of the g buffer + gather
 };
 
 static thread_local std::string g_create_err;
@@ -328,7 +330,7 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
 typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, float*, float*, int*, unsigned long long*,
                          int*, int, unsigned short*, unsigned int*, unsigned long long);
 typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
-                            double*, int*, int*, int, const unsigned short*, const unsigned int*);
+                            double*, int*, int*, int, const unsigned short*, const unsigned int*, float*);
 
 typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*, int*, int);
 
@@ -759,13 +761,14 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
             k_rows_cell<<<rows_grid, 256, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_start,
                                                    h->cell_atoms, P.rcut2, h->stride, h->nbr, h->ncount, h->seg,
                                                    h->flags);
-            k_rev_cell<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->seg, h->rev, h->flags);
-            h->launches += 6;
+            if (!h->scatter) k_rev_cell<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->seg, h->rev,
+                                                                   h->flags);
+            h->launches += h->scatter ? 5 : 6;
         } else {
             k_rows_brute<<<rows_grid, 256, 0, st>>>(n, h->pos4, bt ? h->sys_of : nullptr, bt ? h->sys_start_d : nullptr,
                                                     h->sys_box, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
-            k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
-            h->launches += 2;
+            if (!h->scatter) k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
+            h->launches += h->scatter ? 1 : 2;
         }
     }
     h->list_valid = true;
@@ -828,19 +831,22 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     const int gred = std::min(blocks_for(n, T), 4 * h->num_sms);
     rc = ensure_red(h, gred, nvp);
     if (rc) return rc;
+    // the scatter form adds every contribution into the force output directly
+    float* Fsc = h->scatter ? (F_out ? F_out : h->F) : nullptr;
+    if (Fsc) CK(h, cudaMemsetAsync(Fsc, 0, sizeof(float) * 3 * (size_t)n, st));
     {
         KScope ks(h, KG_FORCE, st, 2);
         // main pass over the stored queues (atoms without one join the wide pass)
         const bool stored = P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW && !P.resolved && h->qpool;
         (stored ? kfs : kf)<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
             n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, h->vpart, h->flags, h->spill, 0,
-            stored ? h->qpool : nullptr, stored ? h->qoff : nullptr);
+            stored ? h->qpool : nullptr, stored ? h->qoff : nullptr, Fsc);
         kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride,
                                                                        h->dEdG, h->gbuf, h->Fown,
                                                                        h->vpart + (size_t)nvp_main * 9, h->flags,
-                                                                       h->spill, 1, nullptr, nullptr);
+                                                                       h->spill, 1, nullptr, nullptr, Fsc);
     }
-    {
+    if (!Fsc) {
         KScope ks(h, KG_GATHER, st);
         k_gather<<<rows_grid, 256, 0, st>>>(n, nv, h->rev, h->gbuf, h->Fown, F_out ? F_out : h->F, h->flags);
     }
@@ -923,6 +929,12 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     h->skin = params->skin;
     h->stride = (params->max_neighbors + 7) & ~7;   // multiple of 8 keeps per-warp shared arrays 16-byte aligned
     h->precision = params->mlp_precision;
+    {
+        // NNP_FORCE_SCATTER=1: forces by global atomics (the paper's CabanaMD form)
+        // instead of the per-slot g buffer and the reverse-index gather
+        const char* env = getenv("NNP_FORCE_SCATTER");
+        h->scatter = env && env[0] == '1';
+    }
     DeviceGuard g(device);
     auto fail = [&](int code) {
         g_create_err = h->err;
@@ -1545,9 +1557,9 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
     k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
     kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, vpart,
-                                                     flags, spill, 0, nullptr, nullptr);
+                                                     flags, spill, 0, nullptr, nullptr, nullptr);
     kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, dEdG, gbuf, Fown,
-                                                                   vpart + (size_t)nvp_main * 9, flags, spill, 1, nullptr, nullptr);
+                                                                   vpart + (size_t)nvp_main * 9, flags, spill, 1, nullptr, nullptr, nullptr);
     k_gather<<<rows_grid, 256, 0, st>>>(n, nv, rev, gbuf, Fown, forces ? forces : Fs, flags);
     k_sum_partial<<<gred, T, 0, st>>>(n, Ei, epart, flags);
     k_finalize<<<1, 256, 0, st>>>(gred, epart, energy, nvp, vpart, nullptr);
