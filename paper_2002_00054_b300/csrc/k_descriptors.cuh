@@ -139,11 +139,18 @@ __host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool
 // (list stride <= 1024) cannot overflow either word; the only rounding is 2^-28
 // eV/A per add, and the sums do not depend on the order of the adds.
 #define FX_LIMIT 32000.0f
+// The roundings to integers use the 1.5 * 2^23 shift: for |x| < 2^22, x + 1.5 * 2^23
+// rounds x to the nearest integer, which then sits in the low mantissa bits
+// (integer = bits(x + S) - bits(S)), and (x + S) - S is that integer as a float;
+// no float/int conversion instructions.  |v 2^6| < 2^22 and |r 2^27| <= 2^20 hold
+// for |v| < FX_LIMIT.
 __device__ __forceinline__ void fx_split(float v, int& hi, int& lo)
 {
-    hi = __float2int_rn(v * 64.0f);
-    const float r = fmaf((float)hi, -1.0f / 64.0f, v);
-    lo = __float2int_rn(r * 134217728.0f);
+    const float S = 12582912.0f;   // 1.5 * 2^23
+    const float th = fmaf(v, 64.0f, S);
+    hi = __float_as_int(th) - __float_as_int(S);
+    const float r = fmaf(th - S, -1.0f / 64.0f, v);
+    lo = __float_as_int(fmaf(r, 134217728.0f, S)) - __float_as_int(S);
 }
 __device__ __forceinline__ void fx_set(const WarpSmem& w, int idx, float v)
 {
