@@ -67,8 +67,9 @@ enum nnp_precision { NNP_FP32 = 0, NNP_BF16 = 1 };
 typedef struct {
     int type;      /* nnp_sf_type                                                  */
     int elem_a;    /* radial: neighbour element, -1 = any.                          */
-                   /* angular: with elem_b the unordered neighbour element pair,    */
-                   /* -1/-1 = any pair (the only angular filter implemented)        */
+                   /* angular: with elem_b the unordered pair of neighbour elements */
+                   /* {elem_a, elem_b} of the pairs (j, k) the function sums over;  */
+                   /* either -1 = every pair; at most 10 distinct pairs per element */
     int elem_b;
     double eta;    /* A^-2, >= 0                                                    */
     double rs;     /* A, radial only (angular: must be 0)                           */
@@ -109,7 +110,14 @@ typedef struct nnp_handle nnp_handle;
 
 /* Creates a handle on CUDA device 'device': validates and copies the parameters
  * (host memory may be freed afterwards).  *out is NULL on failure.  Parameter
- * validation happens before any CUDA call.  Scratch grows on demand later. */
+ * validation happens before any CUDA call.  Scratch grows on demand later.
+ * Force assembly: by default each atom writes its pair contributions g_ij per
+ * neighbour-list slot and forces are gathered per atom through the reverse
+ * index, in a fixed order (bitwise reproducible, no global atomics).  With the
+ * environment variable NNP_FORCE_SCATTER=1, read here, contributions are added
+ * into the forces with global float atomics instead (the scatter form of the
+ * paper's CabanaMD code): no reverse index or g buffer, sums in the order the
+ * atomics land. */
 NNP_API int nnp_create(const nnp_params* params, int device, nnp_handle** out);
 
 /* Frees the handle and its device memory (waits for its pending work).  NULL is a no-op. */
