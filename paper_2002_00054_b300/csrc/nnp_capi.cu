@@ -458,7 +458,8 @@ static void retune_capacity(nnp_handle* h)
     // queue pool: the last evaluation's demand (chunks claimed, including the
     // claims that did not fit) plus a quarter
     const size_t demand = (size_t)h->h_cnt[CNT_QTOP];
-    if (demand > h->cap_qpool) h->want_qpool = demand + demand / 4;
+    if (demand > 0 && (demand > h->cap_qpool || 2 * (demand + demand / 4) < h->cap_qpool))
+        h->want_qpool = demand + demand / 4;
 }
 
 // ------------------------------------------------------------------ scratch
@@ -531,12 +532,14 @@ static int ensure_red(nnp_handle* h, int ne, int nv)
 }
 
 // Queue pool for an evaluation of n atoms: the size the last call asked for, or
-// on first use half the records' upper bound at the current capacity.
+// on first use C^2 / 8 entries per atom (about the narrow water records at the
+// capacity the counts suggest; atoms that do not fit rebuild their queue and
+// the next call gets a larger pool).  Shrinks when more than twice too large.
 static int ensure_qpool(nnp_handle* h, int n)
 {
     size_t want = h->want_qpool;
-    if (want == 0) want = (size_t)n * (queue_record_bound(h->cap_rc) / 2);
-    if (want <= h->cap_qpool) return NNP_OK;
+    if (want == 0) want = (size_t)n * ((size_t)h->cap_rc * h->cap_rc / 8 + 64);
+    if (want <= h->cap_qpool && 2 * want >= h->cap_qpool) return NNP_OK;
     if (h->qpool) cudaFree(h->qpool);
     h->qpool = nullptr;
     h->cap_qpool = 0;
