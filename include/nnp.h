@@ -169,7 +169,15 @@ NNP_API int nnp_descriptors(nnp_handle* h, int n_atoms, const float* pos, const 
  * (nullable).  Forces at the start are computed by the call, unless the previous
  * call on h was nnp_step on the same pos/types buffers, n_atoms and box and the
  * positions and types are bitwise unchanged since it returned (checked on the
- * device); then that call's final forces and energy are reused. */
+ * device); then that call's final forces and energy are reused.
+ * Every decision that differs between steps (neighbour-list rebuild, atoms of
+ * the wide-capacity pass, log entry) is taken on the device, so with
+ * n_steps >= 3 the call launches the first step directly, captures the second
+ * as a CUDA graph on a stream of its own and replays it for the remaining
+ * steps (bitwise the same results; ordered after earlier and before later work
+ * on `stream` by events).  Setting NNP_STEP_GRAPH=0 when the handle is created,
+ * or kernel-group timing, launches every step directly.  An error raised at any
+ * step is reported by the call. */
 NNP_API int nnp_step(nnp_handle* h, int n_atoms, float* pos, float* vel, const int* types, const double* box,
              double dt_fs, int n_steps, double* pe_ke_log, void* stream);
 

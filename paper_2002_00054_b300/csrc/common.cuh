@@ -39,6 +39,7 @@
 #define CNT_PER_CALL 7  // counters [0, CNT_PER_CALL) restart with every API call
 #define CNT_REBUILDS 7
 #define CNT_QTOP 8      // pair-queue pool entries claimed by the current evaluation
+#define CNT_LOGSLOT 9   // next energy-log entry of the running nnp_step call
 #define CNT_N 10
 
 #define LOG2E 1.4426950408889634f

@@ -94,12 +94,21 @@ __global__ void k_kick_ke(int n, const Plan* __restrict__ plan_g, const int* __r
 }
 
 // log[2k + slot] = sum of partials (one block)
-__global__ void k_log_sum(int np, const double* __restrict__ part, double* __restrict__ log, int slot)
+// Energy-log entry s = (*slot)++: log[2s] = potential energy (*epot), log[2s+1] =
+// kinetic energy (the sum of the partials).  The entry index lives on the device,
+// so one launch with fixed arguments serves every step of a replayed step graph.
+__global__ void k_log_sum(int np, const double* __restrict__ part, const double* __restrict__ epot,
+                          double* __restrict__ log, unsigned long long* __restrict__ slot)
 {
     __shared__ double sh[32];
     double v = 0.0;
     for (int k = threadIdx.x; k < np; k += blockDim.x) v += part[k];
     const double s = block_sum_d(v, sh);
-    if (threadIdx.x == 0) log[slot] = s;
+    if (threadIdx.x == 0) {
+        const unsigned long long e = *slot;
+        log[2 * e] = *epot;
+        log[2 * e + 1] = s;
+        *slot = e + 1;
+    }
 }
 

@@ -134,6 +134,11 @@ struct nnp_handle {
     unsigned int* qoff = nullptr;   // [cap_n] record offset / 8 per atom
     unsigned short* seg = nullptr;  // [cap_n][NB_SEG] stencil segments of cell-built rows
     bool scatter = false;           // forces by global atomics instead of the g buffer + gather
+    // nnp_step: the per-step launch sequence captured as a CUDA graph and replayed
+    bool step_graph = true;
+    cudaStream_t gstream = nullptr;   // capture and replay stream (non-blocking, owned)
+    cudaEvent_t gfork = nullptr, gjoin = nullptr;
+    cudaGraphExec_t gexec = nullptr;  // kept across calls, updated in place when only arguments change
 };
 
 static thread_local std::string g_create_err;
@@ -709,7 +714,6 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         for (int a = 0; a < 3; ++a) bx.L[a] = (float)bt->boxes[a];
     }
     const int T = 256;
-    CK(h, cudaMemsetAsync(h->flags + FLAG_ERR, 0, sizeof(int), st));
     const int rows_grid = std::min(blocks_for(n, 8), h->num_sms * 8);
     {
         KScope ks(h, KG_NEIGH, st, 0);
@@ -865,11 +869,13 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     return NNP_OK;
 }
 
-// Called at the start of every evaluating API call: clears work counters.
+// Called at the start of every evaluating API call: clears the error word (errors
+// accumulate over all evaluations of the call) and the work counters.
 static int begin_call(nnp_handle* h, cudaStream_t st)
 {
     h->launches = 0;
     h->evals = 0;
+    CK(h, cudaMemsetAsync(h->flags + FLAG_ERR, 0, sizeof(int), st));
     CK(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CNT_PER_CALL, st));
     return NNP_OK;
 }
@@ -884,6 +890,79 @@ __global__ void k_same(int n, const float* __restrict__ pos, const float* __rest
                    (__float_as_int(pos[3 * i + 1]) != __float_as_int(pc[3 * i + 1])) ||
                    (__float_as_int(pos[3 * i + 2]) != __float_as_int(pc[3 * i + 2])) || (t[i] != tc[i]);
     if (d) *diff = 1;
+}
+
+// One velocity-Verlet step: half kick and drift, evaluation of the new forces
+// and energy (into d_energy), second half kick, energy-log entry.  Every
+// decision that varies between steps (neighbour-list rebuild, wide-capacity
+// atoms, log entry) is taken on the device, so the launch sequence is the same
+// for every step of a call.
+static int md_step(nnp_handle* h, int n, float* pos, float* vel, const int* types, const double* box, float dt,
+                   int gke, double* log, cudaStream_t st)
+{
+    {
+        KScope ks(h, KG_INTEGRATE, st);
+        k_kick_drift<<<blocks_for(n, 256), 256, 0, st>>>(n, h->d_plan, types, h->F, vel, pos, dt);
+    }
+    int rc = run_eval(h, n, pos, types, box, st, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+    if (rc) return rc;
+    KScope ks(h, KG_INTEGRATE, st, 2);
+    k_kick_ke<<<gke, 256, 0, st>>>(n, h->d_plan, types, h->F, vel, dt, h->epart);
+    k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, h->d_energy, log, h->counters + CNT_LOGSLOT);
+    return NNP_OK;
+}
+
+// reps further steps: one step's launch sequence is captured (on the handle's own
+// stream, since the legacy default stream cannot be captured) into a CUDA graph,
+// which is launched reps times, ordered after and before the caller's stream by
+// events.  The executable graph is kept and updated in place while the captured
+// topology stays the same, so a call pays one capture (tens of microseconds) and
+// each step one graph launch instead of about twenty kernel launches.
+static int replay_steps(nnp_handle* h, int n, float* pos, float* vel, const int* types, const double* box, float dt,
+                        int gke, double* log, int reps, cudaStream_t st)
+{
+    if (!h->gstream) {
+        CK(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+        CK(h, cudaEventCreateWithFlags(&h->gfork, cudaEventDisableTiming));
+        CK(h, cudaEventCreateWithFlags(&h->gjoin, cudaEventDisableTiming));
+    }
+    const long long launches0 = h->launches;
+    const int evals0 = h->evals;
+    CK(h, cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
+    const int rc = md_step(h, n, pos, vel, types, box, dt, gke, log, h->gstream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(h->gstream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (ec != cudaSuccess) return set_err(h, NNP_ECUDA, "step graph capture: %s", cudaGetErrorString(ec));
+    if (h->gexec) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(h->gexec, g, &info) != cudaSuccess) {
+            cudaGetLastError();   // an update refused for a changed topology is not an error of the call
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+    }
+    if (!h->gexec) {
+        const cudaError_t ei = cudaGraphInstantiate(&h->gexec, g, 0);
+        if (ei != cudaSuccess) {
+            h->gexec = nullptr;
+            cudaGraphDestroy(g);
+            return set_err(h, NNP_ECUDA, "step graph instantiation: %s", cudaGetErrorString(ei));
+        }
+    }
+    cudaGraphDestroy(g);
+    CK(h, cudaEventRecord(h->gfork, st));
+    CK(h, cudaStreamWaitEvent(h->gstream, h->gfork, 0));
+    for (int r = 0; r < reps; ++r) CK(h, cudaGraphLaunch(h->gexec, h->gstream));
+    CK(h, cudaEventRecord(h->gjoin, h->gstream));
+    CK(h, cudaStreamWaitEvent(st, h->gjoin, 0));
+    // the capture counted one step's launches and evaluations
+    h->launches = launches0 + (h->launches - launches0) * reps;
+    h->evals = evals0 + (h->evals - evals0) * reps;
+    return NNP_OK;
 }
 
 // ---------------------------------------------------------------- public API
@@ -937,6 +1016,9 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
         // instead of the per-slot g buffer and the reverse-index gather
         const char* env = getenv("NNP_FORCE_SCATTER");
         h->scatter = env && env[0] == '1';
+        // NNP_STEP_GRAPH=0: nnp_step launches every kernel of every step itself
+        const char* genv = getenv("NNP_STEP_GRAPH");
+        h->step_graph = !(genv && genv[0] == '0');
     }
     DeviceGuard g(device);
     auto fail = [&](int code) {
@@ -1067,6 +1149,10 @@ int nnp_destroy(nnp_handle* h)
         if (p2) cudaFree(p2);
     if (h->pos_cache) cudaFree(h->pos_cache);
     if (h->types_cache) cudaFree(h->types_cache);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->gfork) cudaEventDestroy(h->gfork);
+    if (h->gjoin) cudaEventDestroy(h->gjoin);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     for (auto& p : h->pending) {
         h->ev_pool.push_back(p.a);
         h->ev_pool.push_back(p.b);
@@ -1160,29 +1246,28 @@ int nnp_step(nnp_handle* h, int n, float* pos, float* vel, const int* types, con
         }
         log = h->d_log;
     }
-    const int T = 256;
-    const int gke = std::min(blocks_for(n, T), 4 * h->num_sms);
+    const int gke = std::min(blocks_for(n, 256), 4 * h->num_sms);
     rc = ensure_red(h, gke, 0);
     if (rc) return rc;
     const float dt = (float)dt_fs;
     rc = begin_call(h, st);
     if (rc) return rc;
+    CK(h, cudaMemsetAsync(h->counters + CNT_LOGSLOT, 0, sizeof(unsigned long long), st));
     // continue from the previous nnp_step if its final state is bitwise unchanged
     bool cont = h->step_valid && h->step_n == n && h->step_pos == pos && h->step_types == types;
     for (int a = 0; a < 3; ++a) cont = cont && (h->step_box[a] == box[a]);
     if (cont) {
         CK(h, cudaMemsetAsync(h->flags + 2, 0, sizeof(int), st));
-        k_same<<<blocks_for(n, T), T, 0, st>>>(n, pos, h->pos_cache, types, h->types_cache, h->flags + 2);
+        k_same<<<blocks_for(n, 256), 256, 0, st>>>(n, pos, h->pos_cache, types, h->types_cache, h->flags + 2);
         h->launches++;
         CK(h, cudaMemcpyAsync(h->h_flags + 2, h->flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
         CK(h, cudaStreamSynchronize(st));
         cont = (h->h_flags[2] == 0);
     }
     h->step_valid = false;
-    if (cont) {
-        CK(h, cudaMemcpyAsync(log, h->d_energy, sizeof(double), cudaMemcpyDeviceToDevice, st));
-    } else {
-        rc = run_eval(h, n, pos, types, box, st, log, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+    // the energy of the starting state: still in d_energy when continuing
+    if (!cont) {
+        rc = run_eval(h, n, pos, types, box, st, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
         if (rc) return rc;
     }
     // the kinetic-energy partials reuse the energy partial buffer (same block count)
@@ -1190,26 +1275,26 @@ int nnp_step(nnp_handle* h, int n, float* pos, float* vel, const int* types, con
     if (rc) return rc;
     {
         KScope ks(h, KG_INTEGRATE, st, 2);
-        k_kick_ke<<<gke, T, 0, st>>>(n, h->d_plan, types, h->F, vel, 0.f, h->epart);
-        k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, log, 1);
+        k_kick_ke<<<gke, 256, 0, st>>>(n, h->d_plan, types, h->F, vel, 0.f, h->epart);
+        k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, h->d_energy, log, h->counters + CNT_LOGSLOT);
     }
-    for (int k = 1; k <= n_steps; ++k) {
-        {
-            KScope ks(h, KG_INTEGRATE, st);
-            k_kick_drift<<<blocks_for(n, T), T, 0, st>>>(n, h->d_plan, types, h->F, vel, pos, dt);
-        }
-        rc = run_eval(h, n, pos, types, box, st, log + 2 * k, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+    int k = 1;
+    if (n_steps >= 3 && h->step_graph && !h->prof_on) {
+        // the first step runs directly and settles every buffer; the rest repeat
+        // its launch sequence with the same arguments
+        rc = md_step(h, n, pos, vel, types, box, dt, gke, log, st);
         if (rc) return rc;
-        {
-            KScope ks(h, KG_INTEGRATE, st, 2);
-            k_kick_ke<<<gke, T, 0, st>>>(n, h->d_plan, types, h->F, vel, dt, h->epart);
-            k_log_sum<<<1, 256, 0, st>>>(gke, h->epart, log, 2 * k + 1);
-        }
+        rc = replay_steps(h, n, pos, vel, types, box, dt, gke, log, n_steps - 1, st);
+        if (rc) return rc;
+        k = n_steps + 1;
     }
-    // remember the final state for a continuing call
+    for (; k <= n_steps; ++k) {
+        rc = md_step(h, n, pos, vel, types, box, dt, gke, log, st);
+        if (rc) return rc;
+    }
+    // remember the final state for a continuing call (its energy stays in d_energy)
     CK(h, cudaMemcpyAsync(h->pos_cache, pos, sizeof(float) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, st));
     CK(h, cudaMemcpyAsync(h->types_cache, types, sizeof(int) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-    CK(h, cudaMemcpyAsync(h->d_energy, log + 2 * (size_t)n_steps, sizeof(double), cudaMemcpyDeviceToDevice, st));
     rc = read_status(h, st);
     if (rc) return rc;
     h->step_valid = true;
