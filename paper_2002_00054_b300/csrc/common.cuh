@@ -127,6 +127,13 @@ __device__ __forceinline__ void cutoff_fn_fast(float r, float hpi_rc, float& fc,
     dfc = -2.0f * hpi_rc * s * c;
 }
 
+// Packed FP32 pairs (one f32x2 instruction for two IEEE round-to-nearest
+// operations; each component is rounded exactly as the scalar operation).
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll

@@ -124,11 +124,12 @@ __host__ __device__ inline size_t sf_warp_bytes(int C)
 {
     return (size_t)C * (16 + 4 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2;
 }
-// PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).
+// PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).  The
+// last 80 bytes hold the warp's nine FP64 virial sums.
 __host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool res)
 {
     return (size_t)C * (16 + (pack ? 16 : 32) + 24) + PAIR_QUEUE * 2 + NNP_MAXG * 4 + (size_t)S * 2 +
-           (res ? (size_t)((C + 15) & ~15) : 0);
+           (res ? (size_t)((C + 15) & ~15) : 0) + 80;
 }
 
 // Fixed-point accumulation of the force pass.  A contribution v, |v| < FX_LIMIT
@@ -151,6 +152,27 @@ __device__ __forceinline__ void fx_split(float v, int& hi, int& lo)
     hi = __float_as_int(th) - __float_as_int(S);
     const float r = fmaf(th - S, -1.0f / 64.0f, v);
     lo = __float_as_int(fmaf(r, 134217728.0f, S)) - __float_as_int(S);
+}
+// Two contributions at once (packed f32x2 arithmetic, the same roundings).
+__device__ __forceinline__ void fx_split2(float2 v, int& hx, int& lx, int& hy, int& ly)
+{
+    const float S = 12582912.0f;
+    const float2 th = fma2(v, f2(64.0f, 64.0f), f2(S, S));
+    hx = __float_as_int(th.x) - __float_as_int(S);
+    hy = __float_as_int(th.y) - __float_as_int(S);
+    const float2 r = fma2(add2(th, f2(-S, -S)), f2(-1.0f / 64.0f, -1.0f / 64.0f), v);
+    const float2 tl = fma2(r, f2(134217728.0f, 134217728.0f), f2(S, S));
+    lx = __float_as_int(tl.x) - __float_as_int(S);
+    ly = __float_as_int(tl.y) - __float_as_int(S);
+}
+__device__ __forceinline__ void fx_add2(const WarpSmem& w, int ix, int iy, float2 v)
+{
+    int hx, lx, hy, ly;
+    fx_split2(v, hx, lx, hy, ly);
+    atomicAdd(&w.sgh[ix], hx);
+    atomicAdd(&w.sgl[ix], lx);
+    atomicAdd(&w.sgh[iy], hy);
+    atomicAdd(&w.sgl[iy], ly);
 }
 __device__ __forceinline__ void fx_set(const WarpSmem& w, int idx, float v)
 {
@@ -625,7 +647,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     constexpr bool PACK = NETA <= 2;
-    unsigned char* base = smem + force_warp_bytes(C, nv.stride, PACK, RES) * wib;
+    const size_t wbytes = force_warp_bytes(C, nv.stride, PACK, RES);
+    unsigned char* base = smem + wbytes * wib;
     WarpSmem w;
     w.nd = reinterpret_cast<float4*>(base);
     w.npf = w.nd + C;
@@ -642,9 +665,10 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     w.ninv = nullptr;
     w.nfe = nullptr;
 
-    double vir[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) vir[q] = 0.0;
+    // virial sums of the warp's atoms (FP64, in shared memory: registers stay free
+    // for the pair loop)
+    double* vir = reinterpret_cast<double*>(base + wbytes - 80);
+    if (lane < 9) vir[lane] = 0.0;
     const int nw = gridDim.x * wpb;
     const int n_items = atom_count(pass, n, spill);
     unsigned long long c_spill = 0;
@@ -690,17 +714,33 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         }
         const int ncls = RES ? E.n_cls : 1;
         for (int cls = 0; NETA > 0 && cls < ncls; ++cls) {
-            // dense weights W[q][l][k] = dE/dG_o * 2^(1-zeta), zeta = 2^k
-            float W[NETA > 0 ? NETA : 1][2][NNP_KMAX + 1];
+            // dense weights dE/dG_o * 2^(1-zeta), zeta = 2^k: WL[q][k] = (lambda = +1,
+            // lambda = -1) for k <= KLO, WT[q][k - KLO - 1] for the one lambda whose
+            // functions reach k > KLO (TX: lambda = +1); eta constants as pairs
+            // (q = 2p, 2p + 1; zero past n_eta)
+            constexpr int NQ = NETA > 0 ? NETA : 1, NP = (NQ + 1) / 2;
+            constexpr int KLO = KP < KN ? KP : KN, KM = KP > KN ? KP : KN;
+            constexpr bool TX = KP > KN;
+            float2 WL[NQ][KLO + 1];
+            float WT[NQ][KM - KLO + 1];
 #pragma unroll
-            for (int q = 0; q < (NETA > 0 ? NETA : 1); ++q)
+            for (int q = 0; q < NQ; ++q)
 #pragma unroll
-                for (int l = 0; l < 2; ++l)
+                for (int kk = 0; kk <= KM; ++kk) {
+                    const int op = (q < E.n_eta && kk <= KP) ? E.ang_out[cls][q][0][kk] : -1;
+                    const int om = (q < E.n_eta && kk <= KN) ? E.ang_out[cls][q][1][kk] : -1;
+                    const float sc = exp2f((float)(1 - (1 << kk)));
+                    const float wp = (op >= 0) ? sW[op] * sc : 0.f, wm = (om >= 0) ? sW[om] * sc : 0.f;
+                    if (kk <= KLO) WL[q][kk] = f2(wp, wm);
+                    else WT[q][kk - KLO - 1] = TX ? wp : wm;
+                }
+            float2 KH[NP], KL[NP], ET[NP];
 #pragma unroll
-                    for (int kk = 0; kk <= NNP_KMAX; ++kk) {
-                        const int o = (q < E.n_eta) ? E.ang_out[cls][q][l][kk] : -1;
-                        W[q][l][kk] = (o >= 0) ? sW[o] * exp2f((float)(1 - (1 << kk))) : 0.f;
-                    }
+            for (int p = 0; p < NP; ++p) {
+                KH[p] = f2(khi[2 * p], (2 * p + 1 < 4) ? khi[2 * p + 1] : 0.f);
+                KL[p] = f2(klo[2 * p], (2 * p + 1 < 4) ? klo[2 * p + 1] : 0.f);
+                ET[p] = f2(-2.0f * etav[2 * p], (2 * p + 1 < 4) ? -2.0f * etav[2 * p + 1] : 0.f);
+            }
             const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             int bp = QHDR, qpos = queue_entries_start(nb);
             for (int A = 0; A < nb; ++A) {
@@ -738,18 +778,20 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             const int j = 32 * A + l, k = 32 * B + ((l + s) & 31);
                             const float4 a = w.nd[j], b = w.nd[k];
                             const float ia = a.w, ib = b.w;
-                            float pav[4], qav[4], pbv[4], qbv[4];
+                            // P_q and dP_q/dr of both neighbours as eta pairs (zero past NETA)
+                            float2 PA[NP], QA[NP], PB[NP], QB[NP];
                             if (PACK) {
                                 const float4 pa4 = w.npf[j], pb4 = w.npf[k];
-                                pav[0] = pa4.x; pav[1] = pa4.y; qav[0] = pa4.z; qav[1] = pa4.w;
-                                pbv[0] = pb4.x; pbv[1] = pb4.y; qbv[0] = pb4.z; qbv[1] = pb4.w;
-                                pav[2] = pav[3] = qav[2] = qav[3] = pbv[2] = pbv[3] = qbv[2] = qbv[3] = 0.f;
+                                PA[0] = f2(pa4.x, pa4.y); QA[0] = f2(pa4.z, pa4.w);
+                                PB[0] = f2(pb4.x, pb4.y); QB[0] = f2(pb4.z, pb4.w);
                             } else {
                                 const float4 pa4 = w.npf[j], qa4 = w.ndp[j], pb4 = w.npf[k], qb4 = w.ndp[k];
-                                pav[0] = pa4.x; pav[1] = pa4.y; pav[2] = pa4.z; pav[3] = pa4.w;
-                                qav[0] = qa4.x; qav[1] = qa4.y; qav[2] = qa4.z; qav[3] = qa4.w;
-                                pbv[0] = pb4.x; pbv[1] = pb4.y; pbv[2] = pb4.z; pbv[3] = pb4.w;
-                                qbv[0] = qb4.x; qbv[1] = qb4.y; qbv[2] = qb4.z; qbv[3] = qb4.w;
+                                PA[0] = f2(pa4.x, pa4.y); QA[0] = f2(qa4.x, qa4.y);
+                                PB[0] = f2(pb4.x, pb4.y); QB[0] = f2(qb4.x, qb4.y);
+                                if (NP > 1) {
+                                    PA[NP - 1] = f2(pa4.z, pa4.w); QA[NP - 1] = f2(qa4.z, qa4.w);
+                                    PB[NP - 1] = f2(pb4.z, pb4.w); QB[NP - 1] = f2(qb4.z, qb4.w);
+                                }
                             }
                             const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
                             const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * (ia * ib);
@@ -760,50 +802,77 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                 rd = rd2 * ird;
                                 cutoff_fn_fast(rd, P.hpi_rc, fcd, dfcd);
                             }
-                            // pw[l][k] = b_l^(2^k); qs[l][k] = lambda_l 2^k b_l^(2^k - 1) = d pw / dc,
-                            // b_l = 1 + lambda_l c (shared by every eta)
-                            float pw[2][NNP_KMAX + 1], qs[2][NNP_KMAX + 1];
+                            // PW[k] = (b_+^(2^k), b_-^(2^k)), QS[k] = d PW[k] / dc, b_(+/-) = 1 +/- c
+                            // (both lambdas in one packed chain up to KLO, then the one that goes on;
+                            // shared by every eta)
+                            float2 PW[KLO + 1], QS[KLO + 1];
+                            PW[0] = fma2(f2(c, c), f2(1.f, -1.f), f2(1.f, 1.f));
+                            QS[0] = f2(1.f, -1.f);
+                            float2 QK = PW[0];
 #pragma unroll
-                            for (int lb = 0; lb < 2; ++lb) {
-                                const float bl = (lb == 0) ? 1.f + c : 1.f - c;
-                                float qk = 1.f;
-                                pw[lb][0] = bl;
-                                qs[lb][0] = (lb == 0) ? 1.f : -1.f;
+                            for (int kk = 1; kk <= KLO; ++kk) {
+                                if (kk > 1) QK = mul2(QK, PW[kk - 1]);
+                                PW[kk] = mul2(PW[kk - 1], PW[kk - 1]);
+                                QS[kk] = mul2(QK, f2((float)(1 << kk), -(float)(1 << kk)));
+                            }
+                            float pt[KM - KLO + 1], qt[KM - KLO + 1];
+                            {
+                                float pw = TX ? PW[KLO].x : PW[KLO].y;
+                                float qk = TX ? QK.x : QK.y;
 #pragma unroll
-                                for (int kk = 1; kk <= NNP_KMAX; ++kk) {
-                                    if (kk <= (lb == 0 ? KP : KN)) {
-                                        qk = qk * pw[lb][kk - 1];
-                                        pw[lb][kk] = pw[lb][kk - 1] * pw[lb][kk - 1];
-                                        qs[lb][kk] = qk * ((lb == 0 ? 1.f : -1.f) * (float)(1 << kk));
-                                    }
+                                for (int kk = KLO + 1; kk <= KM; ++kk) {
+                                    if (kk > 1) qk *= pw;
+                                    pw *= pw;
+                                    pt[kk - KLO - 1] = pw;
+                                    qt[kk - KLO - 1] = qk * (TX ? (float)(1 << kk) : -(float)(1 << kk));
                                 }
                             }
-                            float phic = 0.f, phia = 0.f, phib = 0.f, phid = 0.f;
+                            // S_q = sum W pw, D_q = dS_q/dc (lambda pairs summed at the end)
+                            float Sq[2 * NP], Dq[2 * NP];
 #pragma unroll
-                            for (int q = 0; q < NETA; ++q) {
-                                float S = 0.f, D = 0.f;
+                            for (int q = 0; q < 2 * NP; ++q) {
+                                Sq[q] = 0.f;
+                                Dq[q] = 0.f;
+                                if (q < NQ) {
+                                    float2 s2 = mul2(WL[q][0], PW[0]), d2 = mul2(WL[q][0], QS[0]);
 #pragma unroll
-                                for (int lb = 0; lb < 2; ++lb)
-#pragma unroll
-                                    for (int kk = 0; kk <= NNP_KMAX; ++kk) {
-                                        if (kk <= (lb == 0 ? KP : KN)) {
-                                            S = fmaf(W[q][lb][kk], pw[lb][kk], S);
-                                            D = fmaf(W[q][lb][kk], qs[lb][kk], D);
-                                        }
+                                    for (int kk = 1; kk <= KLO; ++kk) {
+                                        s2 = fma2(WL[q][kk], PW[kk], s2);
+                                        d2 = fma2(WL[q][kk], QS[kk], d2);
                                     }
-                                float Pd = 1.f, dPd = 0.f;
+                                    float st = TX ? s2.x : s2.y, dt = TX ? d2.x : d2.y;
+#pragma unroll
+                                    for (int kk = KLO + 1; kk <= KM; ++kk) {
+                                        st = fmaf(WT[q][kk - KLO - 1], pt[kk - KLO - 1], st);
+                                        dt = fmaf(WT[q][kk - KLO - 1], qt[kk - KLO - 1], dt);
+                                    }
+                                    Sq[q] = TX ? st + s2.y : s2.x + st;
+                                    Dq[q] = TX ? dt + d2.y : d2.x + dt;
+                                }
+                            }
+                            float2 phic2 = f2(0.f, 0.f), phia2 = f2(0.f, 0.f), phib2 = f2(0.f, 0.f), phid2 = f2(0.f, 0.f);
+#pragma unroll
+                            for (int p = 0; p < NP; ++p) {
+                                const float2 S2 = f2(Sq[2 * p], Sq[2 * p + 1]), D2 = f2(Dq[2 * p], Dq[2 * p + 1]);
+                                const float2 pab = mul2(PA[p], PB[p]);
+                                float2 SPd = S2, pabPd = pab;
                                 if (NARROW) {
-                                    const float ed = gauss2(khi[q], klo[q], rd2);
-                                    Pd = ed * fcd;
-                                    dPd = ed * (dfcd - 2.0f * etav[q] * rd * fcd);
+                                    const float2 x2 = f2(rd2, rd2);
+                                    const float2 arg = fma2(KH[p], x2, mul2(KL[p], x2));
+                                    const float2 ed = f2(exp2f(arg.x), (2 * p + 1 < NQ) ? exp2f(arg.y) : 0.f);
+                                    const float2 Pd = mul2(ed, f2(fcd, fcd));
+                                    const float rf = rd * fcd;
+                                    const float2 dPd = mul2(ed, fma2(ET[p], f2(rf, rf), f2(dfcd, dfcd)));
+                                    pabPd = mul2(pab, Pd);
+                                    SPd = mul2(S2, Pd);
+                                    phid2 = fma2(mul2(S2, pab), dPd, phid2);
                                 }
-                                const float pab = pav[q] * pbv[q];
-                                phic = fmaf(D, pab * Pd, phic);
-                                const float SPd = S * Pd;
-                                phia = fmaf(SPd * qav[q], pbv[q], phia);
-                                phib = fmaf(SPd * pav[q], qbv[q], phib);
-                                if (NARROW) phid = fmaf(S * pab, dPd, phid);
+                                phic2 = fma2(D2, pabPd, phic2);
+                                phia2 = fma2(mul2(SPd, QA[p]), PB[p], phia2);
+                                phib2 = fma2(mul2(SPd, PA[p]), QB[p], phib2);
                             }
+                            const float phic = phic2.x + phic2.y, phia = phia2.x + phia2.y;
+                            const float phib = phib2.x + phib2.y, phid = phid2.x + phid2.y;
                             // g_a = phic (b/(ra rb) - c a/ra^2) + phia a/ra - phid (b - a)/rd
                             // g_b = phic (a/(ra rb) - c b/rb^2) + phib b/rb + phid (b - a)/rd
                             const float pc = phic * c;
@@ -816,12 +885,14 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             // |e| = rd); likewise for g_b
                             fx_bad |= !(fabsf(ua) + fabsf(ta) + fabsf(phid) < FX_LIMIT &&
                                         fabsf(ub) + fabsf(tb) + fabsf(phid) < FX_LIMIT);
-                            fx_add(w, 3 * j + 0, ca * a.x + cab * b.x - cd * ex);
-                            fx_add(w, 3 * j + 1, ca * a.y + cab * b.y - cd * ey);
-                            fx_add(w, 3 * j + 2, ca * a.z + cab * b.z - cd * ez);
-                            fx_add(w, 3 * k + 0, cb * b.x + cab * a.x + cd * ex);
-                            fx_add(w, 3 * k + 1, cb * b.y + cab * a.y + cd * ey);
-                            fx_add(w, 3 * k + 2, cb * b.z + cab * a.z + cd * ez);
+                            // (x, y) of g_a and of g_b, and (z of g_a, z of g_b), as packed pairs
+                            const float2 axy = f2(a.x, a.y), bxy = f2(b.x, b.y), exy = f2(ex, ey);
+                            const float2 gaxy = fma2(f2(ca, ca), axy, fma2(f2(cab, cab), bxy, mul2(f2(-cd, -cd), exy)));
+                            const float2 gbxy = fma2(f2(cb, cb), bxy, fma2(f2(cab, cab), axy, mul2(f2(cd, cd), exy)));
+                            const float2 gz = fma2(f2(ca, cb), f2(a.z, b.z), fma2(f2(cab, cab), f2(b.z, a.z), mul2(f2(-cd, cd), f2(ez, ez))));
+                            fx_add2(w, 3 * j + 0, 3 * j + 1, gaxy);
+                            fx_add2(w, 3 * k + 0, 3 * k + 1, gbxy);
+                            fx_add2(w, 3 * j + 2, 3 * k + 2, gz);
                         }
                     }
                     __syncwarp();
@@ -864,7 +935,10 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         }
         fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) vir[q] += (double)warp_sum(v[q]);
+        for (int q = 0; q < 9; ++q) {
+            const float t = warp_sum(v[q]);
+            if (lane == q) vir[q] += (double)t;
+        }
         if (lane == 0) {
             if (Fscat) {
                 atomicAdd(Fscat + 3 * (size_t)i + 0, fx);
@@ -877,11 +951,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         __syncwarp();
     }
     if (__any_sync(FULL, fx_bad) && lane == 0) atomicOr(&flags[FLAG_ERR], ERR_RANGE);
-    if (lane == 0) {
-        const int gw = blockIdx.x * wpb + wib;
-#pragma unroll
-        for (int q = 0; q < 9; ++q) vir_part[(size_t)gw * 9 + q] = vir[q];
-    }
+    __syncwarp();
+    if (lane < 9) vir_part[(size_t)(blockIdx.x * wpb + wib) * 9 + lane] = vir[lane];
 }
 
 // F_m = Fown_m - sum_s g[nbr(m, s), rev(m, s)]   (no atomics, fixed order)
