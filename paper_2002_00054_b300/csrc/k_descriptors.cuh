@@ -297,6 +297,15 @@ __device__ __forceinline__ unsigned valid_mask(int A, int B, int l, int M)
     return m;
 }
 
+// |b - a|^2 with the x and y differences and squares as packed pairs
+__device__ __forceinline__ float dist2_jk(const float4 a, const float4 b)
+{
+    const float2 d = add2(f2(b.x, b.y), f2(-a.x, -a.y));
+    const float2 d2 = mul2(d, d);
+    const float ez = b.z - a.z;
+    return fmaf(ez, ez, d2.x + d2.y);
+}
+
 // Bitmask over s of the contributing partners of lane l's j in block (A, B).
 // A full partner block (32 present) is walked with a fixed, unrolled trip count
 // (s = 1..16 on the diagonal); a partial one by scanning its valid bits.
@@ -310,27 +319,19 @@ __device__ __forceinline__ unsigned live_mask(int A, int B, int l, int M, const 
     if (32 * B + 32 <= M) {
         if (A == B) {
 #pragma unroll
-            for (int s = 1; s <= 16; ++s) {
-                const float4 b = blk[(l + s) & 31];
-                const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
-                if (ex * ex + ey * ey + ez * ez < rc2) mask |= 1u << s;
-            }
+            for (int s = 1; s <= 16; ++s)
+                if (dist2_jk(a, blk[(l + s) & 31]) < rc2) mask |= 1u << s;
         } else {
 #pragma unroll
-            for (int s = 0; s < 32; ++s) {
-                const float4 b = blk[(l + s) & 31];
-                const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
-                if (ex * ex + ey * ey + ez * ez < rc2) mask |= 1u << s;
-            }
+            for (int s = 0; s < 32; ++s)
+                if (dist2_jk(a, blk[(l + s) & 31]) < rc2) mask |= 1u << s;
         }
         return mask & v;
     }
     while (v) {
         const int s = __ffs(v) - 1;
         v &= v - 1u;
-        const float4 b = blk[(l + s) & 31];
-        const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
-        if (ex * ex + ey * ey + ez * ez < rc2) mask |= 1u << s;
+        if (dist2_jk(a, blk[(l + s) & 31]) < rc2) mask |= 1u << s;
     }
     return mask;
 }
@@ -480,15 +481,22 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         // angular (one pass per neighbour-element pair class)
         const int ncls = RES ? E.n_cls : 1;
         for (int cls = 0; NETA > 0 && cls < ncls; ++cls) {
-            constexpr int NQ = NETA > 0 ? NETA : 1;
+            constexpr int NQ = NETA > 0 ? NETA : 1, NP = (NQ + 1) / 2;
             constexpr int NA = NQ * 2 * (NNP_KMAX + 1);   // dense accumulators, index (q*2 + l)*(KMAX+1) + k
-            float acc[NQ][2][NNP_KMAX + 1];
+            // accumulators of eta pairs (q = 2p, 2p + 1) as packed f32x2
+            float2 acc[NP][2][NNP_KMAX + 1];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q)
+            for (int p = 0; p < NP; ++p)
 #pragma unroll
                 for (int l = 0; l < 2; ++l)
 #pragma unroll
-                    for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[q][l][kk] = 0.f;
+                    for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[p][l][kk] = f2(0.f, 0.f);
+            float2 KH[NP], KL[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                KH[p] = f2(khi[2 * p], (2 * p + 1 < 4) ? khi[2 * p + 1] : 0.f);
+                KL[p] = f2(klo[2 * p], (2 * p + 1 < 4) ? klo[2 * p + 1] : 0.f);
+            }
             const int nb = (M + 31) >> 5;
             const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             // where this atom's queue record goes (nullptr: not stored)
@@ -546,7 +554,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                             const int j = 32 * A + l, k = 32 * B + ((l + sidx) & 31);
                             const float4 a = w.nd[j], b = w.nd[k];
                             const float4 pa4 = w.npf[j], pb4 = w.npf[k];
-                            const float pav[4] = {pa4.x, pa4.y, pa4.z, pa4.w}, pbv[4] = {pb4.x, pb4.y, pb4.z, pb4.w};
+                            const float2 PA[2] = {f2(pa4.x, pa4.y), f2(pa4.z, pa4.w)};
+                            const float2 PB[2] = {f2(pb4.x, pb4.y), f2(pb4.z, pb4.w)};
                             const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * (w.ninv[j] * w.ninv[k]);
                             float fcd = 1.f, rd2 = 0.f;
                             if (NARROW) {
@@ -555,23 +564,58 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                                 float dfcd;
                                 cutoff_fn_fast(rd2 * rsqrtf(rd2), P.hpi_rc, fcd, dfcd);
                             }
+                            // b_(+/-)^(2^k), b_(+/-) = 1 +/- c: both lambdas in one packed chain
+                            // while both go on
+                            constexpr int KLO = KP < KN ? KP : KN;
                             float pw[2][NNP_KMAX + 1];
-                            pw[0][0] = 1.f + c;
-                            pw[1][0] = 1.f - c;
+                            float2 pp = fma2(f2(c, c), f2(1.f, -1.f), f2(1.f, 1.f));
+                            pw[0][0] = pp.x;
+                            pw[1][0] = pp.y;
 #pragma unroll
                             for (int kk = 1; kk <= NNP_KMAX; ++kk) {
-                                if (kk <= KP) pw[0][kk] = pw[0][kk - 1] * pw[0][kk - 1];
-                                if (kk <= KN) pw[1][kk] = pw[1][kk - 1] * pw[1][kk - 1];
+                                if (kk <= KLO) {
+                                    pp = mul2(pp, pp);
+                                    pw[0][kk] = pp.x;
+                                    pw[1][kk] = pp.y;
+                                } else {
+                                    if (kk <= KP) pw[0][kk] = pw[0][kk - 1] * pw[0][kk - 1];
+                                    if (kk <= KN) pw[1][kk] = pw[1][kk - 1] * pw[1][kk - 1];
+                                }
                             }
+                            if constexpr (NETA % 2 == 0) {
+                                // even eta count: both of a pair in one packed instruction
 #pragma unroll
-                            for (int q = 0; q < NETA; ++q) {
-                                float R = pav[q] * pbv[q];
-                                if (NARROW) R *= gauss2(khi[q], klo[q], rd2) * fcd;
+                                for (int p = 0; p < NP; ++p) {
+                                    float2 R = mul2(PA[p], PB[p]);
+                                    if (NARROW) {
+                                        const float2 x2 = f2(rd2, rd2);
+                                        const float2 arg = fma2(KH[p], x2, mul2(KL[p], x2));
+                                        R = mul2(R, mul2(f2(exp2f(arg.x), exp2f(arg.y)), f2(fcd, fcd)));
+                                    }
 #pragma unroll
-                                for (int lb = 0; lb < 2; ++lb)
+                                    for (int lb = 0; lb < 2; ++lb)
 #pragma unroll
-                                    for (int kk = 0; kk <= NNP_KMAX; ++kk)
-                                        if (kk <= (lb == 0 ? KP : KN)) acc[q][lb][kk] = fmaf(pw[lb][kk], R, acc[q][lb][kk]);
+                                        for (int kk = 0; kk <= NNP_KMAX; ++kk)
+                                            if (kk <= (lb == 0 ? KP : KN))
+                                                acc[p][lb][kk] = fma2(f2(pw[lb][kk], pw[lb][kk]), R, acc[p][lb][kk]);
+                                }
+                            } else {
+                                // odd eta count: a padded pair would cost more than it saves
+#pragma unroll
+                                for (int q = 0; q < NETA; ++q) {
+                                    const float2 pa = PA[q >> 1], pb = PB[q >> 1];
+                                    float R = (q & 1) ? pa.y * pb.y : pa.x * pb.x;
+                                    if (NARROW) R *= gauss2(khi[q], klo[q], rd2) * fcd;
+#pragma unroll
+                                    for (int lb = 0; lb < 2; ++lb)
+#pragma unroll
+                                        for (int kk = 0; kk <= NNP_KMAX; ++kk)
+                                            if (kk <= (lb == 0 ? KP : KN)) {
+                                                float2& a2 = acc[q >> 1][lb][kk];
+                                                if (q & 1) a2.y = fmaf(pw[lb][kk], R, a2.y);
+                                                else a2.x = fmaf(pw[lb][kk], R, a2.x);
+                                            }
+                                }
                             }
                         }
                     }
@@ -586,8 +630,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
                     const int idx = c0 + t;
-                    v[t] = (idx < NA) ? acc[idx / (2 * (NNP_KMAX + 1))][(idx / (NNP_KMAX + 1)) % 2][idx % (NNP_KMAX + 1)]
-                                      : 0.f;
+                    const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
+                    v[t] = (idx < NA) ? ((q & 1) ? acc[q >> 1][l][kk].y : acc[q >> 1][l][kk].x) : 0.f;
                 }
                 const double tot = warp_reduce_scatter32(v, lane);
                 const int idx = c0 + lane;
