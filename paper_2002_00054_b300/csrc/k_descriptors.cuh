@@ -741,6 +741,17 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                                   n_list, sig);
         if (over_capacity(M, C, pass, i, spill, false, lane, flags, c_spill)) continue;
         const int nb = (M + 31) >> 5;
+        // largest 1/r of the staged neighbours (for the range bound below)
+        float iam = 0.f;
+        bool nonfin = false;
+        for (int m = lane; m < M; m += 32) {
+            const float x = w.nd[m].w;
+            iam = fmaxf(iam, x);
+            nonfin |= !(x < INFINITY);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) iam = fmaxf(iam, __shfl_xor_sync(FULL, iam, o));
+        nonfin = __any_sync(FULL, nonfin);
         // the descriptor pass's queue record, used when this staging reproduces it
         const unsigned short* rec = nullptr;
         if (STORED && NETA > 0) {
@@ -785,6 +796,27 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 KL[p] = f2(klo[2 * p], (2 * p + 1 < 4) ? klo[2 * p + 1] : 0.f);
                 ET[p] = f2(-2.0f * etav[2 * p], (2 * p + 1 < 4) ? -2.0f * etav[2 * p + 1] : 0.f);
             }
+            // A bound on every triplet contribution of this atom and class: with
+            // b = 1 +/- c <= 2, |b^zeta| <= 2^zeta and |d b^zeta / dc| <= zeta 2^(zeta-1);
+            // P <= 1 and |dP/dr| <= pi/(2 rc) + 2 eta rc for every neighbour and (narrow)
+            // for r_jk < rc; so |phia|, |phib|, |phid| <= sum_q Smax_q Qmax_q, |phic| <=
+            // sum_q Dmax_q, and each component of g_a, g_b is at most |phia| + 2 |phic| /
+            // r_min + |phid|.  The per-triplet range test runs only when the bound (with a
+            // factor 2 of margin) does not hold or is not finite.
+            float bnd = 0.f;
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                float sm = 0.f, dm = 0.f;
+#pragma unroll
+                for (int kk = 0; kk <= KM; ++kk) {
+                    const float a = (kk <= KLO) ? fabsf(WL[q][kk].x) + fabsf(WL[q][kk].y) : fabsf(WT[q][kk - KLO - 1]);
+                    sm += a * (float)(1 << (1 << kk));
+                    dm += a * (float)(1 << (kk + (1 << kk) - 1));
+                }
+                const float qm = P.hpi_rc + 2.f * etav[q] * P.rc;
+                bnd += sm * qm * (NARROW ? 2.f : 1.f) + 2.f * iam * dm;
+            }
+            const bool exact = nonfin || !(bnd < 0.5f * FX_LIMIT);
             const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             int bp = QHDR, qpos = queue_entries_start(nb);
             for (int A = 0; A < nb; ++A) {
@@ -927,8 +959,9 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             const float cd = NARROW ? phid * ird : 0.f;
                             // every component of g_a is at most |u_a| + |phic / ra| + |phid| (|a| = ra,
                             // |e| = rd); likewise for g_b
-                            fx_bad |= !(fabsf(ua) + fabsf(ta) + fabsf(phid) < FX_LIMIT &&
-                                        fabsf(ub) + fabsf(tb) + fabsf(phid) < FX_LIMIT);
+                            if (exact)
+                                fx_bad |= !(fabsf(ua) + fabsf(ta) + fabsf(phid) < FX_LIMIT &&
+                                            fabsf(ub) + fabsf(tb) + fabsf(phid) < FX_LIMIT);
                             // (x, y) of g_a and of g_b, and (z of g_a, z of g_b), as packed pairs
                             const float2 axy = f2(a.x, a.y), bxy = f2(b.x, b.y), exy = f2(ex, ey);
                             const float2 gaxy = fma2(f2(ca, ca), axy, fma2(f2(cab, cab), bxy, mul2(f2(-cd, -cd), exy)));

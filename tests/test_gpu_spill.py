@@ -122,6 +122,29 @@ def test_spilled_atoms_in_static_entry():
     assert np.abs(f.double().cpu().numpy() - ref["F"]).max() <= F_ABS
 
 
+def test_large_forces_take_the_exact_range_test():
+    """Output-layer weights x 3000 (forces up to ~8000 eV/A): for about a third
+    of the atoms the per-atom bound on the triplet contributions exceeds half the
+    fixed-point range, so the force kernel tests each contribution; the bound
+    itself stays below the range, so no contribution fails the test, and the
+    forces of both kinds of atoms match the oracle (tolerances x 3000)."""
+    from paper_2002_00054_b300 import NNP
+    scale = 3000.0
+    m = workloads.water_model()
+    w = [x.copy() for x in m["weights"]]
+    for x in w:
+        x[-26:-1] *= scale
+    big = dict(m, weights=w)
+    pos, types, box = workloads.water_random()
+    p, t = to_dev(f32(pos), types)
+    out = NNP(big).compute(p, t, f32(box))
+    ref = oracle.compute(big, f32(pos), types, f32(box))
+    dF = np.abs(out["F"].double().cpu().numpy() - ref["F"]).max()
+    assert dF <= scale * F_ABS, dF
+    dE = np.abs(out["Ei"].double().cpu().numpy() - ref["Ei"]).max()
+    assert dE <= 1e-5 * np.abs(ref["Ei"]).max(), dE
+
+
 def test_force_contribution_out_of_range_is_an_error():
     """Force contributions are summed in fixed point (|v| < 32000 eV/A per
     contribution); a model whose forces exceed that range fails the call with
