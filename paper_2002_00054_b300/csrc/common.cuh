@@ -99,6 +99,15 @@ struct Plan {
     int s_elem;              // floats per element in the shared-memory image
     int p_woff[NNP_MAXL], p_boff[NNP_MAXL];  // packed (caller) layout offsets
     int n_params_elem;
+    // image of the lane-per-atom FP32 network kernel, per element (floats): hidden
+    // layer l: lw_f[l] = W_l^T [in_l][lw_hp] (zero columns past out_l), lw_fb[l] =
+    // bias [lw_hp], lw_b[l] = W_l [lw_hp][K_l] (zero rows past out_l and columns past
+    // in_l; K_0 = lw_kb0, K_l = lw_hp for l > 0); output layer lw_out = w [lw_kb0
+    // or lw_hp], lw_outb = bias; lw_invs = 1/s [lw_kb0].  lw_hp: largest hidden width
+    // rounded up to 4; lw_kb0: n_G rounded up to 32; element stride lw_elem = 4 mod
+    // 32 words; lw_rows: activation rows per warp (n_G + hidden widths).
+    int lw_f[NNP_MAXL], lw_fb[NNP_MAXL], lw_b[NNP_MAXL];
+    int lw_out, lw_outb, lw_invs, lw_elem, lw_rows, lw_hp, lw_kb0;
     int gs;                  // row stride of G / dEdG buffers
     ElemPlan e[NNP_MAXE];
 };

@@ -37,6 +37,23 @@ void split(double x, float& hi, float& lo)
 
 }  // namespace
 
+typedef void (*MlpKernel)(int, const float4*, const Plan*, const float*, const float*, float*, float*);
+
+// FP32 network kernel for hidden widths up to hp (a multiple of 4, at most 32)
+static MlpKernel pick_mlp(int hp)
+{
+    switch (hp) {
+    case 4: return k_mlp_fp32<4>;
+    case 8: return k_mlp_fp32<8>;
+    case 12: return k_mlp_fp32<12>;
+    case 16: return k_mlp_fp32<16>;
+    case 20: return k_mlp_fp32<20>;
+    case 24: return k_mlp_fp32<24>;
+    case 28: return k_mlp_fp32<28>;
+    default: return k_mlp_fp32<32>;
+    }
+}
+
 struct nnp_handle {
     int device = 0;
     Plan plan;
@@ -117,6 +134,7 @@ struct nnp_handle {
     int max_smem = 0;
     int wpb_sf = 8, wpb_force = 8, wpb_tan = 4;
     size_t smem_sf = 0, smem_force = 0, smem_mlp = 0;
+    MlpKernel kmlp = nullptr;   // FP32 network, instantiated for the hidden width
     int grid_sf = 0, grid_force = 0, grid_mlp = 0;
     int cap_rc = 0;   // main launches: neighbours inside the cutoff staged per warp (set_capacity)
     // wide-capacity pass over the atoms above cap_rc (capacity = list stride)
@@ -215,6 +233,31 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
     }
     P.s_elem = (soff + 3) & ~3;
     P.n_params_elem = poff;
+    {
+        int hp = 4;
+        for (int l = 1; l < p->n_layers; ++l) hp = std::max(hp, (p->widths[l] + 3) & ~3);
+        P.lw_hp = hp;
+        P.lw_kb0 = (ng + 31) & ~31;
+        int lo = 0, rows = ng;
+        for (int l = 0; l + 1 < p->n_layers; ++l) {
+            const int in = p->widths[l];
+            P.lw_f[l] = lo;
+            lo += in * hp;
+            P.lw_fb[l] = lo;
+            lo += hp;
+            P.lw_b[l] = lo;
+            lo += hp * (l == 0 ? P.lw_kb0 : hp);
+            rows += p->widths[l + 1];
+        }
+        P.lw_out = lo;
+        lo += (p->n_layers > 1) ? hp : P.lw_kb0;
+        P.lw_outb = lo;
+        lo += 4;
+        P.lw_invs = lo;
+        lo += P.lw_kb0;
+        P.lw_elem = ((lo + 27) / 32) * 32 + 4;
+        P.lw_rows = rows;
+    }
     n_params = poff * p->n_elements;
     for (int i = 0; i < n_params; ++i)
         if (!std::isfinite(p->weights[i])) return fail("weights must be finite");
@@ -826,8 +869,8 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
                                                 h->Ei, h->dEdG, h->flags);
     } else {
         KScope ks(h, KG_MLP, st);
-        const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
-        k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, h->pos4, h->d_plan, h->d_w, h->G, h->Ei, h->dEdG);
+        const int gmlp = std::min(blocks_for(n, 128), h->grid_mlp);
+        h->kmlp<<<gmlp, 128, h->smem_mlp, st>>>(n, h->pos4, h->d_plan, h->d_w, h->G, h->Ei, h->dEdG);
     }
     if (dEdG_out) CK(h, cudaMemcpy2DAsync(dEdG_out, sizeof(float) * P.width[0], h->dEdG, sizeof(float) * P.gs,
                                           sizeof(float) * P.width[0], n, cudaMemcpyDeviceToDevice, st));
@@ -1070,7 +1113,9 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
         h->smem_force_sp = pf * h->wpb_force_sp;
         h->grid_sp = h->num_sms;
     }
-    h->smem_mlp = sizeof(float) * (size_t)P.s_elem * P.n_elem;
+    // weight images of every element, then four warps' activation rows
+    h->smem_mlp = sizeof(float) * ((size_t)P.lw_elem * P.n_elem + 4 * (size_t)P.lw_rows * 33);
+    h->kmlp = pick_mlp(P.lw_hp);
     if (h->smem_mlp > (size_t)max_smem) {
         set_err(h, NNP_EUNSUPPORTED, "network weights do not fit in shared memory");
         return fail(NNP_EUNSUPPORTED);
@@ -1087,7 +1132,7 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
         CKC(cudaFuncSetAttribute((const void*)fs3, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     }
     CKC(cudaFuncSetAttribute((const void*)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
-    CKC(cudaFuncSetAttribute((const void*)k_mlp_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    CKC(cudaFuncSetAttribute((const void*)h->kmlp, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     if (h->precision == NNP_BF16) {
         auto r16 = [](int x) { return (x + 15) & ~15; };
         h->tcs = TcShape{r16(P.width[0]), r16(P.width[1]), r16(P.width[2])};
@@ -1127,7 +1172,7 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
         if (set_capacity(h, c) != NNP_OK) return fail(NNP_EINVAL);
     }
     int bs = 0;
-    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)k_mlp_fp32, 256, h->smem_mlp));
+    CKC(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)h->kmlp, 128, h->smem_mlp));
     h->grid_mlp = std::max(1, bs) * h->num_sms;
 #undef CKC
     *out = h;
@@ -1642,8 +1687,8 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
                                                  spill, 0, nullptr, nullptr, 0ull);
     ksf<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, G, nullptr, flags, counters,
                                                              spill, 1, nullptr, nullptr, 0ull);
-    const int gmlp = std::min(blocks_for(n, 8), h->grid_mlp);
-    k_mlp_fp32<<<gmlp, 256, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
+    const int gmlp = std::min(blocks_for(n, 128), h->grid_mlp);
+    h->kmlp<<<gmlp, 128, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
     kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, vpart,
                                                      flags, spill, 0, nullptr, nullptr, nullptr);
     kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, dEdG, gbuf, Fown,
