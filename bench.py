@@ -58,8 +58,8 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # atom: list rows, positions, pair-queue records and the per-slot g buffer all
 # scale with atoms).  Valid only for the kernel sources with this hash;
 # otherwise traffic is null.
-TRAFFIC = {"force": (469.229824e6 + 227.259136e6) / 110592, "descriptors": (84.415488e6 + 328.769792e6) / 110592}
-TRAFFIC_SRC_SHA = "866fd782cab1"
+TRAFFIC = {"force": (470.480128e6 + 228.633088e6) / 110592, "descriptors": (84.052992e6 + 328.640768e6) / 110592}
+TRAFFIC_SRC_SHA = "2a290bec11ff"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
