@@ -111,13 +111,16 @@ typedef struct nnp_handle nnp_handle;
 /* Creates a handle on CUDA device 'device': validates and copies the parameters
  * (host memory may be freed afterwards).  *out is NULL on failure.  Parameter
  * validation happens before any CUDA call.  Scratch grows on demand later.
- * Force assembly: by default each atom writes its pair contributions g_ij per
- * neighbour-list slot and forces are gathered per atom through the reverse
- * index, in a fixed order (bitwise reproducible, no global atomics).  With the
- * environment variable NNP_FORCE_SCATTER=1, read here, contributions are added
- * into the forces with global float atomics instead (the scatter form of the
- * paper's CabanaMD code): no reverse index or g buffer, sums in the order the
- * atomics land. */
+ * Force assembly: by default each atom adds its pair contributions -g_ij into
+ * the forces of its neighbours as 64-bit fixed-point integers (units 2^-27
+ * eV/A) with global integer atomics; integer sums do not depend on the order of
+ * the atomics, so forces are reproducible bit for bit, and each component is
+ * rounded to float once.  Environment variables read here select the other
+ * forms: NNP_FORCE_GATHER=1 writes g_ij per neighbour-list slot and gathers the
+ * forces per atom through a reverse index (fixed order, float sums; the reverse
+ * index and slot buffer take 20 bytes per list slot), NNP_FORCE_SCATTER=1 adds
+ * floats with global atomics (the scatter form of the paper's CabanaMD code;
+ * sums in the order the atomics land). */
 NNP_API int nnp_create(const nnp_params* params, int device, nnp_handle** out);
 
 /* Frees the handle and its device memory (waits for its pending work).  NULL is a no-op. */

@@ -192,6 +192,11 @@ __device__ __forceinline__ float fx_get(const WarpSmem& w, int idx)
 {
     return fmaf((float)w.sgl[idx], 1.0f / 134217728.0f, (float)w.sgh[idx] * (1.0f / 64.0f));
 }
+// the same sum as one integer in units of 2^-27 eV/A (exact: |value| < 2^52)
+__device__ __forceinline__ long long fx_get64(const WarpSmem& w, int idx)
+{
+    return (long long)w.sgh[idx] * 2097152LL + (long long)w.sgl[idx];
+}
 
 // Stages the neighbours of atom i within the cutoff, compacted in list order.
 // Returns M.  FORCE: nd.w = 1/r, dP/dr, the radial part of g (into sg), slot map.
@@ -684,7 +689,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
         double* __restrict__ vir_part, int* __restrict__ flags, int* __restrict__ spill, int pass,
         const unsigned short* __restrict__ qpool, const unsigned int* __restrict__ qoff,
-        float* __restrict__ Fscat)
+        float* __restrict__ Fscat, unsigned long long* __restrict__ Fq)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -977,10 +982,24 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             }
         }
         __syncwarp();
-        // write g per list slot (or, with Fscat, add -g_ij to F_j with global
-        // atomics: the scatter form), own force and virial
+        // force assembly: with Fq, -g_ij is added into F_j as one 64-bit integer per
+        // component (units 2^-27 eV/A; integer sums do not depend on the order of
+        // the atomics, so the forces are reproducible bit for bit); with Fscat, as
+        // floats (order-dependent); otherwise g is written per list slot for the
+        // gather.  Then the own force and the virial.
         const int cnt = n_list;
-        if (Fscat) {
+        if (Fq) {
+            const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
+            for (int s = lane; s < cnt; s += 32) {
+                const int c = w.cmap[s];
+                if (c >= 0) {
+                    unsigned long long* fj = Fq + 3 * (size_t)(row[s] & NB_INDEX_MASK);
+                    atomicAdd(fj + 0, (unsigned long long)(-fx_get64(w, 3 * c)));
+                    atomicAdd(fj + 1, (unsigned long long)(-fx_get64(w, 3 * c + 1)));
+                    atomicAdd(fj + 2, (unsigned long long)(-fx_get64(w, 3 * c + 2)));
+                }
+            }
+        } else if (Fscat) {
             const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
             for (int s = lane; s < cnt; s += 32) {
                 const int c = w.cmap[s];
@@ -1000,23 +1019,44 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             }
         }
         float fx = 0.f, fy = 0.f, fz = 0.f, v[9];
+        long long qx = 0, qy = 0, qz = 0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) v[q] = 0.f;
         for (int m = lane; m < M; m += 32) {
             const float4 d = w.nd[m];
             const float gx = fx_get(w, 3 * m), gy = fx_get(w, 3 * m + 1), gz = fx_get(w, 3 * m + 2);
-            fx += gx; fy += gy; fz += gz;
+            if (Fq) {
+                qx += fx_get64(w, 3 * m);
+                qy += fx_get64(w, 3 * m + 1);
+                qz += fx_get64(w, 3 * m + 2);
+            } else {
+                fx += gx; fy += gy; fz += gz;
+            }
             v[0] -= d.x * gx; v[1] -= d.x * gy; v[2] -= d.x * gz;
             v[3] -= d.y * gx; v[4] -= d.y * gy; v[5] -= d.y * gz;
             v[6] -= d.z * gx; v[7] -= d.z * gy; v[8] -= d.z * gz;
         }
-        fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
             const float t = warp_sum(v[q]);
             if (lane == q) vir[q] += (double)t;
         }
-        if (lane == 0) {
+        if (Fq) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                qx += __shfl_xor_sync(FULL, qx, o);
+                qy += __shfl_xor_sync(FULL, qy, o);
+                qz += __shfl_xor_sync(FULL, qz, o);
+            }
+            if (lane == 0) {
+                atomicAdd(Fq + 3 * (size_t)i + 0, (unsigned long long)qx);
+                atomicAdd(Fq + 3 * (size_t)i + 1, (unsigned long long)qy);
+                atomicAdd(Fq + 3 * (size_t)i + 2, (unsigned long long)qz);
+            }
+        } else {
+            fx = warp_sum(fx); fy = warp_sum(fy); fz = warp_sum(fz);
+        }
+        if (lane == 0 && !Fq) {
             if (Fscat) {
                 atomicAdd(Fscat + 3 * (size_t)i + 0, fx);
                 atomicAdd(Fscat + 3 * (size_t)i + 1, fy);

@@ -54,6 +54,8 @@ static MlpKernel pick_mlp(int hp)
     }
 }
 
+enum { FM_FIXED = 0, FM_GATHER = 1, FM_FLOAT = 2 };
+
 struct nnp_handle {
     int device = 0;
     Plan plan;
@@ -151,7 +153,11 @@ struct nnp_handle {
     size_t want_qpool = 0;     // entries the next evaluation should have (0: estimate)
     unsigned int* qoff = nullptr;   // [cap_n] record offset / 8 per atom
     unsigned short* seg = nullptr;  // [cap_n][NB_SEG] stencil segments of cell-built rows
-    bool scatter = false;           // forces by global atomics instead of the g buffer + gather
+    // force assembly: FM_FIXED (default) 64-bit fixed-point integer atomics into
+    // Fq; FM_GATHER per-slot g buffer and reverse-index gather; FM_FLOAT float
+    // atomics (order-dependent)
+    int fmode = 0;
+    unsigned long long* Fq = nullptr;   // [cap_n][3], units 2^-27 eV/A
     // nnp_step: the per-step launch sequence captured as a CUDA graph and replayed
     bool step_graph = true;
     cudaStream_t gstream = nullptr;   // capture and replay stream (non-blocking, owned)
@@ -378,7 +384,8 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
 typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, float*, float*, int*, unsigned long long*,
                          int*, int, unsigned short*, unsigned int*, unsigned long long);
 typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
-                            double*, int*, int*, int, const unsigned short*, const unsigned int*, float*);
+                            double*, int*, int*, int, const unsigned short*, const unsigned int*, float*,
+                            unsigned long long*);
 
 typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*, int*, int);
 
@@ -536,9 +543,12 @@ static int ensure_atoms(nnp_handle* h, int n)
     CK(h, regrow(h->F, (size_t)cap * 3));
     CK(h, regrow(h->nbr, rows));
     CK(h, regrow(h->ncount, cap));
-    CK(h, regrow(h->rev, rows));
+    if (h->fmode == FM_GATHER) {   // reverse index and g buffer: the gather form only
+        CK(h, regrow(h->rev, rows));
+        CK(h, regrow(h->gbuf, rows));
+    }
+    CK(h, regrow(h->Fq, (size_t)cap * 3));
     CK(h, regrow(h->seg, (size_t)cap * NB_SEG));
-    CK(h, regrow(h->gbuf, rows));
     CK(h, regrow(h->cell_of, cap));
     CK(h, regrow(h->cell_atoms, cap));
     CK(h, regrow(h->pos_cache, (size_t)cap * 3));
@@ -811,14 +821,14 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
             k_rows_cell<<<rows_grid, 256, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_start,
                                                    h->cell_atoms, P.rcut2, h->stride, h->nbr, h->ncount, h->seg,
                                                    h->flags);
-            if (!h->scatter) k_rev_cell<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->seg, h->rev,
+            if (h->fmode == FM_GATHER) k_rev_cell<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->seg, h->rev,
                                                                    h->flags);
-            h->launches += h->scatter ? 5 : 6;
+            h->launches += (h->fmode == FM_GATHER) ? 6 : 5;
         } else {
             k_rows_brute<<<rows_grid, 256, 0, st>>>(n, h->pos4, bt ? h->sys_of : nullptr, bt ? h->sys_start_d : nullptr,
                                                     h->sys_box, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
-            if (!h->scatter) k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
-            h->launches += h->scatter ? 1 : 2;
+            if (h->fmode == FM_GATHER) k_rev<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->rev, h->flags);
+            h->launches += (h->fmode == FM_GATHER) ? 2 : 1;
         }
     }
     h->list_valid = true;
@@ -881,24 +891,30 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     const int gred = std::min(blocks_for(n, T), 4 * h->num_sms);
     rc = ensure_red(h, gred, nvp);
     if (rc) return rc;
-    // the scatter form adds every contribution into the force output directly
-    float* Fsc = h->scatter ? (F_out ? F_out : h->F) : nullptr;
+    // the scatter forms add every contribution into the force sums directly
+    float* Fout = F_out ? F_out : h->F;
+    float* Fsc = (h->fmode == FM_FLOAT) ? Fout : nullptr;
+    unsigned long long* Fq = (h->fmode == FM_FIXED) ? h->Fq : nullptr;
     if (Fsc) CK(h, cudaMemsetAsync(Fsc, 0, sizeof(float) * 3 * (size_t)n, st));
+    if (Fq) CK(h, cudaMemsetAsync(Fq, 0, sizeof(unsigned long long) * 3 * (size_t)n, st));
     {
         KScope ks(h, KG_FORCE, st, 2);
         // main pass over the stored queues (atoms without one join the wide pass)
         const bool stored = P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW && !P.resolved && h->qpool;
         (stored ? kfs : kf)<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
             n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, h->vpart, h->flags, h->spill, 0,
-            stored ? h->qpool : nullptr, stored ? h->qoff : nullptr, Fsc);
+            stored ? h->qpool : nullptr, stored ? h->qoff : nullptr, Fsc, Fq);
         kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride,
                                                                        h->dEdG, h->gbuf, h->Fown,
                                                                        h->vpart + (size_t)nvp_main * 9, h->flags,
-                                                                       h->spill, 1, nullptr, nullptr, Fsc);
+                                                                       h->spill, 1, nullptr, nullptr, Fsc, Fq);
     }
-    if (!Fsc) {
+    if (h->fmode == FM_GATHER) {
         KScope ks(h, KG_GATHER, st);
-        k_gather<<<rows_grid, 256, 0, st>>>(n, nv, h->rev, h->gbuf, h->Fown, F_out ? F_out : h->F, h->flags);
+        k_gather<<<rows_grid, 256, 0, st>>>(n, nv, h->rev, h->gbuf, h->Fown, Fout, h->flags);
+    } else if (Fq) {
+        KScope ks(h, KG_GATHER, st);
+        k_fq_forces<<<blocks_for(3 * n, 256), 256, 0, st>>>(3 * n, Fq, Fout);
     }
     if (bt) {
         KScope ks(h, KG_REDUCE, st);
@@ -1055,10 +1071,12 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     h->stride = (params->max_neighbors + 7) & ~7;   // multiple of 8 keeps per-warp shared arrays 16-byte aligned
     h->precision = params->mlp_precision;
     {
-        // NNP_FORCE_SCATTER=1: forces by global atomics (the paper's CabanaMD form)
-        // instead of the per-slot g buffer and the reverse-index gather
+        // force assembly (default: fixed-point integer atomics, reproducible);
+        // NNP_FORCE_GATHER=1: per-slot g buffer and reverse-index gather;
+        // NNP_FORCE_SCATTER=1: float atomics (the paper's CabanaMD form)
         const char* env = getenv("NNP_FORCE_SCATTER");
-        h->scatter = env && env[0] == '1';
+        const char* genv2 = getenv("NNP_FORCE_GATHER");
+        h->fmode = (genv2 && genv2[0] == '1') ? FM_GATHER : (env && env[0] == '1') ? FM_FLOAT : FM_FIXED;
         // NNP_STEP_GRAPH=0: nnp_step launches every kernel of every step itself
         const char* genv = getenv("NNP_STEP_GRAPH");
         h->step_graph = !(genv && genv[0] == '0');
@@ -1190,7 +1208,7 @@ int nnp_destroy(nnp_handle* h)
     for (void* p : dev)
         if (p) cudaFree(p);
     for (void* p2 : {(void*)h->sys_of, (void*)h->sys_start_d, (void*)h->T, (void*)h->gpart, (void*)h->spill,
-                     (void*)h->qpool, (void*)h->qoff, (void*)h->seg})
+                     (void*)h->qpool, (void*)h->qoff, (void*)h->seg, (void*)h->Fq})
         if (p2) cudaFree(p2);
     if (h->pos_cache) cudaFree(h->pos_cache);
     if (h->types_cache) cudaFree(h->types_cache);
@@ -1690,9 +1708,10 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     const int gmlp = std::min(blocks_for(n, 128), h->grid_mlp);
     h->kmlp<<<gmlp, 128, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
     kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, vpart,
-                                                     flags, spill, 0, nullptr, nullptr, nullptr);
+                                                     flags, spill, 0, nullptr, nullptr, nullptr, nullptr);
     kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, dEdG, gbuf, Fown,
-                                                                   vpart + (size_t)nvp_main * 9, flags, spill, 1, nullptr, nullptr, nullptr);
+                                                                   vpart + (size_t)nvp_main * 9, flags, spill, 1, nullptr, nullptr, nullptr,
+                                                                   nullptr);
     k_gather<<<rows_grid, 256, 0, st>>>(n, nv, rev, gbuf, Fown, forces ? forces : Fs, flags);
     k_sum_partial<<<gred, T, 0, st>>>(n, Ei, epart, flags);
     k_finalize<<<1, 256, 0, st>>>(gred, epart, energy, nvp, vpart, nullptr);

@@ -193,11 +193,15 @@ def test_box_too_small(water_nnp):
 
 
 @pytest.mark.parametrize("name", ["water", "fcc"])
-def test_scatter_forces_match_gather(name, monkeypatch):
-    """NNP_FORCE_SCATTER=1 adds every pair's contribution into the forces with
-    global atomics (the paper's scatter form) instead of the per-slot g buffer
-    and the reverse-index gather: the same forces up to summation order, and the
-    same parity with the oracle."""
+@pytest.mark.parametrize("form", ["gather", "float"])
+def test_force_assembly_forms_agree(name, form, monkeypatch):
+    """The default force assembly adds -g_ij into F_j as 64-bit fixed-point
+    integers (exact, order-independent sums, one rounding per component);
+    NNP_FORCE_GATHER=1 writes g per list slot and gathers through the reverse
+    index, NNP_FORCE_SCATTER=1 adds floats with global atomics (the paper's
+    scatter form).  Same energies, forces equal up to float summation order,
+    the same parity with the oracle, and MD steps (neighbour rebuilds with or
+    without a reverse index) keep it."""
     from paper_2002_00054_b300 import NNP
     if name == "water":
         m, (pos, types, box) = workloads.water_model(), workloads.water_lattice((2, 2, 2), seed=5)
@@ -205,16 +209,23 @@ def test_scatter_forces_match_gather(name, monkeypatch):
         m, (pos, types, box) = workloads.fcc_model(), workloads.fcc((6, 6, 6), sigma=0.1, seed=6)
     pos, box = f32(pos), f32(box)
     p, t = to_dev(pos, types)
-    gat = NNP(m).compute(p, t, box)
-    monkeypatch.setenv("NNP_FORCE_SCATTER", "1")
-    sc_h = NNP(m)
-    sc = sc_h.compute(p, t, box)
-    assert torch.equal(gat["Ei"], sc["Ei"])
-    assert (gat["F"] - sc["F"]).abs().max().item() <= 2e-6
-    check(sc, oracle.compute(m, pos, types, box), what="%s scatter" % name)
-    # continued MD steps with the scatter form (rebuilds without a reverse index)
-    v = torch.zeros_like(p)
-    x = p.clone()
-    sc_h.step(x, v, t, box, 0.5, 5)
-    ref = oracle.compute(m, x.double().cpu().numpy(), types, box)
-    check(sc_h.compute(x, t, box), ref, what="%s scatter after steps" % name)
+    fixed_h = NNP(m)
+    fx = fixed_h.compute(p, t, box)
+    fx2 = fixed_h.compute(p, t, box)
+    assert torch.equal(fx["F"], fx2["F"])          # reproducible bit for bit
+    monkeypatch.setenv("NNP_FORCE_GATHER" if form == "gather" else "NNP_FORCE_SCATTER", "1")
+    o_h = NNP(m)
+    monkeypatch.delenv("NNP_FORCE_GATHER" if form == "gather" else "NNP_FORCE_SCATTER")
+    ot = o_h.compute(p, t, box)
+    assert torch.equal(fx["Ei"], ot["Ei"])
+    assert (fx["F"] - ot["F"]).abs().max().item() <= 2e-6
+    ref = oracle.compute(m, pos, types, box)
+    check(fx, ref, what="%s fixed-point scatter" % name)
+    check(ot, ref, what="%s %s" % (name, form))
+    # continued MD steps with both forms from the same start
+    for h in (fixed_h, o_h):
+        v = torch.zeros_like(p)
+        x = p.clone()
+        h.step(x, v, t, box, 0.5, 5)
+        check(h.compute(x, t, box), oracle.compute(m, x.double().cpu().numpy(), types, box),
+              what="%s after steps" % name)
