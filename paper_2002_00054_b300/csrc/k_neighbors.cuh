@@ -124,10 +124,12 @@ __global__ void k_cell_fill(int n, const int* __restrict__ cell_of, int* __restr
     cell_atoms[slot] = i;
 }
 
-// Deterministic order inside each cell (ascending atom index): warp per cell, rank sort.
+// Deterministic order inside each cell (ascending atom index): warp per cell, rank
+// sort; the positions are written in the same order (cpos), so the row builder
+// reads an atom's index and position with independent loads.
 #define CELL_CAP 256
 __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start, int* __restrict__ cell_atoms,
-                            int* __restrict__ flags)
+                            const float4* __restrict__ pos4, float4* __restrict__ cpos, int* __restrict__ flags)
 {
     if (!flags[FLAG_REBUILD]) return;
     __shared__ int buf[8][CELL_CAP];
@@ -145,6 +147,7 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start, int* 
             int v = buf[w][k], rank = 0;
             for (int q = 0; q < cnt; ++q) rank += (buf[w][q] < v);
             cell_atoms[s0 + rank] = v;
+            cpos[s0 + rank] = pos4[v];
         }
         __syncwarp();
     }
@@ -157,11 +160,15 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start, int* 
 #define NB_SEG 28
 __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int ncx, int ncy, int ncz,
                             const int* __restrict__ cell_start, const int* __restrict__ cell_atoms,
+                            const float4* __restrict__ cpos,
                             float rcut2, int stride, uint32_t* __restrict__ nbr, int* __restrict__ ncount,
                             unsigned short* __restrict__ seg, int* __restrict__ flags)
 {
     if (!flags[FLAG_REBUILD]) return;
+    // per warp: how many stencil cells start at each position of the current round
+    __shared__ int hist[8][32];   // blockDim.x <= 256
     const int lane = threadIdx.x & 31;
+    int* hc = hist[threadIdx.x >> 5];
     const int nw = gridDim.x * (blockDim.x >> 5);
     for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
         const float4 pi = pos4[i];
@@ -170,6 +177,7 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
         // lane t < 27: stencil cell t = (dz+1)*9 + (dy+1)*3 + (dx+1), its atom range
         // and periodic shift; then an exclusive scan of the cell sizes
         int b0 = 0, len = 0, code = 62;   // code of shift (0, 0, 0)
+        float ox = 0.f, oy = 0.f, oz = 0.f;
         if (lane < 27) {
             const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
             int x = cx + dx, y = cy + dy, z = cz + dz, sx = 0, sy = 0, sz = 0;
@@ -180,6 +188,9 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
             b0 = cell_start[c];
             len = cell_start[c + 1] - b0;
             code = (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2);
+            ox = (float)sx * box.L[0];
+            oy = (float)sy * box.L[1];
+            oz = (float)sz * box.L[2];
         }
         int pre = len;   // inclusive scan over lanes
 #pragma unroll
@@ -191,24 +202,34 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
         pre -= len;   // first flat candidate index of cell `lane`
         // candidates of all 27 cells in stencil order, 32 per round
         int cnt = 0, my_seg = 0;
+        int c_before = 0;   // stencil cells u >= 1 whose first index lies before the round
         for (int f0 = 0; f0 < total; f0 += 32) {
             const int f = f0 + lane;
-            // cell of candidate f: the last t whose first index is <= f
-            int t = 0;
+            // cell of candidate f: the number of cells u >= 1 with first index <= f
+            // (first indices do not decrease with u), from a count of the cells
+            // starting at each position of the round and an inclusive scan
+            hc[lane] = 0;
+            __syncwarp();
+            if (lane >= 1 && lane < 27 && pre >= f0 && pre < f0 + 32) atomicAdd(&hc[pre - f0], 1);
+            __syncwarp();
+            int cum = hc[lane];
 #pragma unroll
-            for (int u = 1; u < 27; ++u)
-                if (__shfl_sync(FULL, pre, u) <= f) t = u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, cum, o);
+                if (lane >= o) cum += v;
+            }
+            const int t = c_before + cum;
+            c_before += __shfl_sync(FULL, cum, 31);
             const int tb0 = __shfl_sync(FULL, b0, t), tpre = __shfl_sync(FULL, pre, t);
             const int tcode = __shfl_sync(FULL, code, t);
+            const float tox = __shfl_sync(FULL, ox, t), toy = __shfl_sync(FULL, oy, t), toz = __shfl_sync(FULL, oz, t);
             bool keep = false;
             int j = 0;
             if (f < total) {
                 j = cell_atoms[tb0 + (f - tpre)];
-                const float4 pj = pos4[j];
-                const int sx = tcode / 25 - 2, sy = (tcode / 5) % 5 - 2, sz = tcode % 5 - 2;
-                const float ox = (float)sx * box.L[0], oy = (float)sy * box.L[1], oz = (float)sz * box.L[2];
-                const float ddx = pair_disp(pj.x, pi.x, ox), ddy = pair_disp(pj.y, pi.y, oy),
-                            ddz = pair_disp(pj.z, pi.z, oz);
+                const float4 pj = cpos[tb0 + (f - tpre)];
+                const float ddx = pair_disp(pj.x, pi.x, tox), ddy = pair_disp(pj.y, pi.y, toy),
+                            ddz = pair_disp(pj.z, pi.z, toz);
                 const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                 keep = (r2 < rcut2) && !(j == i && tcode == 62);
             }

@@ -74,6 +74,7 @@ struct nnp_handle {
     uint32_t* nbr = nullptr;
     int *ncount = nullptr, *rev = nullptr, *cell_of = nullptr, *cell_atoms = nullptr;
     float4* gbuf = nullptr;
+    float4* cpos = nullptr;   // positions in cell order (row builder)
     // cells
     int cap_cells = 0;
     int *cell_count = nullptr, *cell_start = nullptr, *cursor = nullptr;
@@ -551,6 +552,7 @@ static int ensure_atoms(nnp_handle* h, int n)
     CK(h, regrow(h->seg, (size_t)cap * NB_SEG));
     CK(h, regrow(h->cell_of, cap));
     CK(h, regrow(h->cell_atoms, cap));
+    CK(h, regrow(h->cpos, cap));
     CK(h, regrow(h->pos_cache, (size_t)cap * 3));
     CK(h, regrow(h->types_cache, cap));
     CK(h, regrow(h->elem_idx, cap));
@@ -816,11 +818,11 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
                                                          h->cell_count, h->flags);
             k_cell_scan<<<1, 1024, 0, st>>>(ncell, h->cell_count, h->cell_start, h->cursor, h->flags);
             k_cell_fill<<<blocks_for(n, T), T, 0, st>>>(n, h->cell_of, h->cursor, h->cell_atoms, h->flags);
-            k_cell_sort<<<std::min(blocks_for(ncell, 8), h->num_sms * 8), 256, 0, st>>>(ncell, h->cell_start,
-                                                                                        h->cell_atoms, h->flags);
+            k_cell_sort<<<std::min(blocks_for(ncell, 8), h->num_sms * 8), 256, 0, st>>>(
+                ncell, h->cell_start, h->cell_atoms, h->pos4, h->cpos, h->flags);
             k_rows_cell<<<rows_grid, 256, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_start,
-                                                   h->cell_atoms, P.rcut2, h->stride, h->nbr, h->ncount, h->seg,
-                                                   h->flags);
+                                                   h->cell_atoms, h->cpos, P.rcut2, h->stride, h->nbr, h->ncount,
+                                                   h->seg, h->flags);
             if (h->fmode == FM_GATHER) k_rev_cell<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->seg, h->rev,
                                                                    h->flags);
             h->launches += (h->fmode == FM_GATHER) ? 6 : 5;
@@ -1203,7 +1205,7 @@ int nnp_destroy(nnp_handle* h)
     DeviceGuard g(h->device);
     cudaDeviceSynchronize();
     void* dev[] = {h->elem_idx, h->elem_part, h->elem_off, h->d_plan, h->d_w, h->off, h->ref, h->pos4, h->Fown, h->G, h->dEdG, h->Ei, h->F, h->nbr,
-                   h->ncount, h->rev, h->cell_of, h->cell_atoms, h->gbuf, h->cell_count, h->cell_start, h->cursor,
+                   h->ncount, h->rev, h->cell_of, h->cell_atoms, h->cpos, h->gbuf, h->cell_count, h->cell_start, h->cursor,
                    h->epart, h->vpart, h->d_energy, h->d_log, h->flags, h->counters, h->sys_box};
     for (void* p : dev)
         if (p) cudaFree(p);
