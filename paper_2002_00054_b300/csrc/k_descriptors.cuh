@@ -103,8 +103,10 @@ __device__ __forceinline__ bool over_capacity(int M, int C, int pass, int i, int
 
 // Per-warp shared-memory arrays (C = capacity inside the cutoff, S = list stride).
 struct WarpSmem {
-    float4* nd;     // (dx, dy, dz, r) (descriptor pass) or (dx, dy, dz, 1/r) (force pass)
+    float4* nd;     // (dx, dy, dz, h) (descriptor pass) or (dx, dy, dz, 1/r) (force pass)
     float* ninv;    // 1 / r (descriptor pass)
+    float* nr;      // r (descriptor pass)
+    float* nh;      // h = r^2 / 2 - rc^2 / 4 (force passes that rebuild the live masks)
     float4* npf;    // P_q; force pass with <= 2 eta: (P_0, P_1, dP_0/dr, dP_1/dr)
     float4* ndp;    // dP_q / dr (force pass with > 2 eta)
     float2* nfe;    // (f_c, element) (descriptor pass)
@@ -122,14 +124,15 @@ static_assert(NNP_MAXRAD * 20 <= PAIR_QUEUE * 2, "radial table must fit the queu
 
 __host__ __device__ inline size_t sf_warp_bytes(int C)
 {
-    return (size_t)C * (16 + 4 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2;
+    return (size_t)C * (16 + 8 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2;
 }
-// PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).  The
-// last 80 bytes hold the warp's nine FP64 virial sums.
-__host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool res)
+// PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).  STORED
+// (queues from the descriptor pass) needs no h array.  The last 80 bytes hold
+// the warp's nine FP64 virial sums.
+__host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool res, bool stored = false)
 {
     return (size_t)C * (16 + (pack ? 16 : 32) + 24) + PAIR_QUEUE * 2 + NNP_MAXG * 4 + (size_t)S * 2 +
-           (res ? (size_t)((C + 15) & ~15) : 0) + 80;
+           (res ? (size_t)((C + 15) & ~15) : 0) + (stored ? 0 : (size_t)C * 4) + 80;
 }
 
 // Fixed-point accumulation of the force pass.  A contribution v, |v| < FX_LIMIT
@@ -198,6 +201,17 @@ __device__ __forceinline__ long long fx_get64(const WarpSmem& w, int idx)
     return (long long)w.sgh[idx] * 2097152LL + (long long)w.sgl[idx];
 }
 
+// Narrow-kind live test r_jk < rc written with h = r^2 / 2 - rc^2 / 4 of each
+// neighbour: |b - a|^2 < rc^2  <=>  a . b - h_b > h_a.  Three FMAs and a compare
+// per pair; the roundings are explicit, so every kernel that rebuilds a live mask
+// keeps exactly the pairs the descriptor pass kept.
+__device__ __forceinline__ float live_h(float r2, float rc2) { return fmaf(r2, 0.5f, -0.25f * rc2); }
+__device__ __forceinline__ float dist2_fma(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
+__device__ __forceinline__ bool live_pair(const float4 a, float ha, const float4 b, float hb)
+{
+    return fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, -hb))) > ha;
+}
+
 // Stages the neighbours of atom i within the cutoff, compacted in list order.
 // Returns M.  FORCE: nd.w = 1/r, dP/dr, the radial part of g (into sg), slot map.
 template <int NETA, bool FORCE>
@@ -227,7 +241,7 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
             dx = pair_disp(pj.x, pi.x, ox);
             dy = pair_disp(pj.y, pi.y, oy);
             dz = pair_disp(pj.z, pi.z, oz);
-            r2 = dx * dx + dy * dy + dz * dz;
+            r2 = dist2_fma(dx, dy, dz);   // explicit roundings: every pass keeps the same neighbours
             ej = __float_as_int(pj.w);
             keep = r2 < P.rc2;
         }
@@ -248,13 +262,16 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                 pq[q] = ex * fc;
                 dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
             }
+            const float hh = live_h(r2, P.rc2);
             if (!FORCE) {
                 w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
-                w.nd[at] = make_float4(dx, dy, dz, r);
+                w.nd[at] = make_float4(dx, dy, dz, hh);
                 w.ninv[at] = ir;
+                w.nr[at] = r;
                 w.nfe[at] = make_float2(fc, __int_as_float(ej));
             } else {
                 w.nd[at] = make_float4(dx, dy, dz, ir);
+                if (w.nh) w.nh[at] = hh;
                 if (NETA <= 2) {
                     w.npf[at] = make_float4(pq[0], pq[1], dq[0], dq[1]);
                 } else {
@@ -302,41 +319,43 @@ __device__ __forceinline__ unsigned valid_mask(int A, int B, int l, int M)
     return m;
 }
 
-// |b - a|^2 with the x and y differences and squares as packed pairs
-__device__ __forceinline__ float dist2_jk(const float4 a, const float4 b)
-{
-    const float2 d = add2(f2(b.x, b.y), f2(-a.x, -a.y));
-    const float2 d2 = mul2(d, d);
-    const float ez = b.z - a.z;
-    return fmaf(ez, ez, d2.x + d2.y);
-}
-
 // Bitmask over s of the contributing partners of lane l's j in block (A, B).
 // A full partner block (32 present) is walked with a fixed, unrolled trip count
-// (s = 1..16 on the diagonal); a partial one by scanning its valid bits.
-template <bool NARROW>
-__device__ __forceinline__ unsigned live_mask(int A, int B, int l, int M, const float4 a, const float4* nd, float rc2)
+// (s = 1..16 on the diagonal); a partial one by scanning its valid bits.  h of
+// the partners: nd[k].w (HS = 0) or nh[HS * k] (HS > 0).
+template <bool NARROW, int HS>
+__device__ __forceinline__ unsigned live_mask(int A, int B, int l, int M, const float4 a, float ha, const float4* nd,
+                                              const float* nh)
 {
     unsigned v = valid_mask(A, B, l, M);
     if (!NARROW) return v;
     const float4* blk = nd + 32 * B;
+    auto hk = [&](int k, const float4& b) { return HS == 0 ? b.w : nh[HS * (32 * B + k)]; };
     unsigned mask = 0u;
     if (32 * B + 32 <= M) {
         if (A == B) {
 #pragma unroll
-            for (int s = 1; s <= 16; ++s)
-                if (dist2_jk(a, blk[(l + s) & 31]) < rc2) mask |= 1u << s;
+            for (int s = 1; s <= 16; ++s) {
+                const int k = (l + s) & 31;
+                const float4 b = blk[k];
+                if (live_pair(a, ha, b, hk(k, b))) mask |= 1u << s;
+            }
         } else {
 #pragma unroll
-            for (int s = 0; s < 32; ++s)
-                if (dist2_jk(a, blk[(l + s) & 31]) < rc2) mask |= 1u << s;
+            for (int s = 0; s < 32; ++s) {
+                const int k = (l + s) & 31;
+                const float4 b = blk[k];
+                if (live_pair(a, ha, b, hk(k, b))) mask |= 1u << s;
+            }
         }
         return mask & v;
     }
     while (v) {
         const int s = __ffs(v) - 1;
         v &= v - 1u;
-        if (dist2_jk(a, blk[(l + s) & 31]) < rc2) mask |= 1u << s;
+        const int k = (l + s) & 31;
+        const float4 b = blk[k];
+        if (live_pair(a, ha, b, hk(k, b))) mask |= 1u << s;
     }
     return mask;
 }
@@ -413,8 +432,10 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     w.npf = w.nd + C;
     double* sG = reinterpret_cast<double*>(w.npf + C);
     w.ninv = reinterpret_cast<float*>(sG + NNP_MAXG);
-    w.nfe = reinterpret_cast<float2*>(w.ninv + C);
+    w.nr = w.ninv + C;
+    w.nfe = reinterpret_cast<float2*>(w.nr + C);
     w.queue = reinterpret_cast<unsigned short*>(w.nfe + C);
+    w.nh = nullptr;
     w.ndp = nullptr;
     w.sgh = nullptr;
     w.sgl = nullptr;
@@ -468,7 +489,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 const int el = act ? E.rad_elem[rr] : -2;
                 float sum = 0.f, comp = 0.f;
                 for (int m = hf; m < M; m += halves) {
-                    const float r = w.nd[m].w;
+                    const float r = w.nr[m];
                     const float2 fe = w.nfe[m];
                     if (el == -1 || el == __float_as_int(fe.y)) {
                         const float x = r - rs;
@@ -536,7 +557,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int ej = (RES && jl < M) ? __float_as_int(w.nfe[jl].y) : -1;
                 for (int B = A; B < nb; ++B, ++bp) {
-                    unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
+                    unsigned mask = live_mask<NARROW, 0>(A, B, lane, M, al, al.w, w.nd, nullptr);
                     if (cls == 0) c_trip += __popc(mask);
                     if (RES && ce1 >= 0) {
                         const int kl = 32 * B + lane;
@@ -696,7 +717,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
     constexpr bool PACK = NETA <= 2;
-    const size_t wbytes = force_warp_bytes(C, nv.stride, PACK, RES);
+    const size_t wbytes = force_warp_bytes(C, nv.stride, PACK, RES, STORED);
     unsigned char* base = smem + wbytes * wib;
     WarpSmem w;
     w.nd = reinterpret_cast<float4*>(base);
@@ -709,9 +730,13 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     w.queue = reinterpret_cast<unsigned short*>(sW + NNP_MAXG);
     w.cmap = reinterpret_cast<short*>(w.queue + PAIR_QUEUE);
     w.nel = RES ? reinterpret_cast<unsigned char*>(w.cmap + nv.stride) : nullptr;
+    w.nh = STORED ? nullptr
+                  : reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(w.cmap + nv.stride) +
+                                             (RES ? ((C + 15) & ~15) : 0));
     w.rtab = reinterpret_cast<float4*>(w.queue);
     w.rw = reinterpret_cast<float*>(w.rtab + NNP_MAXRAD);
     w.ninv = nullptr;
+    w.nr = nullptr;
     w.nfe = nullptr;
 
     // virial sums of the warp's atoms (FP64, in shared memory: registers stay free
@@ -836,7 +861,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                         qsrc = rec + qpos;
                         qpos += (total + 7) & ~7;
                     } else {
-                        unsigned mask = live_mask<NARROW>(A, B, lane, M, al, w.nd, P.rc2);
+                        unsigned mask = live_mask<NARROW, 1>(A, B, lane, M, al, (jl < M) ? w.nh[jl] : 0.f, w.nd, w.nh);
                         if (RES && ce1 >= 0) {
                             const int kl = 32 * B + lane;
                             mask &= class_mask(ej, kl < M ? (int)w.nel[kl] : -1, ce1, ce2, lane);

@@ -15,7 +15,7 @@
 
 __host__ __device__ inline size_t tangent_warp_bytes(int C)
 {
-    // nd, npf, ndp, nfe (f_c, f_c', element), dv (du, r^ . du) as float4; ninv; queue; FP64 sums
+    // nd, npf, ndp, nfe (f_c, f_c', element, h), dv (du, r^ . du) as float4; ninv; queue; FP64 sums
     return (size_t)C * (16 * 5 + 4) + PAIR_QUEUE * 2 + NNP_MAXG * 8;
 }
 
@@ -76,7 +76,7 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
                 dx = pair_disp(pj.x, pi.x, ox);
                 dy = pair_disp(pj.y, pi.y, oy);
                 dz = pair_disp(pj.z, pi.z, oz);
-                r2 = dx * dx + dy * dy + dz * dz;
+                r2 = dist2_fma(dx, dy, dz);
                 ej = __float_as_int(pj.w);
                 keep = r2 < P.rc2;
             }
@@ -98,7 +98,7 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
                 ninv[at] = ir;
                 npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
                 ndp[at] = make_float4(dq[0], dq[1], dq[2], dq[3]);
-                nfe[at] = make_float4(fc, dfc, __int_as_float(ej), 0.f);
+                nfe[at] = make_float4(fc, dfc, __int_as_float(ej), live_h(r2, P.rc2));
                 ndv[at] = make_float4(dvx, dvy, dvz, (dx * dvx + dy * dvy + dz * dvz) * ir);
             }
             M += __popc(m);
@@ -139,7 +139,8 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
                 const float4 al = (jl < M) ? nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int ej = (RES && jl < M) ? __float_as_int(nfe[jl].z) : -1;
                 for (int B = A; B < nb; ++B) {
-                    unsigned mask = live_mask<NARROW>(A, B, lane, M, al, nd, P.rc2);
+                    unsigned mask = live_mask<NARROW, 4>(A, B, lane, M, al, (jl < M) ? nfe[jl].w : 0.f, nd,
+                                                         &nfe[0].w);
                     if (RES && ce1 >= 0) {
                         const int kl = 32 * B + lane;
                         mask &= class_mask(ej, kl < M ? __float_as_int(nfe[kl].z) : -1, ce1, ce2, lane);
