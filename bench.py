@@ -55,11 +55,10 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # DRAM bytes (read + write) per atom-evaluation of each kernel group, from the
 # ncu --set full capture on the 110,592-atom water box summarised in
 # profiles/k_force_k_sf_water_110k.md (a 2M-atom launch moves the same bytes per
-# atom: list rows, positions, pair-queue records and the per-slot g buffer all
-# scale with atoms).  Valid only for the kernel sources with this hash;
+# atom: list rows, positions and pair-queue records all scale with atoms).  Valid only for the kernel sources with this hash;
 # otherwise traffic is null.
-TRAFFIC = {"force": (470.480128e6 + 228.633088e6) / 110592, "descriptors": (84.052992e6 + 328.640768e6) / 110592}
-TRAFFIC_SRC_SHA = "2a290bec11ff"
+TRAFFIC = {"force": (470.050816e6 + 6.142464e6) / 110592, "descriptors": (84.092416e6 + 328.398336e6) / 110592}
+TRAFFIC_SRC_SHA = "4240f425f3a5"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
