@@ -228,14 +228,22 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
     float Lx, Ly, Lz;
     atom_box(nv, bx, i, Lx, Ly, Lz);
     int M = 0;
+    // list entries two rounds ahead, positions one round ahead
+    uint32_t e_n = (lane < cnt) ? row[lane] : 0u;
+    uint32_t e_nn = (lane + 32 < cnt) ? row[lane + 32] : 0u;
+    float4 p_n = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (lane < cnt) p_n = pos4[e_n & NB_INDEX_MASK];
     for (int base = 0; base < cnt; base += 32) {
         const int s = base + lane;
+        const uint32_t e = e_n;
+        const float4 pj = p_n;
+        e_n = e_nn;
+        if (s + 32 < cnt) p_n = pos4[e_nn & NB_INDEX_MASK];
+        e_nn = (s + 64 < cnt) ? row[s + 64] : 0u;
         bool keep = false;
         float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
         int ej = 0;
         if (s < cnt) {
-            const uint32_t e = row[s];
-            const float4 pj = pos4[e & NB_INDEX_MASK];
             float ox, oy, oz;
             nb_shift(e, Lx, Ly, Lz, ox, oy, oz);
             dx = pair_disp(pj.x, pi.x, ox);
