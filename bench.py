@@ -57,8 +57,8 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # profiles/k_force_k_sf_water_110k.md (a 2M-atom launch moves the same bytes per
 # atom: list rows, positions and pair-queue records all scale with atoms).  Valid only for the kernel sources with this hash;
 # otherwise traffic is null.
-TRAFFIC = {"force": (470.050816e6 + 6.142464e6) / 110592, "descriptors": (84.092416e6 + 328.398336e6) / 110592}
-TRAFFIC_SRC_SHA = "4240f425f3a5"
+TRAFFIC = {"force": (470.211072e6 + 5.535488e6) / 110592, "descriptors": (84.074752e6 + 328.41472e6) / 110592}
+TRAFFIC_SRC_SHA = "b47972487ecd"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
