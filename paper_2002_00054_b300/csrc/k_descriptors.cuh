@@ -272,10 +272,15 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
             }
             const float hh = live_h(r2, P.rc2);
             if (!FORCE) {
-                w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
+                // at most 2 eta: 1/r and r ride in the free half of the P record
+                if (NETA <= 2) {
+                    w.npf[at] = make_float4(pq[0], pq[1], ir, r);
+                } else {
+                    w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
+                    w.ninv[at] = ir;
+                    w.nr[at] = r;
+                }
                 w.nd[at] = make_float4(dx, dy, dz, hh);
-                w.ninv[at] = ir;
-                w.nr[at] = r;
                 w.nfe[at] = make_float2(fc, __int_as_float(ej));
             } else {
                 w.nd[at] = make_float4(dx, dy, dz, ir);
@@ -497,7 +502,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 const int el = act ? E.rad_elem[rr] : -2;
                 float sum = 0.f, comp = 0.f;
                 for (int m = hf; m < M; m += halves) {
-                    const float r = w.nr[m];
+                    const float r = (NETA <= 2) ? w.npf[m].w : w.nr[m];
                     const float2 fe = w.nfe[m];
                     if (el == -1 || el == __float_as_int(fe.y)) {
                         const float x = r - rs;
@@ -590,7 +595,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                             const float4 pa4 = w.npf[j], pb4 = w.npf[k];
                             const float2 PA[2] = {f2(pa4.x, pa4.y), f2(pa4.z, pa4.w)};
                             const float2 PB[2] = {f2(pb4.x, pb4.y), f2(pb4.z, pb4.w)};
-                            const float c = (a.x * b.x + a.y * b.y + a.z * b.z) * (w.ninv[j] * w.ninv[k]);
+                            const float c = (a.x * b.x + a.y * b.y + a.z * b.z) *
+                                            ((NETA <= 2) ? pa4.z * pb4.z : w.ninv[j] * w.ninv[k]);
                             float fcd = 1.f, rd2 = 0.f;
                             if (NARROW) {
                                 const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
