@@ -131,15 +131,23 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
         // angular (one pass per neighbour-element pair class)
         const int ncls = RES ? E.n_cls : 1;
         for (int cls = 0; NETA > 0 && cls < ncls; ++cls) {
-            constexpr int NQ = NETA > 0 ? NETA : 1;
+            constexpr int NQ = NETA > 0 ? NETA : 1, NP = (NQ + 1) / 2;
             constexpr int NA = NQ * 2 * (NNP_KMAX + 1);
-            float acc[NQ][2][NNP_KMAX + 1];
+            // accumulators of eta pairs (q = 2p, 2p + 1) as packed f32x2
+            float2 acc[NP][2][NNP_KMAX + 1];
 #pragma unroll
-            for (int q = 0; q < NQ; ++q)
+            for (int p = 0; p < NP; ++p)
 #pragma unroll
                 for (int l = 0; l < 2; ++l)
 #pragma unroll
-                    for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[q][l][kk] = 0.f;
+                    for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[p][l][kk] = f2(0.f, 0.f);
+            float2 KH[NP], KL[NP], ET[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+                KH[p] = f2(khi[2 * p], (2 * p + 1 < 4) ? khi[2 * p + 1] : 0.f);
+                KL[p] = f2(klo[2 * p], (2 * p + 1 < 4) ? klo[2 * p + 1] : 0.f);
+                ET[p] = f2(-2.0f * etav[2 * p], (2 * p + 1 < 4) ? -2.0f * etav[2 * p + 1] : 0.f);
+            }
             const int nb = (M + 31) >> 5;
             const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             for (int A = 0; A < nb; ++A) {
@@ -194,23 +202,55 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
                                 }
                             }
                         }
+                        if constexpr (NETA % 2 == 0) {
+                            // even eta count: both of a pair in one packed instruction
 #pragma unroll
-                        for (int q = 0; q < NETA; ++q) {
-                            float Pd = 1.f, dPd = 0.f;
-                            if (NARROW) {
-                                const float ed = gauss2(khi[q], klo[q], rd2);
-                                Pd = ed * fcd;
-                                dPd = ed * (dfcd - 2.0f * etav[q] * rd * fcd);
+                            for (int p = 0; p < NP; ++p) {
+                                const float2 PA = f2(pav[2 * p], pav[2 * p + 1]), PB = f2(pbv[2 * p], pbv[2 * p + 1]);
+                                const float2 QA = f2(qav[2 * p], qav[2 * p + 1]), QB = f2(qbv[2 * p], qbv[2 * p + 1]);
+                                float2 Pd = f2(1.f, 1.f), dPd = f2(0.f, 0.f);
+                                if (NARROW) {
+                                    const float2 x2 = f2(rd2, rd2);
+                                    const float2 arg = fma2(KH[p], x2, mul2(KL[p], x2));
+                                    const float2 ed = f2(exp2f(arg.x), exp2f(arg.y));
+                                    Pd = mul2(ed, f2(fcd, fcd));
+                                    const float rf = rd * fcd;
+                                    dPd = mul2(ed, fma2(ET[p], f2(rf, rf), f2(dfcd, dfcd)));
+                                }
+                                const float2 pab = mul2(PA, PB);
+                                const float2 R = mul2(pab, Pd);
+                                float2 dR = mul2(fma2(mul2(QA, PB), f2(va.w, va.w), mul2(mul2(PA, QB), f2(vb.w, vb.w))), Pd);
+                                if (NARROW) dR = fma2(mul2(pab, dPd), f2(drd, drd), dR);
+#pragma unroll
+                                for (int lb = 0; lb < 2; ++lb)
+#pragma unroll
+                                    for (int kk = 0; kk <= NNP_KMAX; ++kk)
+                                        if (kk <= (lb == 0 ? KP : KN))
+                                            acc[p][lb][kk] = fma2(f2(pw[lb][kk], pw[lb][kk]), dR,
+                                                                  fma2(f2(qd[lb][kk], qd[lb][kk]), R, acc[p][lb][kk]));
                             }
-                            const float R = pav[q] * pbv[q] * Pd;
-                            float dR = (qav[q] * pbv[q] * va.w + pav[q] * qbv[q] * vb.w) * Pd;
-                            if (NARROW) dR = fmaf(pav[q] * pbv[q] * dPd, drd, dR);
+                        } else {
 #pragma unroll
-                            for (int lb = 0; lb < 2; ++lb)
+                            for (int q = 0; q < NETA; ++q) {
+                                float Pd = 1.f, dPd = 0.f;
+                                if (NARROW) {
+                                    const float ed = gauss2(khi[q], klo[q], rd2);
+                                    Pd = ed * fcd;
+                                    dPd = ed * (dfcd - 2.0f * etav[q] * rd * fcd);
+                                }
+                                const float R = pav[q] * pbv[q] * Pd;
+                                float dR = (qav[q] * pbv[q] * va.w + pav[q] * qbv[q] * vb.w) * Pd;
+                                if (NARROW) dR = fmaf(pav[q] * pbv[q] * dPd, drd, dR);
 #pragma unroll
-                                for (int kk = 0; kk <= NNP_KMAX; ++kk)
-                                    if (kk <= (lb == 0 ? KP : KN))
-                                        acc[q][lb][kk] = fmaf(pw[lb][kk], dR, fmaf(qd[lb][kk], R, acc[q][lb][kk]));
+                                for (int lb = 0; lb < 2; ++lb)
+#pragma unroll
+                                    for (int kk = 0; kk <= NNP_KMAX; ++kk)
+                                        if (kk <= (lb == 0 ? KP : KN)) {
+                                            float2& a2 = acc[q >> 1][lb][kk];
+                                            float& av = (q & 1) ? a2.y : a2.x;
+                                            av = fmaf(pw[lb][kk], dR, fmaf(qd[lb][kk], R, av));
+                                        }
+                            }
                         }
                     }
                     __syncwarp();
@@ -222,8 +262,8 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
                     const int idx = c0 + t;
-                    v[t] = (idx < NA) ? acc[idx / (2 * (NNP_KMAX + 1))][(idx / (NNP_KMAX + 1)) % 2][idx % (NNP_KMAX + 1)]
-                                      : 0.f;
+                    const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
+                    v[t] = (idx < NA) ? ((q & 1) ? acc[q >> 1][l][kk].y : acc[q >> 1][l][kk].x) : 0.f;
                 }
                 const double tot = warp_reduce_scatter32(v, lane);
                 const int idx = c0 + lane;
