@@ -16,7 +16,7 @@ BF16 on the 1,048,576-atom FCC crystal with errors against the oracle on the
 4,000-atom FCC box (fcc_precision), and the oracle timed on the host cores
 (cpu_baseline).  --mode combined runs the 1,048,320-atom BF16 autograd NVE run.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (the reference arm of this build).
+workload (the reference arm: the paper ships no code to install).
 """
 from __future__ import annotations
 
