@@ -349,7 +349,7 @@ def combined_run(args, dev):
     a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a0.record()
     log = []
-    max_row, spilled = 0, 0
+    max_row, spilled, r_min = 0, 0, float("inf")
     for k in range(args.steps):
         v += 0.5 * dt * F * inv_m
         x += dt * v
@@ -357,6 +357,8 @@ def combined_run(args, dev):
         v += 0.5 * dt * F * inv_m
         st = nnp.stats()
         max_row, spilled = max(max_row, st["max_list_row"]), spilled + st["spilled_atoms"]
+        if st["min_distance"] > 0:
+            r_min = min(r_min, st["min_distance"])
         if (k + 1) % 100 == 0:
             log.append(etot(E))
     a1.record()
@@ -381,6 +383,7 @@ def combined_run(args, dev):
             "conserved_energy_drift_ev_per_atom_per_ns": drift, "energy_log_every_100_steps": log,
             "initial_force_rms_vs_fp32_ev_per_A": f_rms,
             "max_list_row": max_row, "spilled_atom_evaluations": spilled,
+            "min_pair_distance_A": r_min,
             "fp32_nnp_step": {"conserved_energy_drift_ev_per_atom_per_ns": float(fp32_drift),
                               "final_temperature_K": float(2 * lg[-1, 1] / (3 * n * workloads.KB_EV)),
                               "ms_per_step": b0.elapsed_time(b1) / args.steps,

@@ -232,6 +232,9 @@ typedef struct {
     long long rc_capacity;     /* neighbours inside r_c the main launches stage
                                   per atom; re-tuned after every call from the
                                   counts seen (results do not depend on it)      */
+    double min_distance;       /* closest pair distance within r_c (A) in any
+                                  evaluation of the last call that computed
+                                  descriptors; -1 if none                       */
 } nnp_stats;
 NNP_API int nnp_get_stats(nnp_handle* h, nnp_stats* out);
 

@@ -38,7 +38,7 @@ class Stats(ctypes.Structure):
                 ("triplets", ctypes.c_longlong), ("rebuilds", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("max_list_row", ctypes.c_longlong),
                 ("max_cutoff_row", ctypes.c_longlong), ("spilled_atoms", ctypes.c_longlong),
-                ("rc_capacity", ctypes.c_longlong)]
+                ("rc_capacity", ctypes.c_longlong), ("min_distance", ctypes.c_double)]
 
 
 # name -> (restype, argtypes); every symbol declared in include/nnp.h

@@ -40,7 +40,8 @@
 #define CNT_REBUILDS 7
 #define CNT_QTOP 8      // pair-queue pool entries claimed by the current evaluation
 #define CNT_LOGSLOT 9   // next energy-log entry of the running nnp_step call
-#define CNT_N 10
+#define CNT_MINR 10     // 0xffffffff - bits(r) of the closest pair within the cutoff (call-wide max)
+#define CNT_N 11
 
 #define LOG2E 1.4426950408889634f
 

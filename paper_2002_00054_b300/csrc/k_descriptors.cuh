@@ -461,6 +461,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     // 3 largest row, 4 largest cutoff row; triplets per lane, spills in lane 0
     unsigned long long cnt = 0, c_spill = 0;
     unsigned c_trip = 0;
+    float r_min = INFINITY;   // closest staged neighbour of this lane's atoms
     // this warp's chunk [qcur, qend) of the queue pool, in units of 8 entries
     // (main pass, when forces follow)
     unsigned qcur = 0, qend = 0;
@@ -487,6 +488,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             if (qoff && lane == 0) qoff[i] = QOFF_NONE;
             continue;
         }
+        for (int m = lane; m < M; m += 32) r_min = fminf(r_min, (NETA <= 2) ? w.npf[m].w : w.nr[m]);
         // radial: lane <-> descriptor (two neighbour halves when n_rad <= 16), loop over
         // neighbours with broadcast reads; Kahan-compensated sums (they feed
         // G~ = (G - mu)/s with |mu/s| up to ~20)
@@ -710,6 +712,11 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         atomicAdd(&counters[CNT_TRIPLETS], t);
         if (c_spill) atomicAdd(&counters[CNT_SPILL], c_spill);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r_min = fminf(r_min, __shfl_xor_sync(FULL, r_min, o));
+    // positive floats order like their bits: the largest complement is the closest pair
+    if (lane == 0 && r_min < INFINITY)
+        atomicMax(&counters[CNT_MINR], 0xffffffffull - (unsigned long long)__float_as_uint(r_min));
 }
 
 // ---------------------------------------------------------------- force pass

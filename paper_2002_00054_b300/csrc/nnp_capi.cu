@@ -938,6 +938,7 @@ static int begin_call(nnp_handle* h, cudaStream_t st)
     h->evals = 0;
     CK(h, cudaMemsetAsync(h->flags + FLAG_ERR, 0, sizeof(int), st));
     CK(h, cudaMemsetAsync(h->counters, 0, sizeof(unsigned long long) * CNT_PER_CALL, st));
+    CK(h, cudaMemsetAsync(h->counters + CNT_MINR, 0, sizeof(unsigned long long), st));
     return NNP_OK;
 }
 
@@ -1521,6 +1522,13 @@ int nnp_kernel_times(nnp_handle* h, int max_groups, double* total_ms, long long*
     return m;
 }
 
+static float __uint_as_float_host(unsigned u)
+{
+    float f;
+    memcpy(&f, &u, sizeof f);
+    return f;
+}
+
 int nnp_get_stats(nnp_handle* h, nnp_stats* out)
 {
     if (!h || !out) return NNP_EINVAL;
@@ -1539,6 +1547,7 @@ int nnp_get_stats(nnp_handle* h, nnp_stats* out)
     out->max_cutoff_row = (long long)c[CNT_MAXRC];
     out->spilled_atoms = (long long)c[CNT_SPILL];
     out->rc_capacity = h->cap_rc;
+    out->min_distance = c[CNT_MINR] ? (double)__uint_as_float_host((unsigned)(0xffffffffull - c[CNT_MINR])) : -1.0;
     return NNP_OK;
 }
 

@@ -214,4 +214,5 @@ class NNP:
     def stats(self):
         s = _capi.Stats()
         self._check(self._lib.nnp_get_stats(self.h, ctypes.byref(s)))
-        return {k: int(getattr(s, k)) for k, _ in _capi.Stats._fields_}
+        return {k: (float(getattr(s, k)) if t is ctypes.c_double else int(getattr(s, k)))
+                for k, t in _capi.Stats._fields_}

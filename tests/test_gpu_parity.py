@@ -154,6 +154,14 @@ def test_stats_counts(water_nnp):
     assert s["cutoff_entries"] == sum(len(x[0]) for x in nb)
     assert s["pairs"] == sum(len(x[0]) * (len(x[0]) - 1) // 2 for x in nb)
     assert 0 < s["triplets"] < s["pairs"]
+    # closest pair inside the cutoff (float distance of the same displacement)
+    r_min = min(np.sqrt((x[1] ** 2).sum(1)).min() for x in nb if len(x[0]))
+    assert abs(s["min_distance"] - r_min) <= 1e-6 * r_min
+    # a moved pair is seen by the next call
+    q = p.clone()
+    q[1] = q[0] + torch.tensor([0.31, 0.0, 0.0], device="cuda")
+    water_nnp.compute(q, t, f32(box))
+    assert abs(water_nnp.stats()["min_distance"] - 0.31) <= 1e-6
 
 
 # ------------------------------------------------------------- errors
