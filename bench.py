@@ -474,6 +474,21 @@ def ablation_run(args, dev):
         out[form] = {"value": n * args.steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / args.steps,
                      "kernels_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1] > 0}}
         h.close()
+    # descriptor pass: warp per atom (the kernels used everywhere) against one
+    # thread per atom (the flat level of the paper's parallelism study)
+    h = NNP(model, device=dev.index, max_neighbors=max_nb)
+    p = torch.from_numpy(pos_h).to(dev)
+    Gf = h.descriptors_flat(p, t, box)
+    Gw, _ = h.descriptors(p, t, box, dEdG=False)
+    h.profile(True)
+    calls = 3
+    for _ in range(calls):
+        h.descriptors_flat(p, t, box)
+    kt = h.kernel_times()
+    out["descriptor_parallelism"] = {
+        "warp_per_atom_ms": kt["descriptors"][0] / calls, "thread_per_atom_ms": kt["descriptors_flat"][0] / calls,
+        "max_rel_difference": float(((Gf - Gw).abs().max(0).values / Gw.abs().max(0).values.clamp_min(1e-30)).max())}
+    h.close()
     return out
 
 

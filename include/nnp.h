@@ -164,6 +164,16 @@ NNP_API int nnp_compute(nnp_handle* h, int n_atoms, const float* pos, const int*
 NNP_API int nnp_descriptors(nnp_handle* h, int n_atoms, const float* pos, const int* types, const double* box,
                     float* G, float* dEdG, void* stream);
 
+/* Raw descriptors G of one system computed with one thread per atom (each
+ * thread walks its own neighbours and neighbour pairs: the flat level of the
+ * paper's parallelism study, Sec. 4.3 / Fig. 6), for comparison with the
+ * warp-per-atom kernels of every other call; FP32 sums, much slower.  The
+ * neighbour list is built (or reused) as by nnp_descriptors.  Models with
+ * element-pair-resolved angular descriptors: NNP_EUNSUPPORTED.
+ *   G  device float [n_atoms][n_G]. */
+NNP_API int nnp_descriptors_flat(nnp_handle* h, int n_atoms, const float* pos, const int* types, const double* box,
+                                 float* G, void* stream);
+
 /* n_steps velocity-Verlet NVE steps (Sec. 4.2 energy conservation):
  *   v += dt/2 F/m;  x += dt v;  F = F(x);  v += dt/2 F/m
  * pos, vel: device float [n_atoms][3], updated in place (positions are not wrapped).

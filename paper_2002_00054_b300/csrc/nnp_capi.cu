@@ -22,6 +22,7 @@
 #include "k_mlp_tc.cuh"
 #include "k_neighbors.cuh"
 #include "k_train.cuh"
+#include "k_flat.cuh"
 
 namespace {
 
@@ -109,8 +110,8 @@ struct nnp_handle {
     std::vector<cudaEvent_t> ev_pool;
     struct Pending { int id; cudaEvent_t a, b; };
     std::vector<Pending> pending;
-    double prof_ms[8] = {0};
-    long long prof_n[8] = {0};
+    double prof_ms[16] = {0};   // per kernel group (at most 16 groups)
+    long long prof_n[16] = {0};
     long long launches = 0;   // kernels launched by the current / last call
 
     // batches of independent systems (training): layout of the cached list
@@ -623,9 +624,10 @@ struct DeviceGuard {
     }
 };
 
-enum { KG_NEIGH = 0, KG_SF, KG_MLP, KG_FORCE, KG_GATHER, KG_REDUCE, KG_INTEGRATE, KG_N };
+enum { KG_NEIGH = 0, KG_SF, KG_MLP, KG_FORCE, KG_GATHER, KG_REDUCE, KG_INTEGRATE, KG_FLAT, KG_N };
 static const char* kKgName[KG_N] = {"neighbor_maintenance", "descriptors", "network", "force", "gather",
-                                    "reductions", "integrate"};
+                                    "reductions", "integrate", "descriptors_flat"};
+static_assert(KG_N <= 16, "kernel-group timers hold 16 groups");
 
 static cudaEvent_t ev_get(nnp_handle* h)
 {
@@ -1286,6 +1288,35 @@ int nnp_descriptors(nnp_handle* h, int n, const float* pos, const int* types, co
     if (rc) return rc;
     return run_eval(h, n, pos, types, box, (cudaStream_t)stream, nullptr, nullptr, nullptr, nullptr, G, dEdG,
                     dEdG ? 2 : 1);
+}
+
+int nnp_descriptors_flat(nnp_handle* h, int n, const float* pos, const int* types, const double* box, float* G,
+                         void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    h->err.clear();
+    if (!G) return set_err(h, NNP_EINVAL, "G must not be NULL");
+    if (h->plan.resolved)
+        return set_err(h, NNP_EUNSUPPORTED, "the thread-per-atom descriptors do not resolve angular pair classes");
+    int rc = common_args(h, n, pos, types, box);
+    if (rc) return rc;
+    if (n == 0) return NNP_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    h->step_valid = false;
+    rc = begin_call(h, st);
+    if (rc) return rc;
+    // neighbour list (and the warp-per-atom pass, which this call does not return)
+    rc = run_eval(h, n, pos, types, box, st, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1);
+    if (rc) return rc;
+    Box bx;
+    for (int a = 0; a < 3; ++a) bx.L[a] = (float)box[a];
+    NbView nv{h->nbr, h->ncount, h->stride};
+    {
+        KScope ks(h, KG_FLAT, st);
+        k_sf_flat<<<blocks_for(n, 128), 128, 0, st>>>(n, h->pos4, bx, nv, h->d_plan, G, h->flags);
+    }
+    return read_status(h, st);
 }
 
 int nnp_step(nnp_handle* h, int n, float* pos, float* vel, const int* types, const double* box, double dt_fs,
