@@ -485,6 +485,27 @@ def ablation_run(args, dev):
     for _ in range(calls):
         h.descriptors_flat(p, t, box)
     kt = h.kernel_times()
+    # neighbour-list skin: rebuild frequency against list length (list capacity
+    # scaled with the neighbour sphere's volume)
+    rc = float(model["cutoff"])
+    out["skin"] = {}
+    for skin in (0.5, 1.0, 1.5, 2.0):
+        mn = int(np.ceil(max_nb * ((rc + skin) / (rc + 1.0)) ** 3 / 8.0) * 8)
+        hs = NNP(model, device=dev.index, max_neighbors=mn, skin=skin)
+        p = torch.from_numpy(pos_h).to(dev)
+        v = torch.from_numpy(vel_h).to(dev)
+        hs.step(p, v, t, box, DT_FS, args.warmup)
+        r0 = hs.stats()["rebuilds"]
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        hs.step(p, v, t, box, DT_FS, args.steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out["skin"]["%.1f" % skin] = {"value": n * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+                                      "rebuilds": hs.stats()["rebuilds"] - r0, "max_neighbors": mn}
+        hs.close()
     out["descriptor_parallelism"] = {
         "warp_per_atom_ms": kt["descriptors"][0] / calls, "thread_per_atom_ms": kt["descriptors_flat"][0] / calls,
         "max_rel_difference": float(((Gf - Gw).abs().max(0).values / Gw.abs().max(0).values.clamp_min(1e-30)).max())}
