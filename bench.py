@@ -250,21 +250,31 @@ def reference_arm(args, rank):
 def training_leg(dev, steps, warmup):
     """Force-matching training step on the ragged batch of 256 water-like
     configurations (66-510 atoms): energies and forces, loss, gradient with
-    respect to every network parameter (energy term + double backward)."""
+    respect to every network parameter (energy term + double backward).  With
+    more than one rank the step is data-parallel over configurations: each rank
+    takes an atom-balanced shard, normalises its loss terms by the whole batch
+    and the parameter gradient is summed with one all_reduce per step."""
     import torch
+    import torch.distributed as dist
     from paper_2002_00054_b300 import NNP
-    from paper_2002_00054_b300.autograd import EnergyForces, NNPEnergy, TrainingBatch, force_matching_loss
+    from paper_2002_00054_b300.autograd import EnergyForces, NNPEnergy, TrainingBatch
+    from paper_2002_00054_b300.data_parallel import allreduce_grad, shard_by_atoms, shard_loss
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    rank = dist.get_rank() if world > 1 else 0
     systems = workloads.train_batch()
-    starts = np.cumsum([0] + [len(p) for p, _, _ in systems]).astype(np.int32)
-    pos = np.concatenate([p for p, _, _ in systems]).astype(np.float32)
-    types = np.concatenate([t for _, t, _ in systems]).astype(np.int32)
-    boxes = np.stack([b for _, _, b in systems]).astype(np.float32).astype(np.float64)
+    n_all = np.array([len(p) for p, _, _ in systems])
+    lo, hi = shard_by_atoms(n_all, rank, world)
+    mine = systems[lo:hi]
+    starts = np.cumsum([0] + [len(p) for p, _, _ in mine]).astype(np.int32)
+    pos = np.concatenate([p for p, _, _ in mine]).astype(np.float32)
+    types = np.concatenate([t for _, t, _ in mine]).astype(np.int32)
+    boxes = np.stack([b for _, _, b in mine]).astype(np.float32).astype(np.float64)
     model = workloads.water_model()
     teacher = NNP(workloads.water_model(seed=workloads.SEED_TEACHER_MODEL), device=dev.index)
     p = torch.from_numpy(pos).to(dev)
     t = torch.from_numpy(types).to(dev)
     lab = teacher.compute_batch(p, t, starts, boxes)   # labels: teacher network + force noise
-    gen = torch.Generator(device=dev).manual_seed(workloads.SEED_TRAIN)
+    gen = torch.Generator(device=dev).manual_seed(workloads.SEED_TRAIN + rank)
     Fref = lab["F"].double() + 0.01 * torch.randn(lab["F"].shape, generator=gen, device=dev, dtype=torch.float64)
     Eref = lab["energy"]
     teacher.close()
@@ -282,8 +292,9 @@ def training_leg(dev, steps, warmup):
                 x = p.clone().requires_grad_(True)
                 E = NNPEnergy.apply(x, w, batch)
                 F = -torch.autograd.grad(E.sum(), x, create_graph=True)[0]
-            loss = force_matching_loss(E, F, Eref, Fref, n_atoms, 10.0)
+            loss = shard_loss(E, F, Eref, Fref, n_atoms, len(systems), int(n_all.sum()), 10.0)
             loss.backward()
+            allreduce_grad(w.grad)
             return loss
         for _ in range(warmup):
             step()
@@ -295,8 +306,16 @@ def training_leg(dev, steps, warmup):
         a1.record()
         torch.cuda.synchronize()
         ms = a0.elapsed_time(a1) / steps
-        out[form] = {"ms_per_step": ms, "configs": len(systems), "atoms": int(starts[-1]),
-                     "atom_gradients_per_s": starts[-1] / (ms * 1e-3), "loss": float(loss.item())}
+        loss_v = float(loss.item())
+        if world > 1:
+            tt = torch.tensor([ms, loss_v], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt[:1], op=dist.ReduceOp.MAX)
+            dist.all_reduce(tt[1:], op=dist.ReduceOp.SUM)
+            ms, loss_v = float(tt[0]), float(tt[1])
+        out[form] = {"ms_per_step": ms, "configs": len(systems), "atoms": int(n_all.sum()),
+                     "atom_gradients_per_s": int(n_all.sum()) / (ms * 1e-3), "loss": loss_v,
+                     "parallelism": ("data-parallel over configurations, gradient all_reduce, %d ranks" % world)
+                     if world > 1 else "single"}
     nnp.close()
     return out
 
