@@ -14,7 +14,8 @@ owned atoms' energies.
 decompose() is host bookkeeping (numpy); evaluate_decomposed() runs the domains
 one after another through a caller-supplied evaluation (on one GPU: NNP.compute),
 and exchange_halo() does the same selection with torch.distributed, one domain
-per rank, where each rank starts from its own atoms only.
+per rank, where each rank starts from its own atoms only; allreduce_energy()
+sums the ranks' owned energies (FP64).
 """
 from __future__ import annotations
 
@@ -122,3 +123,15 @@ def exchange_halo(pos_own, types_own, gid_own, box, cutoff, rank, world, skin=1.
     p, t = d.local(pos_all, types_all)
     gid = np.concatenate([gid_all[d.owned], gid_all[d.ghost]])
     return p, t, gid, len(d.owned), d.box
+
+
+def allreduce_energy(e_owned):
+    """Total energy of the box from the ranks' owned-atom energy sums: an FP64
+    all_reduce (sum) over the process group (the input on one rank)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(e_owned)], dtype=torch.float64)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t[0])
+

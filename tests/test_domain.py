@@ -57,6 +57,7 @@ def _rank(rank, world, port, out):
     r = oracle.compute(m, p, t, lbox)
     np.save(os.path.join(out, "r%d.npy" % rank),
             np.concatenate([gid[:n_own, None].astype(float), r["Ei"][:n_own, None], r["F"][:n_own]], axis=1))
+    np.save(os.path.join(out, "e%d.npy" % rank), np.array([domain.allreduce_energy(r["Ei"][:n_own].sum())]))
     dist.destroy_process_group()
 
 
@@ -74,6 +75,8 @@ def test_two_gloo_ranks_match_undivided(tmp_path):
     np.testing.assert_allclose(rows[:, 1], ref["Ei"][gid], rtol=0, atol=1e-10)
     np.testing.assert_allclose(rows[:, 2:], ref["F"][gid], rtol=0, atol=1e-9)
     assert abs(rows[:, 1].sum() - ref["energy"]) <= 1e-9 * abs(ref["energy"])
+    for r in range(2):   # every rank holds the total energy after the all_reduce
+        assert abs(np.load(os.path.join(tmp_path, "e%d.npy" % r))[0] - ref["energy"]) <= 1e-9 * abs(ref["energy"])
 
 
 @pytest.mark.gpu
