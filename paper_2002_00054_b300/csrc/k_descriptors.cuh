@@ -124,7 +124,7 @@ static_assert(NNP_MAXRAD * 20 <= PAIR_QUEUE * 2, "radial table must fit the queu
 
 __host__ __device__ inline size_t sf_warp_bytes(int C)
 {
-    return (size_t)C * (16 + 8 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2;
+    return (size_t)C * (16 + 8 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2 + 16;   // + closest-pair slot
 }
 // PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).  STORED
 // (queues from the descriptor pass) needs no h array.  The last 80 bytes hold
@@ -219,7 +219,7 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                                                const float4* __restrict__ pos4, const Plan& P, const ElemPlan& E,
                                                const float* khi, const float* klo, const float* etav, int C,
                                                const WarpSmem& w, const float* sW, int lane, int* flags, int& n_list,
-                                               unsigned& sig)
+                                               unsigned& sig, float& r2min)
 {
     const int cnt = nv.ncount[i];
     n_list = cnt;
@@ -259,6 +259,7 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
         if (FORCE && s < cnt) w.cmap[s] = (keep && at < C) ? (short)at : (short)-1;
         if (keep && at < C) {
             if (r2 < 1e-8f) atomicOr(&flags[FLAG_ERR], ERR_CLOSE);
+            if (!FORCE) r2min = fminf(r2min, r2);
             const float r = sqrtf(r2);
             const float ir = 1.0f / r;
             float fc, dfc;
@@ -461,7 +462,9 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     // 3 largest row, 4 largest cutoff row; triplets per lane, spills in lane 0
     unsigned long long cnt = 0, c_spill = 0;
     unsigned c_trip = 0;
-    float r_min = INFINITY;   // closest staged neighbour of this lane's atoms
+    // per warp: closest staged neighbour (r^2) so far (last 16 bytes of the warp's area)
+    float* s_r2min = reinterpret_cast<float*>(base + sf_warp_bytes(C) - 16);
+    if (lane == 0) *s_r2min = INFINITY;
     // this warp's chunk [qcur, qend) of the queue pool, in units of 8 entries
     // (main pass, when forces follow)
     unsigned qcur = 0, qend = 0;
@@ -482,13 +485,17 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         }
         int n_list;
         unsigned sig;
+        float r2_atom = INFINITY;
         const int M = stage_neighbors<NETA, false>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, nullptr, lane,
-                                                   flags, n_list, sig);
+                                                   flags, n_list, sig, r2_atom);
+        // closest staged neighbour: kept per warp in shared memory, not in a register
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) r2_atom = fminf(r2_atom, __shfl_xor_sync(FULL, r2_atom, o));
+        if (lane == 0) *s_r2min = fminf(*s_r2min, r2_atom);
         if (over_capacity(M, C, pass, i, spill, true, lane, flags, c_spill)) {
             if (qoff && lane == 0) qoff[i] = QOFF_NONE;
             continue;
         }
-        for (int m = lane; m < M; m += 32) r_min = fminf(r_min, (NETA <= 2) ? w.npf[m].w : w.nr[m]);
         // radial: lane <-> descriptor (two neighbour halves when n_rad <= 16), loop over
         // neighbours with broadcast reads; Kahan-compensated sums (they feed
         // G~ = (G - mu)/s with |mu/s| up to ~20)
@@ -712,11 +719,9 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         atomicAdd(&counters[CNT_TRIPLETS], t);
         if (c_spill) atomicAdd(&counters[CNT_SPILL], c_spill);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r_min = fminf(r_min, __shfl_xor_sync(FULL, r_min, o));
     // positive floats order like their bits: the largest complement is the closest pair
-    if (lane == 0 && r_min < INFINITY)
-        atomicMax(&counters[CNT_MINR], 0xffffffffull - (unsigned long long)__float_as_uint(r_min));
+    if (lane == 0 && *s_r2min < INFINITY)
+        atomicMax(&counters[CNT_MINR], 0xffffffffull - (unsigned long long)__float_as_uint(sqrtf(*s_r2min)));
 }
 
 // ---------------------------------------------------------------- force pass
@@ -788,8 +793,9 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         }
         int n_list;
         unsigned sig;
+        float r2_unused = 0.f;
         const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
-                                                  n_list, sig);
+                                                  n_list, sig, r2_unused);
         if (over_capacity(M, C, pass, i, spill, false, lane, flags, c_spill)) continue;
         const int nb = (M + 31) >> 5;
         // largest 1/r of the staged neighbours (for the range bound below)
