@@ -57,8 +57,8 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # profiles/k_force_k_sf_water_110k.md (a 2M-atom launch moves the same bytes per
 # atom: list rows, positions and pair-queue records all scale with atoms).  Valid only for the kernel sources with this hash;
 # otherwise traffic is null.
-TRAFFIC = {"force": (470.211072e6 + 5.535488e6) / 110592, "descriptors": (84.074752e6 + 328.41472e6) / 110592}
-TRAFFIC_SRC_SHA = "b47972487ecd"
+TRAFFIC = {"force": (470.266112e6 + 5.384448e6) / 110592, "descriptors": (84.519936e6 + 329.367296e6) / 110592}
+TRAFFIC_SRC_SHA = "344cb4eccf1e"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
