@@ -1074,24 +1074,32 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         long long qx = 0, qy = 0, qz = 0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) v[q] = 0.f;
+        // the virial only when the caller asked for it (vir_part != nullptr)
         for (int m = lane; m < M; m += 32) {
-            const float4 d = w.nd[m];
-            const float gx = fx_get(w, 3 * m), gy = fx_get(w, 3 * m + 1), gz = fx_get(w, 3 * m + 2);
             if (Fq) {
                 qx += fx_get64(w, 3 * m);
                 qy += fx_get64(w, 3 * m + 1);
                 qz += fx_get64(w, 3 * m + 2);
-            } else {
-                fx += gx; fy += gy; fz += gz;
             }
-            v[0] -= d.x * gx; v[1] -= d.x * gy; v[2] -= d.x * gz;
-            v[3] -= d.y * gx; v[4] -= d.y * gy; v[5] -= d.y * gz;
-            v[6] -= d.z * gx; v[7] -= d.z * gy; v[8] -= d.z * gz;
+            if (!Fq || vir_part) {
+                const float gx = fx_get(w, 3 * m), gy = fx_get(w, 3 * m + 1), gz = fx_get(w, 3 * m + 2);
+                if (!Fq) {
+                    fx += gx; fy += gy; fz += gz;
+                }
+                if (vir_part) {
+                    const float4 d = w.nd[m];
+                    v[0] -= d.x * gx; v[1] -= d.x * gy; v[2] -= d.x * gz;
+                    v[3] -= d.y * gx; v[4] -= d.y * gy; v[5] -= d.y * gz;
+                    v[6] -= d.z * gx; v[7] -= d.z * gy; v[8] -= d.z * gz;
+                }
+            }
         }
+        if (vir_part) {
 #pragma unroll
-        for (int q = 0; q < 9; ++q) {
-            const float t = warp_sum(v[q]);
-            if (lane == q) vir[q] += (double)t;
+            for (int q = 0; q < 9; ++q) {
+                const float t = warp_sum(v[q]);
+                if (lane == q) vir[q] += (double)t;
+            }
         }
         if (Fq) {
 #pragma unroll
@@ -1121,7 +1129,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     }
     if (__any_sync(FULL, fx_bad) && lane == 0) atomicOr(&flags[FLAG_ERR], ERR_RANGE);
     __syncwarp();
-    if (lane < 9) vir_part[(size_t)(blockIdx.x * wpb + wib) * 9 + lane] = vir[lane];
+    if (vir_part && lane < 9) vir_part[(size_t)(blockIdx.x * wpb + wib) * 9 + lane] = vir[lane];
 }
 
 // F_m = Fown_m - sum_s g[nbr(m, s), rev(m, s)]   (no atomics, fixed order)

@@ -906,11 +906,13 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         // main pass over the stored queues (atoms without one join the wide pass)
         const bool stored = P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW && !P.resolved && h->qpool;
         (stored ? kfs : kf)<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
-            n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, h->vpart, h->flags, h->spill, 0,
+            n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, vir_out ? h->vpart : nullptr,
+            h->flags, h->spill, 0,
             stored ? h->qpool : nullptr, stored ? h->qoff : nullptr, Fsc, Fq);
         kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride,
                                                                        h->dEdG, h->gbuf, h->Fown,
-                                                                       h->vpart + (size_t)nvp_main * 9, h->flags,
+                                                                       vir_out ? h->vpart + (size_t)nvp_main * 9 : nullptr,
+                                                                       h->flags,
                                                                        h->spill, 1, nullptr, nullptr, Fsc, Fq);
     }
     if (h->fmode == FM_GATHER) {
@@ -926,7 +928,8 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     } else {
         KScope ks(h, KG_REDUCE, st, 2);
         k_sum_partial<<<gred, T, 0, st>>>(n, h->Ei, h->epart, h->flags);
-        k_finalize<<<1, 256, 0, st>>>(gred, h->epart, energy ? energy : h->d_energy, nvp, h->vpart, vir_out);
+        k_finalize<<<1, 256, 0, st>>>(gred, h->epart, energy ? energy : h->d_energy, vir_out ? nvp : 0, h->vpart,
+                                      vir_out);
     }
     if (Ei_out) CK(h, cudaMemcpyAsync(Ei_out, h->Ei, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     return NNP_OK;
