@@ -72,6 +72,7 @@ __device__ __forceinline__ int atom_at(int pass, int it, const int* spill)
 // entries of the pool with one atomic; the pool counter also records the
 // demand when the pool is too small.
 #define QOFF_NONE 0xffffffffu
+#define QOFF_SPILLED 0xfffffffeu   // not stored: already queued for the wide-capacity pass
 #define QCHUNK 65536ull
 #define QHDR 4
 __host__ __device__ inline int queue_entries_start(int nb)
@@ -107,6 +108,7 @@ struct WarpSmem {
     float* ninv;    // 1 / r (descriptor pass)
     float* nr;      // r (descriptor pass)
     float* nh;      // h = r^2 / 2 - rc^2 / 4 (force passes that rebuild the live masks)
+    int* jidx;      // atom index of each staged neighbour (force pass over stored staging)
     float4* npf;    // P_q; force pass with <= 2 eta: (P_0, P_1, dP_0/dr, dP_1/dr)
     float4* ndp;    // dP_q / dr (force pass with > 2 eta)
     float2* nfe;    // (f_c, element) (descriptor pass)
@@ -126,13 +128,14 @@ __host__ __device__ inline size_t sf_warp_bytes(int C)
 {
     return (size_t)C * (16 + 8 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2 + 16;   // + closest-pair slot
 }
-// PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).  STORED
-// (queues from the descriptor pass) needs no h array.  The last 80 bytes hold
-// the warp's nine FP64 virial sums.
+// PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).  A 4C-byte
+// array holds h (passes that rebuild the live masks) or the neighbours' atom
+// indices (the pass over stored staging).  The last 80 bytes hold the warp's
+// nine FP64 virial sums.
 __host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool res, bool stored = false)
 {
     return (size_t)C * (16 + (pack ? 16 : 32) + 24) + PAIR_QUEUE * 2 + NNP_MAXG * 4 + (size_t)S * 2 +
-           (res ? (size_t)((C + 15) & ~15) : 0) + (stored ? 0 : (size_t)C * 4) + 80;
+           (res ? (size_t)((C + 15) & ~15) : 0) + (size_t)C * 4 + 80;
 }
 
 // Fixed-point accumulation of the force pass.  A contribution v, |v| < FX_LIMIT
@@ -212,6 +215,28 @@ __device__ __forceinline__ bool live_pair(const float4 a, float ha, const float4
     return fmaf(a.z, b.z, fmaf(a.y, b.y, fmaf(a.x, b.x, -hb))) > ha;
 }
 
+// Radial part of g_ij for staged neighbour `at`: the sum over the radial
+// descriptors that take the neighbour's element of dE/dG * dG/dr * d / r, into
+// the fixed-point accumulators.
+__device__ __forceinline__ void radial_g(const WarpSmem& w, const Plan& P, const ElemPlan& E, int at, float r, float ir,
+                                         float fc, float dfc, int ej, float dx, float dy, float dz, int* flags)
+{
+    float gr = 0.f;
+    auto rad = [&](int rr) {
+        const float4 t = w.rtab[rr];
+        const float x = r - t.z;
+        const float ex = gauss2(t.x, t.y, x * x);
+        gr += w.rw[rr] * ex * fmaf(t.w * x, fc, dfc);
+    };
+    for (int rr = 0; rr < E.rad_nall; ++rr) rad(rr);
+    for (int rr = E.rad_beg[ej], re = E.rad_end[ej]; rr < re; ++rr) rad(rr);
+    const float gs = gr * ir;
+    if (!(fabsf(gs) * P.rc < FX_LIMIT)) atomicOr(&flags[FLAG_ERR], ERR_RANGE);
+    fx_set(w, 3 * at + 0, gs * dx);
+    fx_set(w, 3 * at + 1, gs * dy);
+    fx_set(w, 3 * at + 2, gs * dz);
+}
+
 // Stages the neighbours of atom i within the cutoff, compacted in list order.
 // Returns M.  FORCE: nd.w = 1/r, dP/dr, the radial part of g (into sg), slot map.
 template <int NETA, bool FORCE>
@@ -219,7 +244,8 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                                                const float4* __restrict__ pos4, const Plan& P, const ElemPlan& E,
                                                const float* khi, const float* klo, const float* etav, int C,
                                                const WarpSmem& w, const float* sW, int lane, int* flags, int& n_list,
-                                               unsigned& sig, float& r2min)
+                                               unsigned& sig, float& r2min, float4* __restrict__ stg = nullptr,
+                                               size_t stg_plane = 0)
 {
     const int cnt = nv.ncount[i];
     n_list = cnt;
@@ -293,22 +319,16 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                     w.ndp[at] = make_float4(dq[0], dq[1], dq[2], dq[3]);
                 }
                 if (w.nel) w.nel[at] = (unsigned char)ej;
-                // radial part of g_ij: sum over the radial descriptors that take the
-                // neighbour's element of dE/dG * dG/dr * d / r
-                float gr = 0.f;
-                auto rad = [&](int rr) {
-                    const float4 t = w.rtab[rr];
-                    const float x = r - t.z;
-                    const float ex = gauss2(t.x, t.y, x * x);
-                    gr += w.rw[rr] * ex * fmaf(t.w * x, fc, dfc);
-                };
-                for (int rr = 0; rr < E.rad_nall; ++rr) rad(rr);
-                for (int rr = E.rad_beg[ej], re = E.rad_end[ej]; rr < re; ++rr) rad(rr);
-                const float gs = gr * ir;
-                if (!(fabsf(gs) * P.rc < FX_LIMIT)) atomicOr(&flags[FLAG_ERR], ERR_RANGE);
-                fx_set(w, 3 * at + 0, gs * dx);
-                fx_set(w, 3 * at + 1, gs * dy);
-                fx_set(w, 3 * at + 2, gs * dz);
+                radial_g(w, P, E, at, r, ir, fc, dfc, ej, dx, dy, dz, flags);
+            }
+            if (!FORCE && stg) {
+                // staged record for the force pass, one plane each: (d, 1/r),
+                // (P_0, P_1, dP_0/dr, dP_1/dr), (r, f_c, f_c', atom index | element << 24)
+                const size_t idx = (size_t)i * C + at;
+                stg[idx] = make_float4(dx, dy, dz, ir);
+                stg[stg_plane + idx] = make_float4(pq[0], pq[1], dq[0], dq[1]);
+                stg[2 * stg_plane + idx] =
+                    make_float4(r, fc, dfc, __int_as_float((int)((e & NB_INDEX_MASK) | ((uint32_t)ej << 24))));
             }
         }
         M += __popc(m);
@@ -434,7 +454,8 @@ __global__ void __launch_bounds__(128, 6)
 k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g,
      int C, float* __restrict__ Gs, float* __restrict__ Graw, int* __restrict__ flags,
      unsigned long long* __restrict__ counters, int* __restrict__ spill, int pass,
-     unsigned short* __restrict__ qpool, unsigned int* __restrict__ qoff, unsigned long long qcap)
+     unsigned short* __restrict__ qpool, unsigned int* __restrict__ qoff, unsigned long long qcap,
+     float4* __restrict__ stg, size_t stg_plane)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -450,6 +471,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     w.nfe = reinterpret_cast<float2*>(w.nr + C);
     w.queue = reinterpret_cast<unsigned short*>(w.nfe + C);
     w.nh = nullptr;
+    w.jidx = nullptr;
     w.ndp = nullptr;
     w.sgh = nullptr;
     w.sgl = nullptr;
@@ -487,13 +509,13 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         unsigned sig;
         float r2_atom = INFINITY;
         const int M = stage_neighbors<NETA, false>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, nullptr, lane,
-                                                   flags, n_list, sig, r2_atom);
+                                                   flags, n_list, sig, r2_atom, pass == 0 ? stg : nullptr, stg_plane);
         // closest staged neighbour: kept per warp in shared memory, not in a register
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r2_atom = fminf(r2_atom, __shfl_xor_sync(FULL, r2_atom, o));
         if (lane == 0) *s_r2min = fminf(*s_r2min, r2_atom);
         if (over_capacity(M, C, pass, i, spill, true, lane, flags, c_spill)) {
-            if (qoff && lane == 0) qoff[i] = QOFF_NONE;
+            if (qoff && lane == 0) qoff[i] = QOFF_SPILLED;
             continue;
         }
         // radial: lane <-> descriptor (two neighbour halves when n_rad <= 16), loop over
@@ -556,7 +578,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                     unsigned long long old = 0;
                     if (lane == 0) old = atomicAdd(&counters[CNT_QTOP], sz);
                     old = __shfl_sync(FULL, old, 0);
-                    if (old + sz <= qcap && old + sz < (8ull << 32)) {
+                    if (old + sz <= qcap && ((old + sz) >> 3) < 0xfffffff0ull) {   // offsets stay below the markers
                         qcur = (unsigned)(old >> 3);
                         qend = (unsigned)((old + sz) >> 3);
                     } else {
@@ -736,7 +758,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
         double* __restrict__ vir_part, int* __restrict__ flags, int* __restrict__ spill, int pass,
         const unsigned short* __restrict__ qpool, const unsigned int* __restrict__ qoff,
-        float* __restrict__ Fscat, unsigned long long* __restrict__ Fq)
+        float* __restrict__ Fscat, unsigned long long* __restrict__ Fq, const float4* __restrict__ stg,
+        size_t stg_plane)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -756,9 +779,14 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     w.queue = reinterpret_cast<unsigned short*>(sW + NNP_MAXG);
     w.cmap = reinterpret_cast<short*>(w.queue + PAIR_QUEUE);
     w.nel = RES ? reinterpret_cast<unsigned char*>(w.cmap + nv.stride) : nullptr;
-    w.nh = STORED ? nullptr
-                  : reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(w.cmap + nv.stride) +
-                                             (RES ? ((C + 15) & ~15) : 0));
+    {
+        unsigned char* harea = reinterpret_cast<unsigned char*>(w.cmap + nv.stride) + (RES ? ((C + 15) & ~15) : 0);
+        w.nh = STORED ? nullptr : reinterpret_cast<float*>(harea);
+        w.jidx = STORED ? reinterpret_cast<int*>(harea) : nullptr;
+    }
+    // the main pass over stored queues reads the descriptor pass's staged
+    // neighbours instead of staging them again (stg; at most 2 eta)
+    const bool staged = STORED && PACK && stg != nullptr;
     w.rtab = reinterpret_cast<float4*>(w.queue);
     w.rw = reinterpret_cast<float*>(w.rtab + NNP_MAXRAD);
     w.ninv = nullptr;
@@ -791,12 +819,36 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             khi[q] = (q < E.n_eta) ? E.ang_khi[q] : 0.f;
             klo[q] = (q < E.n_eta) ? E.ang_klo[q] : 0.f;
         }
-        int n_list;
-        unsigned sig;
-        float r2_unused = 0.f;
-        const int M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
-                                                  n_list, sig, r2_unused);
-        if (over_capacity(M, C, pass, i, spill, false, lane, flags, c_spill)) continue;
+        int n_list = 0;
+        unsigned sig = 0u;
+        int M;
+        const unsigned short* rec = nullptr;
+        if (staged) {
+            // the descriptor pass's staging of this atom; its queue record gives M
+            const unsigned o = (NETA > 0) ? qoff[i] : QOFF_NONE;
+            if (o == QOFF_SPILLED) continue;   // the descriptor pass queued it already
+            if (o == QOFF_NONE) {               // no record (pool full): the wide pass takes it
+                if (lane == 0) spill[1 + atomicAdd(spill, 1)] = i;
+                continue;
+            }
+            rec = qpool + (size_t)o * 8;
+            M = rec[0];
+            const size_t base = (size_t)i * C;
+            for (int m = lane; m < M; m += 32) {
+                const float4 a = stg[base + m], pq = stg[stg_plane + base + m], ax = stg[2 * stg_plane + base + m];
+                w.nd[m] = a;
+                w.npf[m] = pq;
+                const int jj = __float_as_int(ax.w);
+                w.jidx[m] = jj & (int)NB_INDEX_MASK;
+                radial_g(w, P, E, m, ax.x, a.w, ax.y, ax.z, (int)((unsigned)jj >> 24), a.x, a.y, a.z, flags);
+            }
+            __syncwarp();
+        } else {
+            float r2_unused = 0.f;
+            M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
+                                            n_list, sig, r2_unused);
+            if (over_capacity(M, C, pass, i, spill, false, lane, flags, c_spill)) continue;
+        }
         const int nb = (M + 31) >> 5;
         // largest 1/r of the staged neighbours (for the range bound below)
         float iam = 0.f;
@@ -810,10 +862,9 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         for (int o = 16; o > 0; o >>= 1) iam = fmaxf(iam, __shfl_xor_sync(FULL, iam, o));
         nonfin = __any_sync(FULL, nonfin);
         // the descriptor pass's queue record, used when this staging reproduces it
-        const unsigned short* rec = nullptr;
-        if (STORED && NETA > 0) {
+        if (STORED && NETA > 0 && !staged) {
             const unsigned o = qoff[i];
-            if (o != QOFF_NONE) {
+            if (o != QOFF_NONE && o != QOFF_SPILLED) {
                 const unsigned short* r = qpool + (size_t)o * 8;
                 if (r[0] == (unsigned short)M && r[1] == (unsigned short)(sig & 0xffffu) &&
                     r[2] == (unsigned short)(sig >> 16))
@@ -1040,7 +1091,14 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         // floats (order-dependent); otherwise g is written per list slot for the
         // gather.  Then the own force and the virial.
         const int cnt = n_list;
-        if (Fq) {
+        if (Fq && staged) {
+            for (int m = lane; m < M; m += 32) {
+                unsigned long long* fj = Fq + 3 * (size_t)w.jidx[m];
+                atomicAdd(fj + 0, (unsigned long long)(-fx_get64(w, 3 * m)));
+                atomicAdd(fj + 1, (unsigned long long)(-fx_get64(w, 3 * m + 1)));
+                atomicAdd(fj + 2, (unsigned long long)(-fx_get64(w, 3 * m + 2)));
+            }
+        } else if (Fq) {
             const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
             for (int s = lane; s < cnt; s += 32) {
                 const int c = w.cmap[s];

@@ -160,6 +160,11 @@ struct nnp_handle {
     // atomics (order-dependent)
     int fmode = 0;
     unsigned long long* Fq = nullptr;   // [cap_n][3], units 2^-27 eV/A
+    // staged neighbours written by the descriptor pass for the force pass: three
+    // planes of cap_stg float4 (atom i, staged index m at i * C + m)
+    bool use_stg = true;
+    float4* stg = nullptr;
+    size_t cap_stg = 0;
     // nnp_step: the per-step launch sequence captured as a CUDA graph and replayed
     bool step_graph = true;
     cudaStream_t gstream = nullptr;   // capture and replay stream (non-blocking, owned)
@@ -384,10 +389,10 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
 
 // --------------------------------------------------------------- dispatch
 typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, float*, float*, int*, unsigned long long*,
-                         int*, int, unsigned short*, unsigned int*, unsigned long long);
+                         int*, int, unsigned short*, unsigned int*, unsigned long long, float4*, size_t);
 typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
                             double*, int*, int*, int, const unsigned short*, const unsigned int*, float*,
-                            unsigned long long*);
+                            unsigned long long*, const float4*, size_t);
 
 typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*, int*, int);
 
@@ -850,6 +855,8 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     ForceKernel kfs;
     pick_kernels(P, ksf, kf, kt_unused, kfs);
     h->evals++;
+    bool staged = false;
+    size_t stg_plane = 0;
     {
         // the force pass follows: store the pair queues for it (narrow kind only:
         // there the live masks cost a distance test per pair; wide queues follow
@@ -860,15 +867,36 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
             if (rc) return rc;
             CK(h, cudaMemsetAsync(h->counters + CNT_QTOP, 0, sizeof(unsigned long long), st));
         }
+        // staged neighbours for the force pass: at most 2 eta, integer force atomics;
+        // without the memory the force pass stages again
+        staged = store && P.n_eta_max <= 2 && h->fmode == FM_FIXED && h->use_stg;
+        if (staged) {
+            const size_t plane = (size_t)n * h->cap_rc;
+            if (plane > h->cap_stg) {
+                if (h->stg) cudaFree(h->stg);
+                h->stg = nullptr;
+                h->cap_stg = 0;
+                if (cudaMalloc((void**)&h->stg, 3 * plane * sizeof(float4)) == cudaSuccess) {
+                    h->cap_stg = plane;
+                } else {
+                    cudaGetLastError();
+                    h->stg = nullptr;
+                    h->use_stg = false;   // do not retry on every call
+                }
+            }
+            staged = h->stg != nullptr;
+        }
+        stg_plane = (size_t)n * h->cap_rc;
         KScope ks(h, KG_SF, st, 2);
         CK(h, cudaMemsetAsync(h->spill, 0, sizeof(int), st));
         const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
         ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->G, G_out, h->flags,
                                                      h->counters, h->spill, 0, store ? h->qpool : nullptr,
-                                                     store ? h->qoff : nullptr, (unsigned long long)h->cap_qpool);
+                                                     store ? h->qoff : nullptr, (unsigned long long)h->cap_qpool,
+                                                     staged ? h->stg : nullptr, stg_plane);
         ksf<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride, h->G, G_out,
                                                                  h->flags, h->counters, h->spill, 1, nullptr, nullptr,
-                                                                 0ull);
+                                                                 0ull, nullptr, 0);
     }
     if (stop_after == 1 && !dEdG_out) return read_status(h, st);
     if (h->precision == NNP_BF16) {
@@ -908,12 +936,13 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         (stored ? kfs : kf)<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
             n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, vir_out ? h->vpart : nullptr,
             h->flags, h->spill, 0,
-            stored ? h->qpool : nullptr, stored ? h->qoff : nullptr, Fsc, Fq);
+            stored ? h->qpool : nullptr, stored ? h->qoff : nullptr, Fsc, Fq, (stored && staged) ? h->stg : nullptr,
+            stg_plane);
         kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride,
                                                                        h->dEdG, h->gbuf, h->Fown,
                                                                        vir_out ? h->vpart + (size_t)nvp_main * 9 : nullptr,
                                                                        h->flags,
-                                                                       h->spill, 1, nullptr, nullptr, Fsc, Fq);
+                                                                       h->spill, 1, nullptr, nullptr, Fsc, Fq, nullptr, 0);
     }
     if (h->fmode == FM_GATHER) {
         KScope ks(h, KG_GATHER, st);
@@ -1088,6 +1117,10 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
         // NNP_STEP_GRAPH=0: nnp_step launches every kernel of every step itself
         const char* genv = getenv("NNP_STEP_GRAPH");
         h->step_graph = !(genv && genv[0] == '0');
+        // NNP_STAGE_REUSE=0: the force pass stages the neighbours again instead of
+        // reading the descriptor pass's staged records
+        const char* senv = getenv("NNP_STAGE_REUSE");
+        h->use_stg = !(senv && senv[0] == '0');
     }
     DeviceGuard g(device);
     auto fail = [&](int code) {
@@ -1216,7 +1249,7 @@ int nnp_destroy(nnp_handle* h)
     for (void* p : dev)
         if (p) cudaFree(p);
     for (void* p2 : {(void*)h->sys_of, (void*)h->sys_start_d, (void*)h->T, (void*)h->gpart, (void*)h->spill,
-                     (void*)h->qpool, (void*)h->qoff, (void*)h->seg, (void*)h->Fq})
+                     (void*)h->qpool, (void*)h->qoff, (void*)h->seg, (void*)h->Fq, (void*)h->stg})
         if (p2) cudaFree(p2);
     if (h->pos_cache) cudaFree(h->pos_cache);
     if (h->types_cache) cudaFree(h->types_cache);
@@ -1747,16 +1780,16 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     pick_kernels(P, ksf, kf);
     const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
     ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, G, nullptr, flags, counters,
-                                                 spill, 0, nullptr, nullptr, 0ull);
+                                                 spill, 0, nullptr, nullptr, 0ull, nullptr, 0);
     ksf<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, G, nullptr, flags, counters,
-                                                             spill, 1, nullptr, nullptr, 0ull);
+                                                             spill, 1, nullptr, nullptr, 0ull, nullptr, 0);
     const int gmlp = std::min(blocks_for(n, 128), h->grid_mlp);
     h->kmlp<<<gmlp, 128, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
     kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, vpart,
-                                                     flags, spill, 0, nullptr, nullptr, nullptr, nullptr);
+                                                     flags, spill, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
     kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, dEdG, gbuf, Fown,
                                                                    vpart + (size_t)nvp_main * 9, flags, spill, 1, nullptr, nullptr, nullptr,
-                                                                   nullptr);
+                                                                   nullptr, nullptr, 0);
     k_gather<<<rows_grid, 256, 0, st>>>(n, nv, rev, gbuf, Fown, forces ? forces : Fs, flags);
     k_sum_partial<<<gred, T, 0, st>>>(n, Ei, epart, flags);
     k_finalize<<<1, 256, 0, st>>>(gred, epart, energy, nvp, vpart, nullptr);

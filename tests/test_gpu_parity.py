@@ -261,3 +261,32 @@ def test_thread_per_atom_descriptors(name):
     assert (np.abs(Gf - gref) / scale).max() < 1e-5
     assert (np.abs(Gf - Gw) / scale).max() < 1e-5
 
+
+@pytest.mark.parametrize("spill", [False, True])
+def test_staged_reuse_is_bitwise(spill, monkeypatch):
+    """The force pass reads the neighbours the descriptor pass staged (same
+    arithmetic, integer force sums): bitwise the forces of staging them again
+    (NNP_STAGE_REUSE=0).  With `spill` both handles first evaluate a system at
+    0.75 of liquid density, which lowers the shared-memory capacity below the
+    counts of some atoms of liquid water: those take the wide-capacity pass."""
+    from paper_2002_00054_b300 import NNP
+    m = workloads.water_model()
+    pos, types, box = workloads.water_random(seed=78)
+    pos, box = f32(pos), f32(box)
+    p, t = to_dev(pos, types)
+    a = NNP(m)
+    monkeypatch.setenv("NNP_STAGE_REUSE", "0")
+    b = NNP(m)
+    monkeypatch.delenv("NNP_STAGE_REUSE")
+    if spill:
+        lp, lt, lb = workloads.water_random(box=workloads.WATER_CELL / 0.75 ** (1 / 3), seed=77)
+        lp, lt = to_dev(f32(lp), lt)
+        for h in (a, b):
+            h.compute(lp, lt, f32(lb))
+    oa, ob = a.compute(p, t, box), b.compute(p, t, box)
+    assert (a.stats()["spilled_atoms"] > 0) == spill
+    assert b.stats()["spilled_atoms"] == a.stats()["spilled_atoms"]
+    assert torch.equal(oa["F"], ob["F"]) and torch.equal(oa["Ei"], ob["Ei"])
+    assert torch.equal(oa["virial"], ob["virial"])
+    check(oa, oracle.compute(m, pos, types, box), what="water, staged reuse")
+
