@@ -55,10 +55,10 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # DRAM bytes (read + write) per atom-evaluation of each kernel group, from the
 # ncu --set full capture on the 110,592-atom water box summarised in
 # profiles/k_force_k_sf_water_110k.md (a 2M-atom launch moves the same bytes per
-# atom: list rows, positions and pair-queue records all scale with atoms).  Valid only for the kernel sources with this hash;
+# atom: list rows, positions, pair-queue and staged-neighbour records all scale with atoms).  Valid only for the kernel sources with this hash;
 # otherwise traffic is null.
-TRAFFIC = {"force": (470.266112e6 + 5.384448e6) / 110592, "descriptors": (84.519936e6 + 329.367296e6) / 110592}
-TRAFFIC_SRC_SHA = "344cb4eccf1e"
+TRAFFIC = {"force": (870.938368e6 + 6.496256e6) / 110592, "descriptors": (90.184704e6 + 783.948544e6) / 110592}
+TRAFFIC_SRC_SHA = "92947e016208"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
@@ -678,7 +678,7 @@ def main():
            "config": {"workload": args.workload, "description": desc, "atoms_per_gpu": n, "dt_fs": DT_FS,
                       "parallelism": "replicas" if world > 1 else "single",
                       "l2": "inputs larger than L2: the neighbour list alone is %.1f GB per GPU, the stored "
-                            "pair queues about 3.6 KB per atom" % (n * max_nb * 4 / 1e9),
+                            "pair queues about 3.6 KB and the staged neighbours about 6 KB per atom" % (n * max_nb * 4 / 1e9),
                       "mlp_precision": "fp32"},
            "e2e": e2e, "gpu_launches": st["kernel_launches"], "roofline": roof, "clocks": clocks,
            "kernels_ms": {k: round(v[0], 3) for k, v in timed.items()},
