@@ -86,6 +86,15 @@ __host__ __device__ inline unsigned long long queue_record_bound(int M)
     return (unsigned long long)queue_entries_start(nb) + (unsigned long long)M * (M - 1) / 2 + 7 * nbp;
 }
 
+// L2 prefetch of [p, p + bytes) by the lanes of a warp, one 128-byte line per
+// instruction (every address lies inside the range).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int lane)
+{
+    const char* c = static_cast<const char*>(p);
+    for (size_t o = (size_t)lane * 128; o < bytes; o += 32 * 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+    if (lane == 31 && bytes > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(c + bytes - 1));
+}
+
 // true when atom i must be skipped by this pass (M > C)
 __device__ __forceinline__ bool over_capacity(int M, int C, int pass, int i, int* spill, bool enqueue, int lane,
                                               int* flags, unsigned long long& c_spill)
@@ -553,14 +562,20 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         for (int cls = 0; NETA > 0 && cls < ncls; ++cls) {
             constexpr int NQ = NETA > 0 ? NETA : 1, NP = (NQ + 1) / 2;
             constexpr int NA = NQ * 2 * (NNP_KMAX + 1);   // dense accumulators, index (q*2 + l)*(KMAX+1) + k
-            // accumulators of eta pairs (q = 2p, 2p + 1) as packed f32x2
-            float2 acc[NP][2][NNP_KMAX + 1];
+            // accumulators per eta: (lambda = +1, lambda = -1) as packed f32x2 for
+            // k <= KLO, where both powers come out of one packed chain; beyond, the
+            // one lambda that goes on (TX: lambda = +1) as floats
+            constexpr int KLO = KP < KN ? KP : KN, KM = KP > KN ? KP : KN;
+            constexpr bool TX = KP > KN;
+            float2 accL[NQ][KLO + 1];
+            float accT[NQ][KM - KLO + 1];
 #pragma unroll
-            for (int p = 0; p < NP; ++p)
+            for (int q = 0; q < NQ; ++q) {
 #pragma unroll
-                for (int l = 0; l < 2; ++l)
+                for (int kk = 0; kk <= KLO; ++kk) accL[q][kk] = f2(0.f, 0.f);
 #pragma unroll
-                    for (int kk = 0; kk <= NNP_KMAX; ++kk) acc[p][l][kk] = f2(0.f, 0.f);
+                for (int kk = 0; kk <= KM - KLO; ++kk) accT[q][kk] = 0.f;
+            }
             float2 KH[NP], KL[NP];
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
@@ -635,24 +650,23 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                                 float dfcd;
                                 cutoff_fn_fast(rd2 * rsqrtf(rd2), P.hpi_rc, fcd, dfcd);
                             }
-                            // b_(+/-)^(2^k), b_(+/-) = 1 +/- c: both lambdas in one packed chain
-                            // while both go on
-                            constexpr int KLO = KP < KN ? KP : KN;
-                            float pw[2][NNP_KMAX + 1];
-                            float2 pp = fma2(f2(c, c), f2(1.f, -1.f), f2(1.f, 1.f));
-                            pw[0][0] = pp.x;
-                            pw[1][0] = pp.y;
+                            // PP[k] = (b_+^(2^k), b_-^(2^k)), b_(+/-) = 1 +/- c, one packed chain while
+                            // both lambdas go on; pt: the one that goes on beyond KLO
+                            float2 PP[KLO + 1];
+                            PP[0] = fma2(f2(c, c), f2(1.f, -1.f), f2(1.f, 1.f));
 #pragma unroll
-                            for (int kk = 1; kk <= NNP_KMAX; ++kk) {
-                                if (kk <= KLO) {
-                                    pp = mul2(pp, pp);
-                                    pw[0][kk] = pp.x;
-                                    pw[1][kk] = pp.y;
-                                } else {
-                                    if (kk <= KP) pw[0][kk] = pw[0][kk - 1] * pw[0][kk - 1];
-                                    if (kk <= KN) pw[1][kk] = pw[1][kk - 1] * pw[1][kk - 1];
+                            for (int kk = 1; kk <= KLO; ++kk) PP[kk] = mul2(PP[kk - 1], PP[kk - 1]);
+                            float pt[KM - KLO + 1];
+                            {
+                                float x = TX ? PP[KLO].x : PP[KLO].y;
+#pragma unroll
+                                for (int kk = KLO + 1; kk <= KM; ++kk) {
+                                    x *= x;
+                                    pt[kk - KLO - 1] = x;
                                 }
                             }
+                            // R_q = P_q(r_ij) P_q(r_ik) (P_q(r_jk) f_c(r_jk) for the narrow kind)
+                            float Rq[NQ];
                             if constexpr (NETA % 2 == 0) {
                                 // even eta count: both of a pair in one packed instruction
 #pragma unroll
@@ -663,30 +677,27 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                                         const float2 arg = fma2(KH[p], x2, mul2(KL[p], x2));
                                         R = mul2(R, mul2(f2(exp2f(arg.x), exp2f(arg.y)), f2(fcd, fcd)));
                                     }
-#pragma unroll
-                                    for (int lb = 0; lb < 2; ++lb)
-#pragma unroll
-                                        for (int kk = 0; kk <= NNP_KMAX; ++kk)
-                                            if (kk <= (lb == 0 ? KP : KN))
-                                                acc[p][lb][kk] = fma2(f2(pw[lb][kk], pw[lb][kk]), R, acc[p][lb][kk]);
+                                    Rq[2 * p] = R.x;
+                                    Rq[2 * p + 1] = R.y;
                                 }
                             } else {
                                 // odd eta count: a padded pair would cost more than it saves
 #pragma unroll
-                                for (int q = 0; q < NETA; ++q) {
+                                for (int q = 0; q < NQ; ++q) {
                                     const float2 pa = PA[q >> 1], pb = PB[q >> 1];
                                     float R = (q & 1) ? pa.y * pb.y : pa.x * pb.x;
                                     if (NARROW) R *= gauss2(khi[q], klo[q], rd2) * fcd;
-#pragma unroll
-                                    for (int lb = 0; lb < 2; ++lb)
-#pragma unroll
-                                        for (int kk = 0; kk <= NNP_KMAX; ++kk)
-                                            if (kk <= (lb == 0 ? KP : KN)) {
-                                                float2& a2 = acc[q >> 1][lb][kk];
-                                                if (q & 1) a2.y = fmaf(pw[lb][kk], R, a2.y);
-                                                else a2.x = fmaf(pw[lb][kk], R, a2.x);
-                                            }
+                                    Rq[q] = R;
                                 }
+                            }
+#pragma unroll
+                            for (int q = 0; q < NQ; ++q) {
+                                const float2 R2 = f2(Rq[q], Rq[q]);
+#pragma unroll
+                                for (int kk = 0; kk <= KLO; ++kk) accL[q][kk] = fma2(PP[kk], R2, accL[q][kk]);
+#pragma unroll
+                                for (int kk = KLO + 1; kk <= KM; ++kk)
+                                    accT[q][kk - KLO - 1] = fmaf(pt[kk - KLO - 1], Rq[q], accT[q][kk - KLO - 1]);
                             }
                         }
                     }
@@ -702,7 +713,12 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 for (int t = 0; t < 32; ++t) {
                     const int idx = c0 + t;
                     const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
-                    v[t] = (idx < NA) ? ((q & 1) ? acc[q >> 1][l][kk].y : acc[q >> 1][l][kk].x) : 0.f;
+                    float a = 0.f;
+                    if (idx < NA) {
+                        if (kk <= KLO) a = (l == 0) ? accL[q][kk].x : accL[q][kk].y;
+                        else if (kk <= KM && (l == 0) == TX) a = accT[q][kk - KLO - 1];
+                    }
+                    v[t] = a;
                 }
                 const double tot = warp_reduce_scatter32(v, lane);
                 const int idx = c0 + lane;
@@ -759,7 +775,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         double* __restrict__ vir_part, int* __restrict__ flags, int* __restrict__ spill, int pass,
         const unsigned short* __restrict__ qpool, const unsigned int* __restrict__ qoff,
         float* __restrict__ Fscat, unsigned long long* __restrict__ Fq, const float4* __restrict__ stg,
-        size_t stg_plane)
+        size_t stg_plane, unsigned long long qcap)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const Plan& P = *plan_g;
@@ -823,6 +839,12 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         unsigned sig = 0u;
         int M;
         const unsigned short* rec = nullptr;
+        // the queue record of this warp's next atom goes to L2 once its offset has
+        // arrived (after this atom's staging); the force pass reads records round by
+        // round, so their first reads would otherwise wait on DRAM (prefetching the
+        // next atom's staged neighbours as well measured slower)
+        unsigned o_next = QOFF_NONE;
+        if (staged && it + nw < n_items) o_next = qoff[atom_at(pass, it + nw, spill)];
         if (staged) {
             // the descriptor pass's staging of this atom; its queue record gives M
             const unsigned o = (NETA > 0) ? qoff[i] : QOFF_NONE;
@@ -841,6 +863,11 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 const int jj = __float_as_int(ax.w);
                 w.jidx[m] = jj & (int)NB_INDEX_MASK;
                 radial_g(w, P, E, m, ax.x, a.w, ax.y, ax.z, (int)((unsigned)jj >> 24), a.x, a.y, a.z, flags);
+            }
+            if (o_next < QOFF_SPILLED) {   // up to 4 KB of the record, inside the pool
+                const unsigned long long e0 = (unsigned long long)o_next * 8;
+                const unsigned long long e1 = e0 + 2048 < qcap ? e0 + 2048 : qcap;
+                if (e1 > e0) prefetch_l2(qpool + e0, (size_t)(e1 - e0) * 2, lane);
             }
             __syncwarp();
         } else {

@@ -392,7 +392,7 @@ typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, floa
                          int*, int, unsigned short*, unsigned int*, unsigned long long, float4*, size_t);
 typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
                             double*, int*, int*, int, const unsigned short*, const unsigned int*, float*,
-                            unsigned long long*, const float4*, size_t);
+                            unsigned long long*, const float4*, size_t, unsigned long long);
 
 typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*, int*, int);
 
@@ -937,12 +937,12 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
             n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, vir_out ? h->vpart : nullptr,
             h->flags, h->spill, 0,
             stored ? h->qpool : nullptr, stored ? h->qoff : nullptr, Fsc, Fq, (stored && staged) ? h->stg : nullptr,
-            stg_plane);
+            stg_plane, stored ? (unsigned long long)h->cap_qpool : 0ull);
         kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride,
                                                                        h->dEdG, h->gbuf, h->Fown,
                                                                        vir_out ? h->vpart + (size_t)nvp_main * 9 : nullptr,
                                                                        h->flags,
-                                                                       h->spill, 1, nullptr, nullptr, Fsc, Fq, nullptr, 0);
+                                                                       h->spill, 1, nullptr, nullptr, Fsc, Fq, nullptr, 0, 0ull);
     }
     if (h->fmode == FM_GATHER) {
         KScope ks(h, KG_GATHER, st);
@@ -1786,10 +1786,10 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     const int gmlp = std::min(blocks_for(n, 128), h->grid_mlp);
     h->kmlp<<<gmlp, 128, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
     kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, vpart,
-                                                     flags, spill, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0);
+                                                     flags, spill, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0ull);
     kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, dEdG, gbuf, Fown,
                                                                    vpart + (size_t)nvp_main * 9, flags, spill, 1, nullptr, nullptr, nullptr,
-                                                                   nullptr, nullptr, 0);
+                                                                   nullptr, nullptr, 0, 0ull);
     k_gather<<<rows_grid, 256, 0, st>>>(n, nv, rev, gbuf, Fown, forces ? forces : Fs, flags);
     k_sum_partial<<<gred, T, 0, st>>>(n, Ei, epart, flags);
     k_finalize<<<1, 256, 0, st>>>(gred, epart, energy, nvp, vpart, nullptr);
