@@ -137,6 +137,11 @@ __device__ __forceinline__ void cutoff_fn_fast(float r, float hpi_rc, float& fc,
     dfc = -2.0f * hpi_rc * s * c;
 }
 
+// Units of the force pass's fixed-point sums: the high word counts 2^-FX_HB eV/A,
+// the low word (and the int64 force sums) 2^-FX_LB eV/A.
+#define FX_HB 2
+#define FX_LB 23
+
 // Packed FP32 pairs (one f32x2 instruction for two IEEE round-to-nearest
 // operations; each component is rounded exactly as the scalar operation).
 __device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }

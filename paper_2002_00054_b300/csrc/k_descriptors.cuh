@@ -148,35 +148,39 @@ __host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool
 }
 
 // Fixed-point accumulation of the force pass.  A contribution v, |v| < FX_LIMIT
-// eV/A, is split exactly into hi = round(v 2^6) and lo = round((v - hi 2^-6) 2^27)
-// (the remainder is a float difference of nearby values, so it is exact), and each
-// part is added into its own int32 word with a native shared-memory integer atomic.
-// Per add |hi| < 2^21 and |lo| <= 2^20, so the up to 1024 adds a neighbour receives
-// (list stride <= 1024) cannot overflow either word; the only rounding is 2^-28
-// eV/A per add, and the sums do not depend on the order of the adds.
+// eV/A, is split exactly into hi = round(v 2^H) and lo = round((v - hi 2^-H) 2^L)
+// (H = FX_HB, L = FX_LB; the remainder is a float difference of nearby values, so
+// it is exact), and each part is added into its own int32 word with a native
+// shared-memory integer atomic.  Per add |hi| < 2^21 and |lo| <= 2^(L-H-1) <= 2^20,
+// so the up to 1024 adds a neighbour receives (list stride <= 1024) cannot
+// overflow either word; the only rounding is 2^-(L+1) eV/A per add, and the sums
+// do not depend on the order of the adds.  hi is zero for |v| < 2^-(H+1).
 #define FX_LIMIT 32000.0f
+static_assert(FX_LB - FX_HB <= 21 && FX_HB >= 0 && FX_HB <= 6, "fixed-point word ranges");
 // The roundings to integers use the 1.5 * 2^23 shift: for |x| < 2^22, x + 1.5 * 2^23
 // rounds x to the nearest integer, which then sits in the low mantissa bits
 // (integer = bits(x + S) - bits(S)), and (x + S) - S is that integer as a float;
-// no float/int conversion instructions.  |v 2^6| < 2^22 and |r 2^27| <= 2^20 hold
+// no float/int conversion instructions.  |v 2^H| < 2^22 and |r 2^L| <= 2^20 hold
 // for |v| < FX_LIMIT.
+#define FX_HS ((float)(1 << FX_HB))
+#define FX_LS ((float)(1 << FX_LB))
 __device__ __forceinline__ void fx_split(float v, int& hi, int& lo)
 {
     const float S = 12582912.0f;   // 1.5 * 2^23
-    const float th = fmaf(v, 64.0f, S);
+    const float th = fmaf(v, FX_HS, S);
     hi = __float_as_int(th) - __float_as_int(S);
-    const float r = fmaf(th - S, -1.0f / 64.0f, v);
-    lo = __float_as_int(fmaf(r, 134217728.0f, S)) - __float_as_int(S);
+    const float r = fmaf(th - S, -1.0f / FX_HS, v);
+    lo = __float_as_int(fmaf(r, FX_LS, S)) - __float_as_int(S);
 }
 // Two contributions at once (packed f32x2 arithmetic, the same roundings).
 __device__ __forceinline__ void fx_split2(float2 v, int& hx, int& lx, int& hy, int& ly)
 {
     const float S = 12582912.0f;
-    const float2 th = fma2(v, f2(64.0f, 64.0f), f2(S, S));
+    const float2 th = fma2(v, f2(FX_HS, FX_HS), f2(S, S));
     hx = __float_as_int(th.x) - __float_as_int(S);
     hy = __float_as_int(th.y) - __float_as_int(S);
-    const float2 r = fma2(add2(th, f2(-S, -S)), f2(-1.0f / 64.0f, -1.0f / 64.0f), v);
-    const float2 tl = fma2(r, f2(134217728.0f, 134217728.0f), f2(S, S));
+    const float2 r = fma2(add2(th, f2(-S, -S)), f2(-1.0f / FX_HS, -1.0f / FX_HS), v);
+    const float2 tl = fma2(r, f2(FX_LS, FX_LS), f2(S, S));
     lx = __float_as_int(tl.x) - __float_as_int(S);
     ly = __float_as_int(tl.y) - __float_as_int(S);
 }
@@ -205,12 +209,12 @@ __device__ __forceinline__ void fx_add(const WarpSmem& w, int idx, float v)
 }
 __device__ __forceinline__ float fx_get(const WarpSmem& w, int idx)
 {
-    return fmaf((float)w.sgl[idx], 1.0f / 134217728.0f, (float)w.sgh[idx] * (1.0f / 64.0f));
+    return fmaf((float)w.sgl[idx], 1.0f / FX_LS, (float)w.sgh[idx] * (1.0f / FX_HS));
 }
-// the same sum as one integer in units of 2^-27 eV/A (exact: |value| < 2^52)
+// the same sum as one integer in units of 2^-FX_LB eV/A (exact: |value| < 2^52)
 __device__ __forceinline__ long long fx_get64(const WarpSmem& w, int idx)
 {
-    return (long long)w.sgh[idx] * 2097152LL + (long long)w.sgl[idx];
+    return (long long)w.sgh[idx] * (1ll << (FX_LB - FX_HB)) + (long long)w.sgl[idx];
 }
 
 // Narrow-kind live test r_jk < rc written with h = r^2 / 2 - rc^2 / 4 of each
@@ -1102,9 +1106,33 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             const float2 gaxy = fma2(f2(ca, ca), axy, fma2(f2(cab, cab), bxy, mul2(f2(-cd, -cd), exy)));
                             const float2 gbxy = fma2(f2(cb, cb), bxy, fma2(f2(cab, cab), axy, mul2(f2(cd, cd), exy)));
                             const float2 gz = fma2(f2(ca, cb), f2(a.z, b.z), fma2(f2(cab, cab), f2(b.z, a.z), mul2(f2(-cd, cd), f2(ez, ez))));
-                            fx_add2(w, 3 * j + 0, 3 * j + 1, gaxy);
-                            fx_add2(w, 3 * k + 0, 3 * k + 1, gbxy);
-                            fx_add2(w, 3 * j + 2, 3 * k + 2, gz);
+                            // narrow kind: low words always, the high words only when a lane
+                            // of the warp has one (a contribution of at least 2^-(FX_HB+1)
+                            // eV/A); the wide kind's larger contributions seldom skip them
+                            if constexpr (!NARROW) {
+                                fx_add2(w, 3 * j + 0, 3 * j + 1, gaxy);
+                                fx_add2(w, 3 * k + 0, 3 * k + 1, gbxy);
+                                fx_add2(w, 3 * j + 2, 3 * k + 2, gz);
+                            } else {
+                            int h0, l0, h1, l1, h2, l2, h3, l3, h4, l4, h5, l5;
+                            fx_split2(gaxy, h0, l0, h1, l1);
+                            fx_split2(gbxy, h2, l2, h3, l3);
+                            fx_split2(gz, h4, l4, h5, l5);
+                            atomicAdd(&w.sgl[3 * j + 0], l0);
+                            atomicAdd(&w.sgl[3 * j + 1], l1);
+                            atomicAdd(&w.sgl[3 * k + 0], l2);
+                            atomicAdd(&w.sgl[3 * k + 1], l3);
+                            atomicAdd(&w.sgl[3 * j + 2], l4);
+                            atomicAdd(&w.sgl[3 * k + 2], l5);
+                            if (__any_sync(__activemask(), (h0 | h1 | h2 | h3 | h4 | h5) != 0)) {
+                                if (h0) atomicAdd(&w.sgh[3 * j + 0], h0);
+                                if (h1) atomicAdd(&w.sgh[3 * j + 1], h1);
+                                if (h2) atomicAdd(&w.sgh[3 * k + 0], h2);
+                                if (h3) atomicAdd(&w.sgh[3 * k + 1], h3);
+                                if (h4) atomicAdd(&w.sgh[3 * j + 2], h4);
+                                if (h5) atomicAdd(&w.sgh[3 * k + 2], h5);
+                            }
+                            }
                         }
                     }
                     __syncwarp();
@@ -1113,7 +1141,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         }
         __syncwarp();
         // force assembly: with Fq, -g_ij is added into F_j as one 64-bit integer per
-        // component (units 2^-27 eV/A; integer sums do not depend on the order of
+        // component (units 2^-FX_LB eV/A; integer sums do not depend on the order of
         // the atomics, so the forces are reproducible bit for bit); with Fscat, as
         // floats (order-dependent); otherwise g is written per list slot for the
         // gather.  Then the own force and the virial.

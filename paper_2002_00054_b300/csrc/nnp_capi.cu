@@ -159,7 +159,7 @@ struct nnp_handle {
     // Fq; FM_GATHER per-slot g buffer and reverse-index gather; FM_FLOAT float
     // atomics (order-dependent)
     int fmode = 0;
-    unsigned long long* Fq = nullptr;   // [cap_n][3], units 2^-27 eV/A
+    unsigned long long* Fq = nullptr;   // [cap_n][3], units 2^-FX_LB eV/A
     // staged neighbours written by the descriptor pass for the force pass: three
     // planes of cap_stg float4 (atom i, staged index m at i * C + m)
     bool use_stg = true;
