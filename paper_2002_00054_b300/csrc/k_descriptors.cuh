@@ -184,6 +184,14 @@ __device__ __forceinline__ void fx_split2(float2 v, int& hx, int& lx, int& hy, i
     lx = __float_as_int(tl.x) - __float_as_int(S);
     ly = __float_as_int(tl.y) - __float_as_int(S);
 }
+// lo alone, for |v| < 2^-(FX_HB+1) (hi = 0): the same bits as fx_split2's lo
+__device__ __forceinline__ void fx_lo2(float2 v, int& lx, int& ly)
+{
+    const float S = 12582912.0f;
+    const float2 tl = fma2(v, f2(FX_LS, FX_LS), f2(S, S));
+    lx = __float_as_int(tl.x) - __float_as_int(S);
+    ly = __float_as_int(tl.y) - __float_as_int(S);
+}
 __device__ __forceinline__ void fx_add2(const WarpSmem& w, int ix, int iy, float2 v)
 {
     int hx, lx, hy, ly;
@@ -1114,17 +1122,26 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                 fx_add2(w, 3 * k + 0, 3 * k + 1, gbxy);
                                 fx_add2(w, 3 * j + 2, 3 * k + 2, gz);
                             } else {
-                            int h0, l0, h1, l1, h2, l2, h3, l3, h4, l4, h5, l5;
-                            fx_split2(gaxy, h0, l0, h1, l1);
-                            fx_split2(gbxy, h2, l2, h3, l3);
-                            fx_split2(gz, h4, l4, h5, l5);
+                            const float vm = fmaxf(fmaxf(fmaxf(fabsf(gaxy.x), fabsf(gaxy.y)), fmaxf(fabsf(gbxy.x), fabsf(gbxy.y))),
+                                                   fmaxf(fabsf(gz.x), fabsf(gz.y)));
+                            int h0 = 0, l0, h1 = 0, l1, h2 = 0, l2, h3 = 0, l3, h4 = 0, l4, h5 = 0, l5;
+                            const bool small = __all_sync(__activemask(), vm < 0.5f / FX_HS);
+                            if (small) {
+                                fx_lo2(gaxy, l0, l1);
+                                fx_lo2(gbxy, l2, l3);
+                                fx_lo2(gz, l4, l5);
+                            } else {
+                                fx_split2(gaxy, h0, l0, h1, l1);
+                                fx_split2(gbxy, h2, l2, h3, l3);
+                                fx_split2(gz, h4, l4, h5, l5);
+                            }
                             atomicAdd(&w.sgl[3 * j + 0], l0);
                             atomicAdd(&w.sgl[3 * j + 1], l1);
                             atomicAdd(&w.sgl[3 * k + 0], l2);
                             atomicAdd(&w.sgl[3 * k + 1], l3);
                             atomicAdd(&w.sgl[3 * j + 2], l4);
                             atomicAdd(&w.sgl[3 * k + 2], l5);
-                            if (__any_sync(__activemask(), (h0 | h1 | h2 | h3 | h4 | h5) != 0)) {
+                            if (!small) {
                                 if (h0) atomicAdd(&w.sgh[3 * j + 0], h0);
                                 if (h1) atomicAdd(&w.sgh[3 * j + 1], h1);
                                 if (h2) atomicAdd(&w.sgh[3 * k + 0], h2);
