@@ -387,7 +387,11 @@ __device__ __forceinline__ unsigned live_mask(int A, int B, int l, int M, const 
     const float4* blk = nd + 32 * B;
     auto hk = [&](int k, const float4& b) { return HS == 0 ? b.w : nh[HS * (32 * B + k)]; };
     unsigned mask = 0u;
-    if (32 * B + 32 <= M) {
+    // HS = 0 (descriptor pass): a partner block with at least 16 present takes the
+    // unrolled walk too, masked by v afterwards; its reads past M stay inside the
+    // warp's nd and npf arrays (32 B + 31 <= M + 15 < 2C).  Measured: 16 is faster
+    // than 8 or 1 here.
+    if (32 * B + 32 <= M || (HS == 0 && 32 * B + 16 <= M)) {
         if (A == B) {
 #pragma unroll
             for (int s = 1; s <= 16; ++s) {
