@@ -137,10 +137,14 @@ __device__ __forceinline__ void cutoff_fn_fast(float r, float hpi_rc, float& fc,
     dfc = -2.0f * hpi_rc * s * c;
 }
 
-// Units of the force pass's fixed-point sums: the high word counts 2^-FX_HB eV/A,
-// the low word (and the int64 force sums) 2^-FX_LB eV/A.
-#define FX_HB 2
-#define FX_LB 23
+// Units of the force pass's fixed-point sums, per angular kind: the high word
+// counts 2^-HB eV/A, the low word (and the int64 force sums) 2^-LB eV/A.  The
+// narrow kind's coarse high word is zero for contributions below 1/8 eV/A, so a
+// warp can skip its atomics; the wide kind keeps the finer low word.
+#define FX_HB_NARROW 2
+#define FX_LB_NARROW 23
+#define FX_HB_WIDE 6
+#define FX_LB_WIDE 27
 
 // Packed FP32 pairs (one f32x2 instruction for two IEEE round-to-nearest
 // operations; each component is rounded exactly as the scalar operation).

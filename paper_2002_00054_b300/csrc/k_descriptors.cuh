@@ -149,21 +149,27 @@ __host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool
 
 // Fixed-point accumulation of the force pass.  A contribution v, |v| < FX_LIMIT
 // eV/A, is split exactly into hi = round(v 2^H) and lo = round((v - hi 2^-H) 2^L)
-// (H = FX_HB, L = FX_LB; the remainder is a float difference of nearby values, so
+// (H, L: FxU<NARROW>; the remainder is a float difference of nearby values, so
 // it is exact), and each part is added into its own int32 word with a native
 // shared-memory integer atomic.  Per add |hi| < 2^21 and |lo| <= 2^(L-H-1) <= 2^20,
 // so the up to 1024 adds a neighbour receives (list stride <= 1024) cannot
 // overflow either word; the only rounding is 2^-(L+1) eV/A per add, and the sums
 // do not depend on the order of the adds.  hi is zero for |v| < 2^-(H+1).
 #define FX_LIMIT 32000.0f
-static_assert(FX_LB - FX_HB <= 21 && FX_HB >= 0 && FX_HB <= 6, "fixed-point word ranges");
+template <bool N>
+struct FxU {
+    static constexpr int HB = N ? FX_HB_NARROW : FX_HB_WIDE, LB = N ? FX_LB_NARROW : FX_LB_WIDE;
+    static_assert(LB - HB <= 21 && HB >= 0 && HB <= 6, "fixed-point word ranges");
+};
 // The roundings to integers use the 1.5 * 2^23 shift: for |x| < 2^22, x + 1.5 * 2^23
 // rounds x to the nearest integer, which then sits in the low mantissa bits
 // (integer = bits(x + S) - bits(S)), and (x + S) - S is that integer as a float;
 // no float/int conversion instructions.  |v 2^H| < 2^22 and |r 2^L| <= 2^20 hold
 // for |v| < FX_LIMIT.
-#define FX_HS ((float)(1 << FX_HB))
-#define FX_LS ((float)(1 << FX_LB))
+// (inside the helpers below, which are templated on the kind N)
+#define FX_HS ((float)(1 << FxU<N>::HB))
+#define FX_LS ((float)(1 << FxU<N>::LB))
+template <bool N>
 __device__ __forceinline__ void fx_split(float v, int& hi, int& lo)
 {
     const float S = 12582912.0f;   // 1.5 * 2^23
@@ -173,6 +179,7 @@ __device__ __forceinline__ void fx_split(float v, int& hi, int& lo)
     lo = __float_as_int(fmaf(r, FX_LS, S)) - __float_as_int(S);
 }
 // Two contributions at once (packed f32x2 arithmetic, the same roundings).
+template <bool N>
 __device__ __forceinline__ void fx_split2(float2 v, int& hx, int& lx, int& hy, int& ly)
 {
     const float S = 12582912.0f;
@@ -184,7 +191,8 @@ __device__ __forceinline__ void fx_split2(float2 v, int& hx, int& lx, int& hy, i
     lx = __float_as_int(tl.x) - __float_as_int(S);
     ly = __float_as_int(tl.y) - __float_as_int(S);
 }
-// lo alone, for |v| < 2^-(FX_HB+1) (hi = 0): the same bits as fx_split2's lo
+// lo alone, for |v| < 2^-(HB+1) (hi = 0): the same bits as fx_split2's lo
+template <bool N>
 __device__ __forceinline__ void fx_lo2(float2 v, int& lx, int& ly)
 {
     const float S = 12582912.0f;
@@ -192,37 +200,42 @@ __device__ __forceinline__ void fx_lo2(float2 v, int& lx, int& ly)
     lx = __float_as_int(tl.x) - __float_as_int(S);
     ly = __float_as_int(tl.y) - __float_as_int(S);
 }
+template <bool N>
 __device__ __forceinline__ void fx_add2(const WarpSmem& w, int ix, int iy, float2 v)
 {
     int hx, lx, hy, ly;
-    fx_split2(v, hx, lx, hy, ly);
+    fx_split2<N>(v, hx, lx, hy, ly);
     atomicAdd(&w.sgh[ix], hx);
     atomicAdd(&w.sgl[ix], lx);
     atomicAdd(&w.sgh[iy], hy);
     atomicAdd(&w.sgl[iy], ly);
 }
+template <bool N>
 __device__ __forceinline__ void fx_set(const WarpSmem& w, int idx, float v)
 {
     int hi, lo;
-    fx_split(v, hi, lo);
+    fx_split<N>(v, hi, lo);
     w.sgh[idx] = hi;
     w.sgl[idx] = lo;
 }
+template <bool N>
 __device__ __forceinline__ void fx_add(const WarpSmem& w, int idx, float v)
 {
     int hi, lo;
-    fx_split(v, hi, lo);
+    fx_split<N>(v, hi, lo);
     atomicAdd(&w.sgh[idx], hi);
     atomicAdd(&w.sgl[idx], lo);
 }
+template <bool N>
 __device__ __forceinline__ float fx_get(const WarpSmem& w, int idx)
 {
     return fmaf((float)w.sgl[idx], 1.0f / FX_LS, (float)w.sgh[idx] * (1.0f / FX_HS));
 }
-// the same sum as one integer in units of 2^-FX_LB eV/A (exact: |value| < 2^52)
+// the same sum as one integer in units of 2^-LB eV/A (exact: |value| < 2^52)
+template <bool N>
 __device__ __forceinline__ long long fx_get64(const WarpSmem& w, int idx)
 {
-    return (long long)w.sgh[idx] * (1ll << (FX_LB - FX_HB)) + (long long)w.sgl[idx];
+    return (long long)w.sgh[idx] * (1ll << (FxU<N>::LB - FxU<N>::HB)) + (long long)w.sgl[idx];
 }
 
 // Narrow-kind live test r_jk < rc written with h = r^2 / 2 - rc^2 / 4 of each
@@ -239,6 +252,7 @@ __device__ __forceinline__ bool live_pair(const float4 a, float ha, const float4
 // Radial part of g_ij for staged neighbour `at`: the sum over the radial
 // descriptors that take the neighbour's element of dE/dG * dG/dr * d / r, into
 // the fixed-point accumulators.
+template <bool N>
 __device__ __forceinline__ void radial_g(const WarpSmem& w, const Plan& P, const ElemPlan& E, int at, float r, float ir,
                                          float fc, float dfc, int ej, float dx, float dy, float dz, int* flags)
 {
@@ -253,14 +267,15 @@ __device__ __forceinline__ void radial_g(const WarpSmem& w, const Plan& P, const
     for (int rr = E.rad_beg[ej], re = E.rad_end[ej]; rr < re; ++rr) rad(rr);
     const float gs = gr * ir;
     if (!(fabsf(gs) * P.rc < FX_LIMIT)) atomicOr(&flags[FLAG_ERR], ERR_RANGE);
-    fx_set(w, 3 * at + 0, gs * dx);
-    fx_set(w, 3 * at + 1, gs * dy);
-    fx_set(w, 3 * at + 2, gs * dz);
+    fx_set<N>(w, 3 * at + 0, gs * dx);
+    fx_set<N>(w, 3 * at + 1, gs * dy);
+    fx_set<N>(w, 3 * at + 2, gs * dz);
 }
 
 // Stages the neighbours of atom i within the cutoff, compacted in list order.
 // Returns M.  FORCE: nd.w = 1/r, dP/dr, the radial part of g (into sg), slot map.
-template <int NETA, bool FORCE>
+// N: the force pass's fixed-point units (FxU<N>).
+template <int NETA, bool FORCE, bool N = false>
 __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box& bx, const NbView& nv,
                                                const float4* __restrict__ pos4, const Plan& P, const ElemPlan& E,
                                                const float* khi, const float* klo, const float* etav, int C,
@@ -340,7 +355,7 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                     w.ndp[at] = make_float4(dq[0], dq[1], dq[2], dq[3]);
                 }
                 if (w.nel) w.nel[at] = (unsigned char)ej;
-                radial_g(w, P, E, at, r, ir, fc, dfc, ej, dx, dy, dz, flags);
+                radial_g<N>(w, P, E, at, r, ir, fc, dfc, ej, dx, dy, dz, flags);
             }
             if (!FORCE && stg) {
                 // staged record for the force pass, one plane each: (d, 1/r),
@@ -878,7 +893,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 w.npf[m] = pq;
                 const int jj = __float_as_int(ax.w);
                 w.jidx[m] = jj & (int)NB_INDEX_MASK;
-                radial_g(w, P, E, m, ax.x, a.w, ax.y, ax.z, (int)((unsigned)jj >> 24), a.x, a.y, a.z, flags);
+                radial_g<NARROW>(w, P, E, m, ax.x, a.w, ax.y, ax.z, (int)((unsigned)jj >> 24), a.x, a.y, a.z, flags);
             }
             if (o_next < QOFF_SPILLED) {   // up to 4 KB of the record, inside the pool
                 const unsigned long long e0 = (unsigned long long)o_next * 8;
@@ -888,8 +903,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             __syncwarp();
         } else {
             float r2_unused = 0.f;
-            M = stage_neighbors<NETA, true>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
-                                            n_list, sig, r2_unused);
+            M = stage_neighbors<NETA, true, NARROW>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, sW, lane, flags,
+                                                    n_list, sig, r2_unused);
             if (over_capacity(M, C, pass, i, spill, false, lane, flags, c_spill)) continue;
         }
         const int nb = (M + 31) >> 5;
@@ -968,6 +983,34 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 bnd += sm * qm * (NARROW ? 2.f : 1.f) + 2.f * iam * dm;
             }
             const bool exact = nonfin || !(bnd < 0.5f * FX_LIMIT);
+            // the same weights as eta pairs (q = 2p, 2p + 1) per lambda and k, for the
+            // packed sums S and D of the triplet loop; D's k = 0 terms are constant
+            constexpr bool QPAIR = NQ % 2 == 0;   // odd counts keep the lambda-pair sums
+            float2 WPp[QPAIR ? NP : 1][KP + 1], WPm[QPAIR ? NP : 1][KN + 1], D0[QPAIR ? NP : 1];
+#pragma unroll
+            for (int p = 0; QPAIR && p < NP; ++p) {
+#pragma unroll
+                for (int kk = 0; kk <= KP; ++kk) {
+                    float w2[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int q = 2 * p + h;
+                        w2[h] = (q >= NQ) ? 0.f : (kk <= KLO ? WL[q < NQ ? q : 0][kk].x : (TX ? WT[q < NQ ? q : 0][kk - KLO - 1] : 0.f));
+                    }
+                    WPp[p][kk] = f2(w2[0], w2[1]);
+                }
+#pragma unroll
+                for (int kk = 0; kk <= KN; ++kk) {
+                    float w2[2];
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int q = 2 * p + h;
+                        w2[h] = (q >= NQ) ? 0.f : (kk <= KLO ? WL[q < NQ ? q : 0][kk].y : (!TX ? WT[q < NQ ? q : 0][kk - KLO - 1] : 0.f));
+                    }
+                    WPm[p][kk] = f2(w2[0], w2[1]);
+                }
+                D0[p] = add2(WPp[p][0], mul2(WPm[p][0], f2(-1.f, -1.f)));
+            }
             const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             int bp = QHDR, qpos = queue_entries_start(nb);
             for (int A = 0; A < nb; ++A) {
@@ -1054,7 +1097,35 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                     qt[kk - KLO - 1] = qk * (TX ? (float)(1 << kk) : -(float)(1 << kk));
                                 }
                             }
-                            // S_q = sum W pw, D_q = dS_q/dc (lambda pairs summed at the end)
+                            // (S_2p, S_2p+1) = sum W b^zeta and D = dS/dc as eta pairs
+                            float2 SP[NP], DP[NP];
+                            if constexpr (QPAIR) {
+#pragma unroll
+                            for (int p = 0; p < NP; ++p) {
+                                float2 s2 = f2(0.f, 0.f), d2 = D0[p];
+#pragma unroll
+                                for (int kk = 0; kk <= KP; ++kk) {
+                                    const float bp = (kk <= KLO) ? PW[kk].x : pt[kk - KLO - 1];
+                                    s2 = fma2(WPp[p][kk], f2(bp, bp), s2);
+                                    if (kk > 0) {
+                                        const float dp = (kk <= KLO) ? QS[kk].x : qt[kk - KLO - 1];
+                                        d2 = fma2(WPp[p][kk], f2(dp, dp), d2);
+                                    }
+                                }
+#pragma unroll
+                                for (int kk = 0; kk <= KN; ++kk) {
+                                    const float bm = (kk <= KLO) ? PW[kk].y : pt[kk - KLO - 1];
+                                    s2 = fma2(WPm[p][kk], f2(bm, bm), s2);
+                                    if (kk > 0) {
+                                        const float dm = (kk <= KLO) ? QS[kk].y : qt[kk - KLO - 1];
+                                        d2 = fma2(WPm[p][kk], f2(dm, dm), d2);
+                                    }
+                                }
+                                SP[p] = s2;
+                                DP[p] = d2;
+                            }
+                            } else {
+                            // odd eta count: S_q = sum W pw, D_q = dS_q/dc (lambda pairs summed at the end)
                             float Sq[2 * NP], Dq[2 * NP];
 #pragma unroll
                             for (int q = 0; q < 2 * NP; ++q) {
@@ -1077,10 +1148,16 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                                     Dq[q] = TX ? dt + d2.y : d2.x + dt;
                                 }
                             }
+#pragma unroll
+                            for (int p = 0; p < NP; ++p) {
+                                SP[p] = f2(Sq[2 * p], Sq[2 * p + 1]);
+                                DP[p] = f2(Dq[2 * p], Dq[2 * p + 1]);
+                            }
+                            }
                             float2 phic2 = f2(0.f, 0.f), phia2 = f2(0.f, 0.f), phib2 = f2(0.f, 0.f), phid2 = f2(0.f, 0.f);
 #pragma unroll
                             for (int p = 0; p < NP; ++p) {
-                                const float2 S2 = f2(Sq[2 * p], Sq[2 * p + 1]), D2 = f2(Dq[2 * p], Dq[2 * p + 1]);
+                                const float2 S2 = SP[p], D2 = DP[p];
                                 const float2 pab = mul2(PA[p], PB[p]);
                                 float2 SPd = S2, pabPd = pab;
                                 if (NARROW) {
@@ -1122,22 +1199,22 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             // of the warp has one (a contribution of at least 2^-(FX_HB+1)
                             // eV/A); the wide kind's larger contributions seldom skip them
                             if constexpr (!NARROW) {
-                                fx_add2(w, 3 * j + 0, 3 * j + 1, gaxy);
-                                fx_add2(w, 3 * k + 0, 3 * k + 1, gbxy);
-                                fx_add2(w, 3 * j + 2, 3 * k + 2, gz);
+                                fx_add2<NARROW>(w, 3 * j + 0, 3 * j + 1, gaxy);
+                                fx_add2<NARROW>(w, 3 * k + 0, 3 * k + 1, gbxy);
+                                fx_add2<NARROW>(w, 3 * j + 2, 3 * k + 2, gz);
                             } else {
                             const float vm = fmaxf(fmaxf(fmaxf(fabsf(gaxy.x), fabsf(gaxy.y)), fmaxf(fabsf(gbxy.x), fabsf(gbxy.y))),
                                                    fmaxf(fabsf(gz.x), fabsf(gz.y)));
                             int h0 = 0, l0, h1 = 0, l1, h2 = 0, l2, h3 = 0, l3, h4 = 0, l4, h5 = 0, l5;
-                            const bool small = __all_sync(__activemask(), vm < 0.5f / FX_HS);
+                            const bool small = __all_sync(__activemask(), vm < 0.5f / (float)(1 << FxU<NARROW>::HB));
                             if (small) {
-                                fx_lo2(gaxy, l0, l1);
-                                fx_lo2(gbxy, l2, l3);
-                                fx_lo2(gz, l4, l5);
+                                fx_lo2<NARROW>(gaxy, l0, l1);
+                                fx_lo2<NARROW>(gbxy, l2, l3);
+                                fx_lo2<NARROW>(gz, l4, l5);
                             } else {
-                                fx_split2(gaxy, h0, l0, h1, l1);
-                                fx_split2(gbxy, h2, l2, h3, l3);
-                                fx_split2(gz, h4, l4, h5, l5);
+                                fx_split2<NARROW>(gaxy, h0, l0, h1, l1);
+                                fx_split2<NARROW>(gbxy, h2, l2, h3, l3);
+                                fx_split2<NARROW>(gz, h4, l4, h5, l5);
                             }
                             atomicAdd(&w.sgl[3 * j + 0], l0);
                             atomicAdd(&w.sgl[3 * j + 1], l1);
@@ -1162,7 +1239,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         }
         __syncwarp();
         // force assembly: with Fq, -g_ij is added into F_j as one 64-bit integer per
-        // component (units 2^-FX_LB eV/A; integer sums do not depend on the order of
+        // component (units 2^-LB eV/A, FxU<NARROW>; integer sums do not depend on the order of
         // the atomics, so the forces are reproducible bit for bit); with Fscat, as
         // floats (order-dependent); otherwise g is written per list slot for the
         // gather.  Then the own force and the virial.
@@ -1170,9 +1247,9 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         if (Fq && staged) {
             for (int m = lane; m < M; m += 32) {
                 unsigned long long* fj = Fq + 3 * (size_t)w.jidx[m];
-                atomicAdd(fj + 0, (unsigned long long)(-fx_get64(w, 3 * m)));
-                atomicAdd(fj + 1, (unsigned long long)(-fx_get64(w, 3 * m + 1)));
-                atomicAdd(fj + 2, (unsigned long long)(-fx_get64(w, 3 * m + 2)));
+                atomicAdd(fj + 0, (unsigned long long)(-fx_get64<NARROW>(w, 3 * m)));
+                atomicAdd(fj + 1, (unsigned long long)(-fx_get64<NARROW>(w, 3 * m + 1)));
+                atomicAdd(fj + 2, (unsigned long long)(-fx_get64<NARROW>(w, 3 * m + 2)));
             }
         } else if (Fq) {
             const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
@@ -1180,9 +1257,9 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 const int c = w.cmap[s];
                 if (c >= 0) {
                     unsigned long long* fj = Fq + 3 * (size_t)(row[s] & NB_INDEX_MASK);
-                    atomicAdd(fj + 0, (unsigned long long)(-fx_get64(w, 3 * c)));
-                    atomicAdd(fj + 1, (unsigned long long)(-fx_get64(w, 3 * c + 1)));
-                    atomicAdd(fj + 2, (unsigned long long)(-fx_get64(w, 3 * c + 2)));
+                    atomicAdd(fj + 0, (unsigned long long)(-fx_get64<NARROW>(w, 3 * c)));
+                    atomicAdd(fj + 1, (unsigned long long)(-fx_get64<NARROW>(w, 3 * c + 1)));
+                    atomicAdd(fj + 2, (unsigned long long)(-fx_get64<NARROW>(w, 3 * c + 2)));
                 }
             }
         } else if (Fscat) {
@@ -1191,16 +1268,16 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 const int c = w.cmap[s];
                 if (c >= 0) {
                     float* fj = Fscat + 3 * (size_t)(row[s] & NB_INDEX_MASK);
-                    atomicAdd(fj + 0, -fx_get(w, 3 * c));
-                    atomicAdd(fj + 1, -fx_get(w, 3 * c + 1));
-                    atomicAdd(fj + 2, -fx_get(w, 3 * c + 2));
+                    atomicAdd(fj + 0, -fx_get<NARROW>(w, 3 * c));
+                    atomicAdd(fj + 1, -fx_get<NARROW>(w, 3 * c + 1));
+                    atomicAdd(fj + 2, -fx_get<NARROW>(w, 3 * c + 2));
                 }
             }
         } else {
             float4* grow = gbuf + (size_t)i * nv.stride;
             for (int s = lane; s < cnt; s += 32) {
                 const int c = w.cmap[s];
-                grow[s] = (c >= 0) ? make_float4(fx_get(w, 3 * c), fx_get(w, 3 * c + 1), fx_get(w, 3 * c + 2), 0.f)
+                grow[s] = (c >= 0) ? make_float4(fx_get<NARROW>(w, 3 * c), fx_get<NARROW>(w, 3 * c + 1), fx_get<NARROW>(w, 3 * c + 2), 0.f)
                                    : make_float4(0.f, 0.f, 0.f, 0.f);
             }
         }
@@ -1211,12 +1288,12 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         // the virial only when the caller asked for it (vir_part != nullptr)
         for (int m = lane; m < M; m += 32) {
             if (Fq) {
-                qx += fx_get64(w, 3 * m);
-                qy += fx_get64(w, 3 * m + 1);
-                qz += fx_get64(w, 3 * m + 2);
+                qx += fx_get64<NARROW>(w, 3 * m);
+                qy += fx_get64<NARROW>(w, 3 * m + 1);
+                qz += fx_get64<NARROW>(w, 3 * m + 2);
             }
             if (!Fq || vir_part) {
-                const float gx = fx_get(w, 3 * m), gy = fx_get(w, 3 * m + 1), gz = fx_get(w, 3 * m + 2);
+                const float gx = fx_get<NARROW>(w, 3 * m), gy = fx_get<NARROW>(w, 3 * m + 1), gz = fx_get<NARROW>(w, 3 * m + 2);
                 if (!Fq) {
                     fx += gx; fy += gy; fz += gz;
                 }

@@ -94,12 +94,13 @@ __global__ void k_kick_ke(int n, const Plan* __restrict__ plan_g, const int* __r
 }
 
 // log[2k + slot] = sum of partials (one block)
-// F = Fq 2^-FX_LB: the fixed-point scatter's integer sums with one rounding each
-// (|Fq| < 2^52, so the conversion to double and the scaling are exact)
-__global__ void k_fq_forces(int n3, const unsigned long long* __restrict__ Fq, float* __restrict__ F)
+// F = Fq unit: the fixed-point scatter's integer sums with one rounding each
+// (unit 2^-LB of the model's kind; |Fq| < 2^52, so the conversion to double and
+// the scaling are exact)
+__global__ void k_fq_forces(int n3, const unsigned long long* __restrict__ Fq, double unit, float* __restrict__ F)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n3) F[t] = (float)((double)(long long)Fq[t] * (1.0 / (double)(1ll << FX_LB)));
+    if (t < n3) F[t] = (float)((double)(long long)Fq[t] * unit);
 }
 
 // Energy-log entry s = (*slot)++: log[2s] = potential energy (*epot), log[2s+1] =

@@ -159,7 +159,7 @@ struct nnp_handle {
     // Fq; FM_GATHER per-slot g buffer and reverse-index gather; FM_FLOAT float
     // atomics (order-dependent)
     int fmode = 0;
-    unsigned long long* Fq = nullptr;   // [cap_n][3], units 2^-FX_LB eV/A
+    unsigned long long* Fq = nullptr;   // [cap_n][3], units 2^-LB eV/A (fq_unit)
     // staged neighbours written by the descriptor pass for the force pass: three
     // planes of cap_stg float4 (atom i, staged index m at i * C + m)
     bool use_stg = true;
@@ -455,6 +455,14 @@ static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
 {
     TangentKernel t;
     pick_kernels(P, s, f, t);
+}
+
+// Unit of the int64 force sums: the force kernels run the narrow instantiation
+// for narrow models with angular functions (pick_kernels), the wide one otherwise.
+static double fq_unit(const Plan& P)
+{
+    const bool nar = P.ang_kind == NNP_SF_ANG_NARROW && P.n_eta_max > 0;
+    return std::ldexp(1.0, -(nar ? FX_LB_NARROW : FX_LB_WIDE));
 }
 
 static size_t sf_smem_per_warp(int cap) { return sf_warp_bytes(cap); }
@@ -949,7 +957,7 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         k_gather<<<rows_grid, 256, 0, st>>>(n, nv, h->rev, h->gbuf, h->Fown, Fout, h->flags);
     } else if (Fq) {
         KScope ks(h, KG_GATHER, st);
-        k_fq_forces<<<blocks_for(3 * n, 256), 256, 0, st>>>(3 * n, Fq, Fout);
+        k_fq_forces<<<blocks_for(3 * n, 256), 256, 0, st>>>(3 * n, Fq, fq_unit(P), Fout);
     }
     if (bt) {
         KScope ks(h, KG_REDUCE, st);
