@@ -1190,11 +1190,14 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             if (exact)
                                 fx_bad |= !(fabsf(ua) + fabsf(ta) + fabsf(phid) < FX_LIMIT &&
                                             fabsf(ub) + fabsf(tb) + fabsf(phid) < FX_LIMIT);
-                            // (x, y) of g_a and of g_b, and (z of g_a, z of g_b), as packed pairs
-                            const float2 axy = f2(a.x, a.y), bxy = f2(b.x, b.y), exy = f2(ex, ey);
-                            const float2 gaxy = fma2(f2(ca, ca), axy, fma2(f2(cab, cab), bxy, mul2(f2(-cd, -cd), exy)));
-                            const float2 gbxy = fma2(f2(cb, cb), bxy, fma2(f2(cab, cab), axy, mul2(f2(cd, cd), exy)));
-                            const float2 gz = fma2(f2(ca, cb), f2(a.z, b.z), fma2(f2(cab, cab), f2(b.z, a.z), mul2(f2(-cd, cd), f2(ez, ez))));
+                            // with e = b - a: g_a = (ca + cd) a + (cab - cd) b, g_b = (cab - cd) a +
+                            // (cb + cd) b; (x, y) of g_a and of g_b, and (z of g_a, z of g_b), as
+                            // packed pairs
+                            const float xa = ca + cd, xab = cab - cd, xb = cb + cd;
+                            const float2 axy = f2(a.x, a.y), bxy = f2(b.x, b.y);
+                            const float2 gaxy = fma2(f2(xa, xa), axy, mul2(f2(xab, xab), bxy));
+                            const float2 gbxy = fma2(f2(xab, xab), axy, mul2(f2(xb, xb), bxy));
+                            const float2 gz = fma2(f2(xa, xab), f2(a.z, a.z), mul2(f2(xab, xb), f2(b.z, b.z)));
                             // narrow kind: low words always, the high words only when a lane
                             // of the warp has one (a contribution of at least 2^-(FX_HB+1)
                             // eV/A); the wide kind's larger contributions seldom skip them
