@@ -415,12 +415,15 @@ __device__ __forceinline__ unsigned live_mask(int A, int B, int l, int M, const 
                 if (live_pair(a, ha, b, hk(k, b))) mask |= 1u << s;
             }
         } else {
+            // every lane walks the partners in the same order (broadcast loads at
+            // fixed addresses), bit t <-> partner t; rotated to bit s <-> (l + s) mod 32
+            unsigned mk = 0u;
 #pragma unroll
-            for (int s = 0; s < 32; ++s) {
-                const int k = (l + s) & 31;
-                const float4 b = blk[k];
-                if (live_pair(a, ha, b, hk(k, b))) mask |= 1u << s;
+            for (int t = 0; t < 32; ++t) {
+                const float4 b = blk[t];
+                if (live_pair(a, ha, b, hk(t, b))) mk |= 1u << t;
             }
+            mask = __funnelshift_r(mk, mk, l);
         }
         return mask & v;
     }
