@@ -57,8 +57,8 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # profiles/k_force_k_sf_water_110k.md (a 2M-atom launch moves the same bytes per
 # atom: list rows, positions, pair-queue and staged-neighbour records all scale with atoms).  Valid only for the kernel sources with this hash;
 # otherwise traffic is null.
-TRAFFIC = {"force": (870.938368e6 + 6.496256e6) / 110592, "descriptors": (90.184704e6 + 783.948544e6) / 110592}
-TRAFFIC_SRC_SHA = "92947e016208"
+TRAFFIC = {"force": (916.749824e6 + 7.44192e6) / 110592, "descriptors": (90.37312e6 + 783.91936e6) / 110592}
+TRAFFIC_SRC_SHA = "eb8bf16faca7"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
