@@ -112,8 +112,8 @@ typedef struct nnp_handle nnp_handle;
  * (host memory may be freed afterwards).  *out is NULL on failure.  Parameter
  * validation happens before any CUDA call.  Scratch grows on demand later.
  * Force assembly: by default each atom adds its pair contributions -g_ij into
- * the forces of its neighbours as 64-bit fixed-point integers (units 2^-23
- * eV/A for narrow angular functions, 2^-27 eV/A for wide ones) with global integer atomics; integer sums do not depend on the order of
+ * the forces of its neighbours as 64-bit fixed-point integers (units 2^-27
+ * eV/A) with global integer atomics; integer sums do not depend on the order of
  * the atomics, so forces are reproducible bit for bit, and each component is
  * rounded to float once.  Environment variables read here select the other
  * forms: NNP_FORCE_GATHER=1 writes g_ij per neighbour-list slot and gathers the

@@ -142,7 +142,7 @@ __device__ __forceinline__ void cutoff_fn_fast(float r, float hpi_rc, float& fc,
 // narrow kind's coarse high word is zero for contributions below 1/8 eV/A, so a
 // warp can skip its atomics; the wide kind keeps the finer low word.
 #define FX_HB_NARROW 2
-#define FX_LB_NARROW 23
+#define FX_LB_NARROW 27
 #define FX_HB_WIDE 6
 #define FX_LB_WIDE 27
 

@@ -159,7 +159,12 @@ __host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool
 template <bool N>
 struct FxU {
     static constexpr int HB = N ? FX_HB_NARROW : FX_HB_WIDE, LB = N ? FX_LB_NARROW : FX_LB_WIDE;
-    static_assert(LB - HB <= 21 && HB >= 0 && HB <= 6, "fixed-point word ranges");
+    // CARRY: lo is rounded with a conversion instruction (|r 2^LB| up to 2^(LB-HB-1)),
+    // and the force kernel carries the low words into the high words after every
+    // 32 x 32 block pair, so a low word takes at most 32 adds between carries
+    static constexpr bool CARRY = LB - HB > 21;
+    static_assert((!CARRY && LB - HB <= 21) || (CARRY && LB - HB <= 25), "fixed-point word ranges");
+    static_assert(HB >= 0 && HB <= 6, "fixed-point word ranges");
 };
 // The roundings to integers use the 1.5 * 2^23 shift: for |x| < 2^22, x + 1.5 * 2^23
 // rounds x to the nearest integer, which then sits in the low mantissa bits
@@ -176,7 +181,7 @@ __device__ __forceinline__ void fx_split(float v, int& hi, int& lo)
     const float th = fmaf(v, FX_HS, S);
     hi = __float_as_int(th) - __float_as_int(S);
     const float r = fmaf(th - S, -1.0f / FX_HS, v);
-    lo = __float_as_int(fmaf(r, FX_LS, S)) - __float_as_int(S);
+    lo = FxU<N>::CARRY ? __float2int_rn(r * FX_LS) : __float_as_int(fmaf(r, FX_LS, S)) - __float_as_int(S);
 }
 // Two contributions at once (packed f32x2 arithmetic, the same roundings).
 template <bool N>
@@ -187,18 +192,40 @@ __device__ __forceinline__ void fx_split2(float2 v, int& hx, int& lx, int& hy, i
     hx = __float_as_int(th.x) - __float_as_int(S);
     hy = __float_as_int(th.y) - __float_as_int(S);
     const float2 r = fma2(add2(th, f2(-S, -S)), f2(-1.0f / FX_HS, -1.0f / FX_HS), v);
-    const float2 tl = fma2(r, f2(FX_LS, FX_LS), f2(S, S));
-    lx = __float_as_int(tl.x) - __float_as_int(S);
-    ly = __float_as_int(tl.y) - __float_as_int(S);
+    if (FxU<N>::CARRY) {
+        const float2 x = mul2(r, f2(FX_LS, FX_LS));
+        lx = __float2int_rn(x.x);
+        ly = __float2int_rn(x.y);
+    } else {
+        const float2 tl = fma2(r, f2(FX_LS, FX_LS), f2(S, S));
+        lx = __float_as_int(tl.x) - __float_as_int(S);
+        ly = __float_as_int(tl.y) - __float_as_int(S);
+    }
 }
 // lo alone, for |v| < 2^-(HB+1) (hi = 0): the same bits as fx_split2's lo
 template <bool N>
 __device__ __forceinline__ void fx_lo2(float2 v, int& lx, int& ly)
 {
     const float S = 12582912.0f;
-    const float2 tl = fma2(v, f2(FX_LS, FX_LS), f2(S, S));
-    lx = __float_as_int(tl.x) - __float_as_int(S);
-    ly = __float_as_int(tl.y) - __float_as_int(S);
+    if (FxU<N>::CARRY) {
+        const float2 x = mul2(v, f2(FX_LS, FX_LS));
+        lx = __float2int_rn(x.x);
+        ly = __float2int_rn(x.y);
+    } else {
+        const float2 tl = fma2(v, f2(FX_LS, FX_LS), f2(S, S));
+        lx = __float_as_int(tl.x) - __float_as_int(S);
+        ly = __float_as_int(tl.y) - __float_as_int(S);
+    }
+}
+// Moves the low word's multiples of 2^(LB-HB) into the high word (same value;
+// the low word is left in [0, 2^(LB-HB))).  One lane per word.
+template <bool N>
+__device__ __forceinline__ void fx_carry(const WarpSmem& w, int idx)
+{
+    const int lo = w.sgl[idx];
+    const int c = lo >> (FxU<N>::LB - FxU<N>::HB);
+    w.sgl[idx] = lo - (c << (FxU<N>::LB - FxU<N>::HB));
+    w.sgh[idx] += c;
 }
 template <bool N>
 __device__ __forceinline__ void fx_add2(const WarpSmem& w, int ix, int iy, float2 v)
@@ -1240,6 +1267,16 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                         }
                     }
                     __syncwarp();
+                    if (FxU<NARROW>::CARRY && nb > 3) {
+                        // the slots of blocks A and B took at most 32 adds each: carry.
+                        // With at most 3 blocks a slot meets at most 3 block pairs: 96 adds
+                        // of |lo| <= 2^24 and the radial value stay below 2^31 uncarried.
+                        for (int t = lane; t < 96; t += 32) {
+                            if (96 * A + t < 3 * M) fx_carry<NARROW>(w, 96 * A + t);
+                            if (B != A && 96 * B + t < 3 * M) fx_carry<NARROW>(w, 96 * B + t);
+                        }
+                        __syncwarp();
+                    }
                 }
             }
         }
