@@ -57,8 +57,8 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # profiles/k_force_k_sf_water_110k.md (a 2M-atom launch moves the same bytes per
 # atom: list rows, positions, pair-queue and staged-neighbour records all scale with atoms).  Valid only for the kernel sources with this hash;
 # otherwise traffic is null.
-TRAFFIC = {"force": (916.749824e6 + 7.44192e6) / 110592, "descriptors": (90.37312e6 + 783.91936e6) / 110592}
-TRAFFIC_SRC_SHA = "eb8bf16faca7"
+TRAFFIC = {"force": (912.90624e6 + 7.062272e6) / 110592, "descriptors": (90.52672e6 + 784.187648e6) / 110592}
+TRAFFIC_SRC_SHA = "a493d9392471"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
