@@ -58,7 +58,7 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # atom: list rows, positions, pair-queue and staged-neighbour records all scale with atoms).  Valid only for the kernel sources with this hash;
 # otherwise traffic is null.
 TRAFFIC = {"force": (912.90624e6 + 7.062272e6) / 110592, "descriptors": (90.52672e6 + 784.187648e6) / 110592}
-TRAFFIC_SRC_SHA = "a493d9392471"
+TRAFFIC_SRC_SHA = "e349efb0b720"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 

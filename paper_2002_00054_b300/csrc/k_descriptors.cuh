@@ -151,10 +151,13 @@ __host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool
 // eV/A, is split exactly into hi = round(v 2^H) and lo = round((v - hi 2^-H) 2^L)
 // (H, L: FxU<NARROW>; the remainder is a float difference of nearby values, so
 // it is exact), and each part is added into its own int32 word with a native
-// shared-memory integer atomic.  Per add |hi| < 2^21 and |lo| <= 2^(L-H-1) <= 2^20,
-// so the up to 1024 adds a neighbour receives (list stride <= 1024) cannot
-// overflow either word; the only rounding is 2^-(L+1) eV/A per add, and the sums
-// do not depend on the order of the adds.  hi is zero for |v| < 2^-(H+1).
+// shared-memory integer atomic.  Per add |hi| < 2^21 and |lo| <= 2^(L-H-1).  Without
+// CARRY (L - H <= 21) the up to 1024 adds a neighbour receives (list stride <= 1024)
+// cannot overflow either word; with CARRY the force kernel bounds the adds between
+// carries (see FxU).  The only rounding is 2^-(L+1) eV/A per add, and the sums do
+// not depend on the order of the adds.  hi is zero for |v| < 2^-(H+1).  L stays at
+// 27: with a coarser low unit the contributions below half a unit, which share a
+// radial sign, round away and bias the virial.
 #define FX_LIMIT 32000.0f
 template <bool N>
 struct FxU {
@@ -169,8 +172,8 @@ struct FxU {
 // The roundings to integers use the 1.5 * 2^23 shift: for |x| < 2^22, x + 1.5 * 2^23
 // rounds x to the nearest integer, which then sits in the low mantissa bits
 // (integer = bits(x + S) - bits(S)), and (x + S) - S is that integer as a float;
-// no float/int conversion instructions.  |v 2^H| < 2^22 and |r 2^L| <= 2^20 hold
-// for |v| < FX_LIMIT.
+// no float/int conversion instructions.  |v 2^H| < 2^22 holds for |v| < FX_LIMIT,
+// and |r 2^L| <= 2^20 without CARRY; with CARRY lo takes a conversion instead.
 // (inside the helpers below, which are templated on the kind N)
 #define FX_HS ((float)(1 << FxU<N>::HB))
 #define FX_LS ((float)(1 << FxU<N>::LB))
