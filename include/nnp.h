@@ -120,7 +120,11 @@ typedef struct nnp_handle nnp_handle;
  * forces per atom through a reverse index (fixed order, float sums; the reverse
  * index and slot buffer take 20 bytes per list slot), NNP_FORCE_SCATTER=1 adds
  * floats with global atomics (the scatter form of the paper's CabanaMD code;
- * sums in the order the atomics land). */
+ * sums in the order the atomics land).  With the default form and at most two
+ * eta the descriptor pass also writes each atom's staged neighbours (48 bytes
+ * per neighbour inside r_c) for the force pass to read; NNP_STAGE_REUSE=0 makes
+ * the force pass stage them again instead (the same forces, bit for bit).
+ * NNP_STEP_GRAPH=0 is described at nnp_step. */
 NNP_API int nnp_create(const nnp_params* params, int device, nnp_handle** out);
 
 /* Frees the handle and its device memory (waits for its pending work).  NULL is a no-op. */
