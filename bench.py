@@ -53,10 +53,10 @@ WORKLOADS = {
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2032e6 / 1e12
 MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # DRAM bytes (read + write) per atom-evaluation of each kernel group, from the
-# ncu --set full capture on the 110,592-atom water box summarised in
-# profiles/k_force_k_sf_water_110k.md (a 2M-atom launch moves the same bytes per
-# atom: list rows, positions, pair-queue and staged-neighbour records all scale with atoms).  Valid only for the kernel sources with this hash;
-# otherwise traffic is null.
+# ncu --set full capture on the 110,592-atom water box summarised under
+# profiles/ (a 2M-atom launch moves the same bytes per atom: list rows,
+# positions, pair-queue and staged-neighbour records all scale with atoms).
+# Valid only for the kernel sources with this hash; otherwise traffic is null.
 TRAFFIC = {"force": (912.90624e6 + 7.062272e6) / 110592, "descriptors": (90.52672e6 + 784.187648e6) / 110592}
 TRAFFIC_SRC_SHA = "e349efb0b720"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")

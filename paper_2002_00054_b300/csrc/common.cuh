@@ -16,14 +16,8 @@
 #define WARP 32
 #define FULL 0xffffffffu
 
-// error word bits (flags[FLAG_ERR])
-#define ERR_NEIGH_OVERFLOW 1
-#define ERR_CELL_OVERFLOW 2
-#define ERR_NONFINITE 4
-#define ERR_CLOSE 8
-#define ERR_REV 16
-#define ERR_RC_OVERFLOW 32
-#define ERR_RANGE 64        // a force contribution non-finite or >= 1024 eV/A (fixed-point range)
+// error word bits (flags[FLAG_ERR]) and their status mapping
+#include "error_word.h"
 
 #define FLAG_ERR 0
 #define FLAG_REBUILD 1
@@ -47,9 +41,42 @@
 
 // exp(-eta x2) = 2^(k x2) with k = -eta log2(e) given as hi + lo floats, so the
 // argument carries no systematic rounding of the constant (|k x2| reaches ~20).
+// The hardware exp2 behind exp2f: ~1 ulp, and measured on B300 biased low by
+// 0.82 ulp on average over [-20, 0].  Used per triplet (narrow kind), where its
+// error enters one term among ~10^3.
 __device__ __forceinline__ float gauss2(float khi, float klo, float x2)
 {
     return exp2f(fmaf(khi, x2, klo * x2));
+}
+
+// 2^x to within ~0.5 ulp with no systematic bias, for the per-neighbour factors
+// exp(-eta r^2) f_c(r): every descriptor is a sum of them, and a bias common to
+// all terms survives the sum and the scaling G~ = (G - mu)/s, |mu/s| ~ 20 (a
+// 1-ulp bias of every term moved FCC per-atom energies by ~1e-5 relative).
+// Method: Cody-Waite style reduction x = n + f with n = rint(x), so f is exact
+// and |f| <= 1/2; 2^f = e^(f ln 2) by its Taylor series to degree 8 (truncation
+// below 2^-32 relative), Horner with FMA; then the exact scaling by 2^n.  The
+// coefficients are (ln 2)^k / k!.  Measured on B300 over [-20, 0]: bias
+// -0.002 ulp, rms 0.43 ulp, max 1.09 ulp against FP64 (exp2f: -0.82, 0.97, 2.4).
+__device__ __forceinline__ float exp2_acc(float x)
+{
+    x = fminf(fmaxf(x, -125.0f), 127.0f);
+    const float n = rintf(x);
+    const float f = x - n;
+    float p = 1.3215486790144305e-06f;
+    p = fmaf(p, f, 1.5252733804059838e-05f);
+    p = fmaf(p, f, 1.5403530393381606e-04f);
+    p = fmaf(p, f, 1.3333558146428441e-03f);
+    p = fmaf(p, f, 9.6181291076284772e-03f);
+    p = fmaf(p, f, 5.5504108664821576e-02f);
+    p = fmaf(p, f, 2.4022650695910071e-01f);
+    p = fmaf(p, f, 6.9314718055994531e-01f);
+    p = fmaf(p, f, 1.0f);
+    return p * __int_as_float(((int)n + 127) << 23);
+}
+__device__ __forceinline__ float gauss2_acc(float khi, float klo, float x2)
+{
+    return exp2_acc(fmaf(khi, x2, klo * x2));
 }
 
 // Per-element descriptor plan.  Angular functions of one element share one kind
@@ -86,6 +113,8 @@ struct Plan {
     int resolved;        // some angular class is restricted to an element pair
     float rc, rc2, hpi_rc;   // cutoff, cutoff^2, pi / (2 rc)
     float inv_2rc, inv_2rc_lo;   // 1 / (2 rc) as hi + lo floats
+    // cos(pi k / 64), sin(pi k / 64), k = 0..32, each as hi + lo floats (cospi_dd)
+    float4 cs64[33];
     float rcut2;             // (cutoff + skin)^2
     float half_skin2;        // (skin / 2)^2
     float acc_over_m[NNP_MAXE];  // (1 eV/(A amu) in A/fs^2) / mass
@@ -166,6 +195,113 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     s = a + b;
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
+}
+
+// Double-float ("hi + lo") helpers for the per-neighbour factors of the
+// descriptors.  A descriptor is a sum of these factors over tens of neighbours
+// and is then scaled as G~ = (G - mu)/s with |mu/s| up to ~20, so an error that
+// repeats in every term (a biased function, or the rounding of r entering the
+// steep cutoff near r_c) is amplified ~20x in G~; each factor is therefore
+// formed to about half an ulp before it is rounded to float once.
+
+// |d|^2 = h + l for a float vector d, exact up to terms of order 2^-48 |d|^2
+// (each square split by an FMA, the two sums by TwoSum).
+__device__ __forceinline__ void dd_norm2(float x, float y, float z, float& h, float& l)
+{
+    const float p1 = x * x, e1 = fmaf(x, x, -p1);
+    const float p2 = y * y, e2 = fmaf(y, y, -p2);
+    const float p3 = z * z, e3 = fmaf(z, z, -p3);
+    float s, t1, t2;
+    two_sum(p1, p2, s, t1);
+    two_sum(s, p3, h, t2);
+    l = (e1 + e2 + e3) + (t1 + t2);
+}
+
+// 2^(ah + al) for al a small correction of ah (|al| <= ~1e-6 |ah|), to within
+// ~0.5 ulp and without bias: as exp2_acc, with the reduced argument
+// f = (ah - n) + al (ah - n is exact).
+__device__ __forceinline__ float exp2_acc2(float ah, float al)
+{
+    ah = fminf(fmaxf(ah, -125.0f), 127.0f);
+    const float n = rintf(ah);
+    const float f = (ah - n) + al;
+    float p = 1.3215486790144305e-06f;
+    p = fmaf(p, f, 1.5252733804059838e-05f);
+    p = fmaf(p, f, 1.5403530393381606e-04f);
+    p = fmaf(p, f, 1.3333558146428441e-03f);
+    p = fmaf(p, f, 9.6181291076284772e-03f);
+    p = fmaf(p, f, 5.5504108664821576e-02f);
+    p = fmaf(p, f, 2.4022650695910071e-01f);
+    p = fmaf(p, f, 6.9314718055994531e-01f);
+    p = fmaf(p, f, 1.0f);
+    return p * __int_as_float(((int)n + 127) << 23);
+}
+
+// 2^(ah + al) as h + l to ~2^-27 relative: the same reduction and series, with
+// the leading terms 1 + f ln2 carried in double-float (ln 2 as hi + lo).
+__device__ __forceinline__ void exp2_dd(float ah, float al, float& h, float& l)
+{
+    ah = fminf(fmaxf(ah, -125.0f), 127.0f);
+    const float n = rintf(ah);
+    float f, fl;
+    two_sum(ah - n, al, f, fl);   // f + fl = (ah - n) + al exactly
+    // q2 = (2^f - 1 - f ln2) / f^2, a float series (its terms are below 0.13 f)
+    float q = 1.3215486790144305e-06f;
+    q = fmaf(q, f, 1.5252733804059838e-05f);
+    q = fmaf(q, f, 1.5403530393381606e-04f);
+    q = fmaf(q, f, 1.3333558146428441e-03f);
+    q = fmaf(q, f, 9.6181291076284772e-03f);
+    q = fmaf(q, f, 5.5504108664821576e-02f);
+    q = fmaf(q, f, 2.4022650695910071e-01f);
+    const float ln2h = 6.93147182464599609375e-01f, ln2l = -1.9046542999577e-09f;
+    const float th = f * ln2h;
+    const float tl = fmaf(f, ln2h, -th) + fmaf(f, ln2l, fmaf(fl, ln2h, (f * f) * q));
+    const float sh = 1.0f + th;
+    const float sl = ((1.0f - sh) + th) + tl;   // |th| < 1: Fast2Sum
+    // renormalise, so that h alone is 2^x to within an ulp (|sl| < 0.1 < sh)
+    const float rh = sh + sl;
+    const float rlo = sl - (rh - sh);
+    const float sc = __int_as_float(((int)n + 127) << 23);
+    h = rh * sc;
+    l = rlo * sc;
+}
+
+// cos(pi x) as h + l, x = xh + xl in [0, 1/2], to ~2^-28 absolute, and
+// sin(pi x) to ~1 ulp: table-driven angle addition (Tang's method) with the
+// table cos, sin(pi k / 64) held as hi + lo floats and the reduced angle
+// a = pi (x - k/64), |a| <= pi/128, expanded as cos a = 1 - a^2/2 + a^4/24,
+// sin a = a - a^3/6 (truncation below 1e-10).
+__device__ __forceinline__ void cospi_dd(float xh, float xl, const float4* __restrict__ tab, float& ch, float& cl,
+                                         float& sn)
+{
+    const float kf = rintf(xh * 64.0f);
+    const int k = min(max((int)kf, 0), 32);
+    const float4 t = tab[k];   // (cos hi, cos lo, sin hi, sin lo)
+    const float dd = (xh - (float)k * 0.015625f) + xl;   // xh - k/64 is exact
+    const float a = fmaf(dd, -8.742278e-08f, dd * 3.14159274101257324f);   // pi as hi + lo
+    const float a2 = a * a;
+    const float omc = a2 * fmaf(a2, -4.16666679e-02f, 0.5f);   // 1 - cos a
+    const float sna = a * fmaf(a2, -1.66666672e-01f, 1.0f);    // sin a
+    // cos(pi x) = C - (C (1 - cos a) + S sin a)
+    const float D = fmaf(t.x, omc, t.z * sna) - t.y;
+    float e;
+    two_sum(t.x, -D, ch, e);
+    cl = e;
+    sn = t.z + fmaf(t.x, sna, -t.z * omc);
+}
+
+// Cutoff f_c(r) = cos^2(pi r / (2 rc)) for r = rh + rl: hi + lo to ~2^-27
+// relative where f_c is not tiny, and its derivative dfc (float).
+__device__ __forceinline__ void cutoff_dd(float rh, float rl, float inv_2rc, float inv_2rc_lo, float hpi_rc,
+                                          const float4* __restrict__ tab, float& fh, float& fl, float& dfc)
+{
+    const float xh = rh * inv_2rc;
+    const float xl = fmaf(rh, inv_2rc, -xh) + fmaf(rh, inv_2rc_lo, rl * inv_2rc);
+    float ch, cl, sn;
+    cospi_dd(xh, xl, tab, ch, cl, sn);
+    fh = ch * ch;
+    fl = fmaf(ch, ch, -fh) + 2.0f * ch * cl;
+    dfc = -2.0f * hpi_rc * sn * ch;
 }
 
 // Reduce-scatter of 32 per-lane float accumulators over the warp with compensated

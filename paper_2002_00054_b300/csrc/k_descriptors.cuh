@@ -113,14 +113,14 @@ __device__ __forceinline__ bool over_capacity(int M, int C, int pass, int i, int
 
 // Per-warp shared-memory arrays (C = capacity inside the cutoff, S = list stride).
 struct WarpSmem {
-    float4* nd;     // (dx, dy, dz, h) (descriptor pass) or (dx, dy, dz, 1/r) (force pass)
-    float* ninv;    // 1 / r (descriptor pass)
-    float* nr;      // r (descriptor pass)
+    float4* nd;     // descriptor pass: narrow kind (dx, dy, dz, h), wide kind (u, g) with u the
+                    // unit vector d/r rounded to float and g = (1 - |u|^2)/2; force pass (dx, dy, dz, 1/r)
+    float* ninv;    // 1 / r (descriptor pass, narrow kind with more than 2 eta)
+    float4* nrad;   // (r^2 as hi, lo; f_c; element) (descriptor pass)
     float* nh;      // h = r^2 / 2 - rc^2 / 4 (force passes that rebuild the live masks)
     int* jidx;      // atom index of each staged neighbour (force pass over stored staging)
     float4* npf;    // P_q; force pass with <= 2 eta: (P_0, P_1, dP_0/dr, dP_1/dr)
     float4* ndp;    // dP_q / dr (force pass with > 2 eta)
-    float2* nfe;    // (f_c, element) (descriptor pass)
     unsigned char* nel;   // element of each staged neighbour (force pass, resolved angular)
     int* sgh;       // g accumulators, 3 per neighbour, fixed point: hi words (force)
     int* sgl;       //   and lo words
@@ -133,9 +133,10 @@ struct WarpSmem {
 };
 static_assert(NNP_MAXRAD * 20 <= PAIR_QUEUE * 2, "radial table must fit the queue space");
 
-__host__ __device__ inline size_t sf_warp_bytes(int C)
+// BIG: more than 2 eta (P_q fills its float4; 1/r in its own array)
+__host__ __device__ inline size_t sf_warp_bytes(int C, bool big)
 {
-    return (size_t)C * (16 + 8 + 16 + 8) + NNP_MAXG * 8 + PAIR_QUEUE * 2 + 16;   // + closest-pair slot
+    return (size_t)C * (16 + 16 + 16 + (big ? 4 : 0)) + NNP_MAXG * 8 + PAIR_QUEUE * 2 + 16;   // + closest-pair slot
 }
 // PACK: P_q and dP_q/dr share one float4 per neighbour (at most 2 eta).  A 4C-byte
 // array holds h (passes that rebuild the live masks) or the neighbours' atom
@@ -290,7 +291,7 @@ __device__ __forceinline__ void radial_g(const WarpSmem& w, const Plan& P, const
     auto rad = [&](int rr) {
         const float4 t = w.rtab[rr];
         const float x = r - t.z;
-        const float ex = gauss2(t.x, t.y, x * x);
+        const float ex = gauss2_acc(t.x, t.y, x * x);
         gr += w.rw[rr] * ex * fmaf(t.w * x, fc, dfc);
     };
     for (int rr = 0; rr < E.rad_nall; ++rr) rad(rr);
@@ -304,7 +305,11 @@ __device__ __forceinline__ void radial_g(const WarpSmem& w, const Plan& P, const
 
 // Stages the neighbours of atom i within the cutoff, compacted in list order.
 // Returns M.  FORCE: nd.w = 1/r, dP/dr, the radial part of g (into sg), slot map.
-// N: the force pass's fixed-point units (FxU<N>).
+// N: the force pass's fixed-point units (FxU<N>); in the descriptor pass, the
+// narrow angular kind (the wide kind stages unit vectors instead of d).
+// Both passes compute r, 1/r, f_c, f_c', P_q and dP_q/dr from the same
+// double-float intermediates (|d|^2, r, the cutoff's cos), so the staged values
+// the descriptor pass writes for the force pass are bitwise the force pass's own.
 template <int NETA, bool FORCE, bool N = false>
 __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box& bx, const NbView& nv,
                                                const float4* __restrict__ pos4, const Plan& P, const ElemPlan& E,
@@ -352,29 +357,47 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
         if (keep && at < C) {
             if (r2 < 1e-8f) atomicOr(&flags[FLAG_ERR], ERR_CLOSE);
             if (!FORCE) r2min = fminf(r2min, r2);
-            const float r = sqrtf(r2);
+            // r^2 = r2h + r2l (exact to 2^-48), r = r + rl, the cutoff as fch + fcl
+            float r2h, r2l;
+            dd_norm2(dx, dy, dz, r2h, r2l);
+            const float r = sqrtf(r2h);
             const float ir = 1.0f / r;
-            float fc, dfc;
-            cutoff_fn(r, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, fc, dfc);
+            const float rl = (fmaf(-r, r, r2h) + r2l) * (0.5f * ir);
+            float fch, fcl, dfc;
+            cutoff_dd(r, rl, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, P.cs64, fch, fcl, dfc);
+            const float fc = fch + fcl;
+            // P_q = exp(-eta_q r^2) f_c: both factors as hi + lo, one final rounding
             float pq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int q = 0; q < NETA; ++q) {
-                const float ex = gauss2(khi[q], klo[q], r2);
-                pq[q] = ex * fc;
-                dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
+                const float ah = khi[q] * r2h;
+                const float al = fmaf(khi[q], r2h, -ah) + fmaf(klo[q], r2h, khi[q] * r2l);
+                float eh, el;
+                exp2_dd(ah, al, eh, el);
+                const float ph = eh * fch;
+                pq[q] = ph + (fmaf(eh, fch, -ph) + fmaf(eh, fcl, el * fch));
+                dq[q] = eh * (dfc - 2.0f * etav[q] * r * fc);
             }
             const float hh = live_h(r2, P.rc2);
             if (!FORCE) {
-                // at most 2 eta: 1/r and r ride in the free half of the P record
+                // at most 2 eta: 1/r rides in the free half of the P record
                 if (NETA <= 2) {
-                    w.npf[at] = make_float4(pq[0], pq[1], ir, r);
+                    w.npf[at] = make_float4(pq[0], pq[1], ir, 0.f);
                 } else {
                     w.npf[at] = make_float4(pq[0], pq[1], pq[2], pq[3]);
                     w.ninv[at] = ir;
-                    w.nr[at] = r;
                 }
-                w.nd[at] = make_float4(dx, dy, dz, hh);
-                w.nfe[at] = make_float2(fc, __int_as_float(ej));
+                if (N) {
+                    w.nd[at] = make_float4(dx, dy, dz, hh);
+                } else {
+                    // unit vector and its norm defect g = (1 - |u|^2)/2, exact
+                    const float irl = ir * fmaf(-rl, ir, fmaf(-r, ir, 1.0f));
+                    const float ux = fmaf(dx, irl, dx * ir), uy = fmaf(dy, irl, dy * ir), uz = fmaf(dz, irl, dz * ir);
+                    float sh, sl;
+                    dd_norm2(ux, uy, uz, sh, sl);
+                    w.nd[at] = make_float4(ux, uy, uz, 0.5f * ((1.0f - sh) - sl));
+                }
+                w.nrad[at] = make_float4(r2h, r2l, fc, __int_as_float(ej));
             } else {
                 w.nd[at] = make_float4(dx, dy, dz, ir);
                 if (w.nh) w.nh[at] = hh;
@@ -534,15 +557,15 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     const Plan& P = *plan_g;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int wpb = blockDim.x >> 5;
-    unsigned char* base = smem + sf_warp_bytes(C) * wib;
+    constexpr bool BIG = NETA > 2;
+    unsigned char* base = smem + sf_warp_bytes(C, BIG) * wib;
     WarpSmem w;
     w.nd = reinterpret_cast<float4*>(base);
     w.npf = w.nd + C;
-    double* sG = reinterpret_cast<double*>(w.npf + C);
+    w.nrad = w.npf + C;
+    double* sG = reinterpret_cast<double*>(w.nrad + C);
     w.ninv = reinterpret_cast<float*>(sG + NNP_MAXG);
-    w.nr = w.ninv + C;
-    w.nfe = reinterpret_cast<float2*>(w.nr + C);
-    w.queue = reinterpret_cast<unsigned short*>(w.nfe + C);
+    w.queue = reinterpret_cast<unsigned short*>(w.ninv + (BIG ? C : 0));
     w.nh = nullptr;
     w.jidx = nullptr;
     w.ndp = nullptr;
@@ -558,7 +581,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     unsigned long long cnt = 0, c_spill = 0;
     unsigned c_trip = 0;
     // per warp: closest staged neighbour (r^2) so far (last 16 bytes of the warp's area)
-    float* s_r2min = reinterpret_cast<float*>(base + sf_warp_bytes(C) - 16);
+    float* s_r2min = reinterpret_cast<float*>(base + sf_warp_bytes(C, BIG) - 16);
     if (lane == 0) *s_r2min = INFINITY;
     // this warp's chunk [qcur, qend) of the queue pool, in units of 8 entries
     // (main pass, when forces follow)
@@ -581,7 +604,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         int n_list;
         unsigned sig;
         float r2_atom = INFINITY;
-        const int M = stage_neighbors<NETA, false>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, nullptr, lane,
+        const int M = stage_neighbors<NETA, false, NARROW>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, nullptr, lane,
                                                    flags, n_list, sig, r2_atom, pass == 0 ? stg : nullptr, stg_plane);
         // closest staged neighbour: kept per warp in shared memory, not in a register
 #pragma unroll
@@ -593,7 +616,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         }
         // radial: lane <-> descriptor (two neighbour halves when n_rad <= 16), loop over
         // neighbours with broadcast reads; Kahan-compensated sums (they feed
-        // G~ = (G - mu)/s with |mu/s| up to ~20)
+        // G~ = (G - mu)/s with |mu/s| up to ~20).  The Gaussian's argument is
+        // formed in double-float from r^2 = r2h + r2l (from (r - r_s)^2 for r_s != 0)
         {
             const int halves = (E.n_rad <= 16) ? 2 : 1;
             const int per = 32 / halves;
@@ -606,11 +630,21 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 const int el = act ? E.rad_elem[rr] : -2;
                 float sum = 0.f, comp = 0.f;
                 for (int m = hf; m < M; m += halves) {
-                    const float r = (NETA <= 2) ? w.npf[m].w : w.nr[m];
-                    const float2 fe = w.nfe[m];
-                    if (el == -1 || el == __float_as_int(fe.y)) {
-                        const float x = r - rs;
-                        const float y = gauss2(kh, kl, x * x) * fe.x - comp;
+                    const float4 nr = w.nrad[m];
+                    if (el == -1 || el == __float_as_int(nr.w)) {
+                        float xh = nr.x, xl = nr.y;
+                        if (rs != 0.f) {
+                            const float rh = sqrtf(nr.x);
+                            const float rlo = (fmaf(-rh, rh, nr.x) + nr.y) * (0.5f / rh);
+                            float dh, dl;
+                            two_sum(rh, -rs, dh, dl);
+                            dl += rlo;
+                            xh = dh * dh;
+                            xl = fmaf(dh, dh, -xh) + 2.0f * dh * dl;
+                        }
+                        const float ah = kh * xh;
+                        const float al = fmaf(kh, xh, -ah) + fmaf(kl, xh, kh * xl);
+                        const float y = exp2_acc2(ah, al) * nr.z - comp;
                         const float t = sum + y;
                         comp = (t - sum) - y;
                         sum = t;
@@ -678,13 +712,13 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             for (int A = 0; A < nb; ++A) {
                 const int jl = 32 * A + lane;
                 const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
-                const int ej = (RES && jl < M) ? __float_as_int(w.nfe[jl].y) : -1;
+                const int ej = (RES && jl < M) ? __float_as_int(w.nrad[jl].w) : -1;
                 for (int B = A; B < nb; ++B, ++bp) {
                     unsigned mask = live_mask<NARROW, 0>(A, B, lane, M, al, al.w, w.nd, nullptr);
                     if (cls == 0) c_trip += __popc(mask);
                     if (RES && ce1 >= 0) {
                         const int kl = 32 * B + lane;
-                        mask &= class_mask(ej, kl < M ? __float_as_int(w.nfe[kl].y) : -1, ce1, ce2, lane);
+                        mask &= class_mask(ej, kl < M ? __float_as_int(w.nrad[kl].w) : -1, ce1, ce2, lane);
                     }
                     const int total = enqueue_block(mask, lane, w.queue);
                     if (rec) {
@@ -705,8 +739,6 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                             const float4 pa4 = w.npf[j], pb4 = w.npf[k];
                             const float2 PA[2] = {f2(pa4.x, pa4.y), f2(pa4.z, pa4.w)};
                             const float2 PB[2] = {f2(pb4.x, pb4.y), f2(pb4.z, pb4.w)};
-                            const float c = (a.x * b.x + a.y * b.y + a.z * b.z) *
-                                            ((NETA <= 2) ? pa4.z * pb4.z : w.ninv[j] * w.ninv[k]);
                             float fcd = 1.f, rd2 = 0.f;
                             if (NARROW) {
                                 const float ex = b.x - a.x, ey = b.y - a.y, ez = b.z - a.z;
@@ -717,9 +749,47 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                             // PP[k] = (b_+^(2^k), b_-^(2^k)), b_(+/-) = 1 +/- c, one packed chain while
                             // both lambdas go on; pt: the one that goes on beyond KLO
                             float2 PP[KLO + 1];
-                            PP[0] = fma2(f2(c, c), f2(1.f, -1.f), f2(1.f, 1.f));
+                            if (NARROW) {
+                                const float c = (a.x * b.x + a.y * b.y + a.z * b.z) *
+                                                ((NETA <= 2) ? pa4.z * pb4.z : w.ninv[j] * w.ninv[k]);
+                                PP[0] = fma2(f2(c, c), f2(1.f, -1.f), f2(1.f, 1.f));
 #pragma unroll
-                            for (int kk = 1; kk <= KLO; ++kk) PP[kk] = mul2(PP[kk - 1], PP[kk - 1]);
+                                for (int kk = 1; kk <= KLO; ++kk) PP[kk] = mul2(PP[kk - 1], PP[kk - 1]);
+                            } else {
+                                // wide kind, accurate b: with unit vectors, 1 - c = |u_j - u_k|^2 / 2 and
+                                // 1 + c = |u_j + u_k|^2 / 2 (times 1 + g_j + g_k for the norm defects),
+                                // each to about an ulp relative, without forming c.  The smaller of
+                                // the two is b for one lambda as it stands; the larger is 2 - the
+                                // smaller (exact subtraction; bl = its rounding, exact), which is
+                                // accurate where cos -> +-1 and b -> 2.  A power b^(2^k) amplifies b's
+                                // relative error 2^k times: the top power (zeta up to 16) gets the
+                                // first-order term 2^k bl b^(2^k - 1).
+                                const float2 wx = fma2(f2(b.x, b.x), f2(-1.f, 1.f), f2(a.x, a.x));
+                                const float2 wy = fma2(f2(b.y, b.y), f2(-1.f, 1.f), f2(a.y, a.y));
+                                const float2 wz = fma2(f2(b.z, b.z), f2(-1.f, 1.f), f2(a.z, a.z));
+                                float2 n2 = mul2(wx, wx);
+                                n2 = fma2(wy, wy, n2);
+                                n2 = fma2(wz, wz, n2);
+                                const float gg = a.w + b.w;
+                                const float2 hf = mul2(n2, f2(0.5f, 0.5f));
+                                const float2 sm = fma2(hf, f2(gg, gg), hf);              // (1 - c, 1 + c)
+                                const bool cpos = sm.x < sm.y;                           // c > 0
+                                const float small = cpos ? sm.x : sm.y;
+                                const float big = 2.0f - small;
+                                const float bigl = (2.0f - big) - small;
+                                PP[0] = cpos ? f2(big, small) : f2(small, big);         // (1 + c, 1 - c)
+                                const float2 bl = cpos ? f2(bigl, 0.f) : f2(0.f, bigl);
+                                float2 T = PP[0];
+#pragma unroll
+                                for (int kk = 1; kk <= KLO; ++kk) {
+                                    PP[kk] = mul2(PP[kk - 1], PP[kk - 1]);
+                                    if (kk < KLO) T = mul2(T, PP[kk]);
+                                }
+                                if (KLO >= 2) {
+                                    const float sc = (float)(1 << KLO);
+                                    PP[KLO] = fma2(T, mul2(bl, f2(sc, sc)), PP[KLO]);
+                                }
+                            }
                             float pt[KM - KLO + 1];
                             {
                                 float x = TX ? PP[KLO].x : PP[KLO].y;
@@ -870,8 +940,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     w.rtab = reinterpret_cast<float4*>(w.queue);
     w.rw = reinterpret_cast<float*>(w.rtab + NNP_MAXRAD);
     w.ninv = nullptr;
-    w.nr = nullptr;
-    w.nfe = nullptr;
+    w.nrad = nullptr;
 
     // virial sums of the warp's atoms (FP64, in shared memory: registers stay free
     // for the pair loop)

@@ -44,7 +44,7 @@ k_sf_flat(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
         for (int rr = 0; rr < E.n_rad; ++rr)
             if (E.rad_elem[rr] < 0 || E.rad_elem[rr] == ea) {
                 const float x = ra - E.rad_rs[rr];
-                g[E.rad_out[rr]] += gauss2(E.rad_khi[rr], E.rad_klo[rr], x * x) * fa;
+                g[E.rad_out[rr]] += gauss2_acc(E.rad_khi[rr], E.rad_klo[rr], x * x) * fa;
             }
         if (E.n_eta == 0) continue;
         const float ha = live_h(ra2, P.rc2);

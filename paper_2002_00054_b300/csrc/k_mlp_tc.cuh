@@ -23,7 +23,6 @@
 
 #include "common.cuh"
 
-#define ERR_TIMEOUT 64
 #define TC_TILE 128
 #define TC_TMEM_COLS 128
 

@@ -215,6 +215,12 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
     P.rc2 = (float)(p->cutoff * p->cutoff);
     P.hpi_rc = (float)(M_PI / (2.0 * p->cutoff));
     split(0.5 / p->cutoff, P.inv_2rc, P.inv_2rc_lo);
+    for (int k = 0; k <= 32; ++k) {   // table of the cutoff's cos(pi x) (cospi_dd)
+        float ch, cl, sh, sl;
+        split(std::cos(M_PI * k / 64.0), ch, cl);
+        split(std::sin(M_PI * k / 64.0), sh, sl);
+        P.cs64[k] = make_float4(ch, cl, sh, sl);
+    }
     const double rcut = p->cutoff + p->skin;
     P.rcut2 = (float)(rcut * rcut);
     P.half_skin2 = (float)(0.25 * p->skin * p->skin);
@@ -465,7 +471,7 @@ static double fq_unit(const Plan& P)
     return std::ldexp(1.0, -(nar ? FX_LB_NARROW : FX_LB_WIDE));
 }
 
-static size_t sf_smem_per_warp(int cap) { return sf_warp_bytes(cap); }
+static size_t sf_smem_per_warp(const Plan& P, int cap) { return sf_warp_bytes(cap, P.n_eta_max > 2); }
 static size_t force_smem_per_warp(const Plan& P, int cap, int stride)
 {
     // the kernels' NETA is n_eta_max; resolved models keep each neighbour's element
@@ -482,7 +488,7 @@ static int set_capacity(nnp_handle* h, int C)
     ForceKernel kf;
     TangentKernel kt;
     pick_kernels(h->plan, ksf, kf, kt);
-    const size_t ps = sf_smem_per_warp(C), pf = force_smem_per_warp(h->plan, C, h->stride), pt = tangent_warp_bytes(C);
+    const size_t ps = sf_smem_per_warp(h->plan, C), pf = force_smem_per_warp(h->plan, C, h->stride), pt = tangent_warp_bytes(C);
     const size_t ms = (size_t)h->max_smem;
     if (ps > ms || pf > ms) return set_err(h, NNP_EINVAL, "shared-memory capacity %d does not fit one block", C);
     h->cap_rc = C;
@@ -716,17 +722,9 @@ static int read_status(nnp_handle* h, cudaStream_t st)
         // errors leave the neighbour list and the step state unknown
         h->list_valid = false;
         h->step_valid = false;
-        if (f & ERR_NEIGH_OVERFLOW)
-            return set_err(h, NNP_ENEIGH_OVERFLOW,
-                           "an atom has more than max_neighbors = %d neighbours within cutoff + skin", h->stride);
-        if (f & ERR_CELL_OVERFLOW) return set_err(h, NNP_ENEIGH_OVERFLOW, "a cell holds more than %d atoms", CELL_CAP);
-        if (f & ERR_RC_OVERFLOW) return set_err(h, NNP_ECUDA, "internal error: wide-capacity pass overflowed");
-        if (f & ERR_RANGE)
-            return set_err(h, NNP_ENONFINITE, "a force contribution is non-finite or exceeds %g eV/A", (double)FX_LIMIT);
-        if (f & ERR_CLOSE) return set_err(h, NNP_ENONFINITE, "two atoms are closer than 1e-4 A");
-        if (f & ERR_NONFINITE) return set_err(h, NNP_ENONFINITE, "non-finite position/energy/force or invalid element type");
-        if (f & ERR_REV) return set_err(h, NNP_ECUDA, "internal error: neighbour list not symmetric");
-        return set_err(h, NNP_ECUDA, "device error word 0x%x", f);
+        char msg[256];
+        const int status = error_word_status(f, h->stride, CELL_CAP, (double)FX_LIMIT, msg, sizeof msg);
+        return set_err(h, status, "%s", msg);
     }
     retune_capacity(h);
     return NNP_OK;
@@ -1169,7 +1167,7 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     pick_kernels(P, ksf, kf, kt);
     {
         // wide-capacity pass: capacity = list stride, as many warps as fit (<= 4)
-        const size_t ps = sf_smem_per_warp(h->stride), pf = force_smem_per_warp(P, h->stride, h->stride);
+        const size_t ps = sf_smem_per_warp(P, h->stride), pf = force_smem_per_warp(P, h->stride, h->stride);
         if (ps > (size_t)max_smem || pf > (size_t)max_smem) {
             set_err(h, NNP_EINVAL, "max_neighbors = %d needs more shared memory than one block has", h->stride);
             return fail(NNP_EINVAL);
@@ -1693,14 +1691,12 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     const Plan& P = h->plan;
     const int S = h->stride, T = 256;
     const int gf = std::min(blocks_for(std::max(n, 1), h->wpb_force), h->grid_force);
-    const int nvp_main = gf * h->wpb_force;
-    const int nvp = nvp_main + h->grid_sp * h->wpb_force_sp;
     const int gred = std::min(blocks_for(std::max(n, 1), T), 4 * h->num_sms);
 
     // scratch layout (the same carving sizes and places it)
     auto layout = [&](Carve& c, int** flags, unsigned long long** counters, float4** sys_box, float4** off, float4** ref,
                       float4** pos4, uint32_t** nbr, int** ncount, int** rev, float** G, float** dEdG, float** Ei,
-                      float4** gbuf, float4** Fown, double** vpart, double** epart, float** F, int** spill) {
+                      float4** gbuf, float4** Fown, double** epart, float** F, int** spill) {
         *flags = c.take<int>(4);
         *counters = c.take<unsigned long long>(CNT_N);
         *sys_box = c.take<float4>(1);
@@ -1715,7 +1711,6 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
         *Ei = c.take<float>(n);
         *gbuf = c.take<float4>((size_t)n * S);
         *Fown = c.take<float4>(n);
-        *vpart = c.take<double>((size_t)nvp * 9);
         *epart = c.take<double>(gred);
         *F = c.take<float>((size_t)n * 3);
         *spill = c.take<int>((size_t)n + 1);
@@ -1726,11 +1721,11 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     uint32_t* nbr;
     int *ncount, *rev, *spill;
     float *G, *dEdG, *Ei, *Fs;
-    double *vpart, *epart;
+    double* epart;
     {
         Carve dry{nullptr};
         layout(dry, &flags, &counters, &sys_box, &off, &ref, &pos4, &nbr, &ncount, &rev, &G, &dEdG, &Ei, &gbuf, &Fown,
-               &vpart, &epart, &Fs, &spill);
+               &epart, &Fs, &spill);
         if (dry.off > NNP_STATIC_SCRATCH_BYTES)
             return static_fail(eb, el, NNP_EINVAL,
                                "needs %zu bytes of scratch for n_atoms = %d and max_neighbors = %d; the static "
@@ -1754,8 +1749,8 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
         base = g_static_addr[h->device];
     }
     Carve c{static_cast<unsigned char*>(base)};
-    layout(c, &flags, &counters, &sys_box, &off, &ref, &pos4, &nbr, &ncount, &rev, &G, &dEdG, &Ei, &gbuf, &Fown, &vpart,
-           &epart, &Fs, &spill);
+    layout(c, &flags, &counters, &sys_box, &off, &ref, &pos4, &nbr, &ncount, &rev, &G, &dEdG, &Ei, &gbuf, &Fown, &epart,
+           &Fs, &spill);
 
 #define CKS(call)                                                                                      \
     do {                                                                                              \
@@ -1793,30 +1788,25 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
                                                              spill, 1, nullptr, nullptr, 0ull, nullptr, 0);
     const int gmlp = std::min(blocks_for(n, 128), h->grid_mlp);
     h->kmlp<<<gmlp, 128, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
-    kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, vpart,
+    // no virial output: the force passes write no virial partials
+    kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, nullptr,
                                                      flags, spill, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0ull);
     kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, dEdG, gbuf, Fown,
-                                                                   vpart + (size_t)nvp_main * 9, flags, spill, 1, nullptr, nullptr, nullptr,
+                                                                   nullptr, flags, spill, 1, nullptr, nullptr, nullptr,
                                                                    nullptr, nullptr, 0, 0ull);
     k_gather<<<rows_grid, 256, 0, st>>>(n, nv, rev, gbuf, Fown, forces ? forces : Fs, flags);
     k_sum_partial<<<gred, T, 0, st>>>(n, Ei, epart, flags);
-    k_finalize<<<1, 256, 0, st>>>(gred, epart, energy, nvp, vpart, nullptr);
+    k_finalize<<<1, 256, 0, st>>>(gred, epart, energy, 0, nullptr, nullptr);
     if (atom_energy) CKS(cudaMemcpyAsync(atom_energy, Ei, sizeof(float) * n, cudaMemcpyDeviceToDevice, st));
     CKS(cudaGetLastError());
     int hf = 0;
     CKS(cudaMemcpyAsync(&hf, flags, sizeof(int), cudaMemcpyDeviceToHost, st));
     CKS(cudaStreamSynchronize(st));
 #undef CKS
-    if (hf & ERR_NEIGH_OVERFLOW)
-        return static_fail(eb, el, NNP_ENEIGH_OVERFLOW,
-                           "an atom has more than max_neighbors = %d neighbours within cutoff + skin", S);
-    if (hf & ERR_RC_OVERFLOW) return static_fail(eb, el, NNP_ECUDA, "internal error: wide-capacity pass overflowed");
-    if (hf & ERR_RANGE)
-        return static_fail(eb, el, NNP_ENONFINITE, "a force contribution is non-finite or exceeds %g eV/A",
-                           (double)FX_LIMIT);
-    if (hf & ERR_CLOSE) return static_fail(eb, el, NNP_ENONFINITE, "two atoms are closer than 1e-4 A");
-    if (hf & ERR_NONFINITE)
-        return static_fail(eb, el, NNP_ENONFINITE, "non-finite position/energy/force or invalid element type");
-    if (hf) return static_fail(eb, el, NNP_ECUDA, "device error word 0x%x", hf);
+    if (hf) {
+        char msg[256];
+        const int status = error_word_status(hf, S, CELL_CAP, (double)FX_LIMIT, msg, sizeof msg);
+        return static_fail(eb, el, status, "%s", msg);
+    }
     return NNP_OK;
 }

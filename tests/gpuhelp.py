@@ -5,19 +5,12 @@ import torch
 
 import oracle
 
-# FP32 path tolerances against the FP64 oracle:
+# FP32 path tolerances against the FP64 oracle, as stated for the method:
 #   forces: <= 1e-4 eV/A max-abs;
-#   per-atom energy: |dE_i| <= max(1e-5 * max(|E_i|, rms(E)),  KAPPA * u * sum_s |dE_i/dG_s * G_s|).
-# The second term is the floor that float32 descriptors impose: every descriptor
-# is a sum of positive terms, each rounded to u = 2^-24 relative, so E_i cannot be
-# known better than u times its condition number sum_s |dE_i/dG_s G_s|.  For the
-# water model that floor is ~1e-6 of |E_i| and the 1e-5 bound decides; for the FCC
-# model (per-atom energies ~0.1 eV, |mu/s| up to 18) it is ~3e-5 of |E_i|.
-# KAPPA = 4 allows the few ulp of exp/cos/sqrt in each term.
+#   per-atom energy: |dE_i| <= 1e-5 * max(|E_i|, rms(E)) (the "1e-5 relative" bound,
+#   with the rms as the floor of the scale so that near-zero E_i are not divided by).
 E_REL = 1e-5
 F_ABS = 1e-4
-KAPPA = 4.0
-U32 = 2.0 ** -24
 
 
 def f32(x):
@@ -36,11 +29,9 @@ def energy_err(Ei, ref_Ei):
 
 
 def energy_tol(ref, e_rel=E_REL):
-    """Per-atom energy tolerance (see the module comment)."""
+    """Per-atom energy tolerance: e_rel * max(|E_i|, rms E)."""
     Ei = ref["Ei"]
-    scale = np.maximum(np.abs(Ei), np.sqrt(np.mean(Ei ** 2)))
-    cond = np.abs(ref["dEdG"] * ref["G"]).sum(1)
-    return np.maximum(e_rel * scale, KAPPA * U32 * cond)
+    return e_rel * np.maximum(np.abs(Ei), np.sqrt(np.mean(Ei ** 2)))
 
 
 def check(out, ref, e_rel=E_REL, f_abs=F_ABS, what=""):

@@ -8,7 +8,7 @@ import torch
 
 import oracle
 import workloads
-from tests.gpuhelp import F_ABS, KAPPA, U32, E_REL, f32
+from tests.gpuhelp import F_ABS, E_REL, f32
 
 pytestmark = pytest.mark.gpu
 
@@ -26,8 +26,9 @@ def _sample(pos, box, n_random=24, seed=0):
 def _check_sampled(out, ref, idx, f_abs=F_ABS):
     Ei = out["Ei"].double().cpu().numpy()[idx]
     F = out["F"].double().cpu().numpy()[idx]
-    scale = np.maximum(np.abs(ref["Ei"]), 1e-3)
-    tol = np.maximum(E_REL * scale, KAPPA * U32 * np.abs(ref["dEdG"] * ref["G"]).sum(1))
+    # the scale floor is the sampled atoms' rms energy (the full box's is not known here)
+    scale = np.maximum(np.abs(ref["Ei"]), np.sqrt(np.mean(ref["Ei"] ** 2)))
+    tol = E_REL * scale
     assert np.all(np.abs(Ei - ref["Ei"]) <= tol), np.max(np.abs(Ei - ref["Ei"]) / tol)
     assert np.abs(F - ref["F"]).max() <= f_abs, np.abs(F - ref["F"]).max()
 
