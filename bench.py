@@ -412,23 +412,31 @@ def combined_run(args, dev):
 def domains_run(args, dev):
     """Slab domain decomposition of the workload (2 r_c halo, no reverse exchange),
     the domains evaluated one after another on one GPU, each with its own handle
-    and device-resident inputs: energy + forces per evaluation against the
-    undivided box."""
+    and device-resident inputs, through nnp_compute_domain (energy and virial of
+    the owned atoms): energy + forces + virial per evaluation against the
+    undivided box.  The halo exchange itself (boundary layers, point to point)
+    is host bookkeeping here and is not timed."""
     import torch
     from paper_2002_00054_b300 import NNP, domain
     model, pos_h, types_h, box, desc, max_nb = make_workload(args.workload)
     n = len(pos_h)
 
+    def run(h, p, t, b, n_own):
+        if n_own is None:
+            h.compute(p, t, b)
+        else:
+            h.compute_domain(p, t, b, n_own)
+
     def timed(handles, inputs):
         for _ in range(2):
-            for h, (p, t, b) in zip(handles, inputs):
-                h.compute(p, t, b)
+            for h, inp in zip(handles, inputs):
+                run(h, *inp)
         torch.cuda.synchronize()
         a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         for _ in range(args.steps):
-            for h, (p, t, b) in zip(handles, inputs):
-                h.compute(p, t, b)
+            for h, inp in zip(handles, inputs):
+                run(h, *inp)
         c.record()
         torch.cuda.synchronize()
         return a.elapsed_time(c) / args.steps
@@ -436,7 +444,7 @@ def domains_run(args, dev):
     p0 = torch.from_numpy(pos_h).to(dev)
     t0 = torch.from_numpy(types_h).to(dev)
     full = NNP(model, device=dev.index, max_neighbors=max_nb)
-    ms_full = timed([full], [(p0, t0, box)])
+    ms_full = timed([full], [(p0, t0, box, None)])
     full.close()
     out = {"metric": "energy + force evaluations, atoms/s", "mode": "domains", "workload": args.workload,
            "atoms": n, "steps": args.steps, "undivided_ms": ms_full, "undivided_atoms_per_s": n / (ms_full * 1e-3),
@@ -449,12 +457,16 @@ def domains_run(args, dev):
             local += len(lp)
             handles.append(NNP(model, device=dev.index, max_neighbors=max_nb))
             inputs.append((torch.tensor(lp, dtype=torch.float32, device=dev),
-                           torch.tensor(lt, dtype=torch.int32, device=dev), d.box))
+                           torch.tensor(lt, dtype=torch.int32, device=dev), d.box, len(d.owned)))
         ms = timed(handles, inputs)
         for h in handles:
             h.close()
+        # what each rank's point-to-point exchange would send: its two 2 r_c layers
+        sent = [sum(len(x) for x in domain.boundary_layers(pos_h[d.owned], box, model["cutoff"], k, nd)) * 40
+                for k, d in enumerate(doms)]
         out["decomposed"].append({"domains": nd, "ms": ms, "atoms_per_s": n / (ms * 1e-3),
                                   "local_atoms_over_owned": local / n,
+                                  "halo_bytes_sent_per_rank_max": max(sent),
                                   "per_domain_ms_if_concurrent": ms / nd})
     return out
 

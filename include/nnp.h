@@ -162,6 +162,23 @@ NNP_API int nnp_compute(nnp_handle* h, int n_atoms, const float* pos, const int*
                 double cutoff, double* energy, float* atom_energy, float* forces, double* virial,
                 void* stream);
 
+/* One spatial domain of a decomposed periodic box (the paper's outlook on
+ * multi-node runs, Sec. 5): as nnp_compute on the domain's local atoms, the
+ * n_owned atoms the domain owns first, then copies of every atom within 2 r_c
+ * of the domain (its halo), at positions in a local box.  With a 2 r_c halo an
+ * owned atom's energy and force come out exact, so no forces are sent back.
+ *   n_owned      0 <= n_owned <= n_atoms
+ *   energy       device double [1]: sum_{i < n_owned} E_i in FP64 (nullable)
+ *   virial       device double [9]: the pair virial of the owned atoms'
+ *                energies, -sum_{i < n_owned} sum_j d_ij^a dE_i/dd_ij^b
+ *                (nullable); summed over domains it is the box's virial
+ *   atom_energy, forces: for every local atom (the caller keeps the first
+ *                n_owned; halo atoms' values are not those of the box)
+ * Everything else as nnp_compute. */
+NNP_API int nnp_compute_domain(nnp_handle* h, int n_atoms, int n_owned, const float* pos, const int* types,
+                               const double* box, double* energy, float* atom_energy, float* forces, double* virial,
+                               void* stream);
+
 /* Raw descriptors G (Fig. 1b step 1) and dE_i/dG_i (the network's input gradient
  * used by step 3) of one system; arguments as nnp_compute.
  *   G, dEdG      device float [n_atoms][n_G] (each nullable). */
@@ -287,7 +304,9 @@ NNP_API int nnp_kernel_times(nnp_handle* h, int max_groups, double* total_ms, lo
  *
  * The first call on a device looks up the array's device address (a runtime
  * call, made once per device with that device current); make that first call
- * before any stream capture.  Every call shares the one array and leaves its
+ * before any stream capture.  The address is kept for the life of the process:
+ * after cudaDeviceReset on a device, do not call this entry point on that
+ * device again in the same process.  Every call shares the one array and leaves its
  * contents behind: calls whose work overlaps on the GPU (different streams or
  * host threads without ordering) race on it; serialise them.
  *

@@ -15,6 +15,9 @@ Functions and the paper passages they follow:
                       (E_system += E_i), forces by the chain rule of step 3 and
                       the pair virial.
   compute_subset() -- the same outputs for a chosen set of atoms only.
+  compute_owned()  -- energy and virial of the first n_own atoms' energies
+                      (a spatial domain's owned atoms; Sec. 5's multi-node
+                      outlook), Ei and F of every atom.
   mlp()            -- the per-element network alone (Sec. 3.1, "~30 x 2").
   md()             -- velocity-Verlet NVE (energy conservation, Sec. 4.2).
   param_grad()     -- force-matching parameter gradient (energy term plus the
@@ -113,6 +116,8 @@ def _load():
             lib.or_mlp.restype = ctypes.c_double
             lib.or_compute.argtypes = [P(_Model), P(_System), ctypes.c_int, P(_Out)]
             lib.or_compute.restype = ctypes.c_int
+            lib.or_compute_owned.argtypes = [P(_Model), P(_System), ctypes.c_int, ctypes.c_int, P(_Out)]
+            lib.or_compute_owned.restype = ctypes.c_int
             lib.or_compute_subset.argtypes = [P(_Model), P(_System), ctypes.c_int, P(ctypes.c_ubyte), P(_Out)]
             lib.or_compute_subset.restype = ctypes.c_int
             lib.or_md.argtypes = [P(_Model), P(_System), P(ctypes.c_double), P(ctypes.c_double),
@@ -265,6 +270,25 @@ def compute(model, pos, types, box, nbmode=NB_AUTO):
     if _load().or_compute(ctypes.byref(m.st), ctypes.byref(s.st), int(nbmode), ctypes.byref(o)):
         raise RuntimeError("oracle compute failed")
     return {"energy": float(E[0]), "Ei": Ei, "F": F, "virial": vir.reshape(3, 3), "G": G, "dEdG": dEdG}
+
+
+def compute_owned(model, pos, types, box, n_own, nbmode=NB_AUTO):
+    """compute() with the energy and the virial summed over the energies of the
+    first n_own atoms only (a domain's owned atoms, its halo copies after them);
+    Ei and F for every atom."""
+    m = _as_model(model)
+    s = _Sys(pos, types, box)
+    n = s.st.n
+    ldg = max(m.n_sf)
+    null = ctypes.POINTER(ctypes.c_double)()
+    Ei = np.zeros(n)
+    F = np.zeros((n, 3))
+    vir = np.zeros(9)
+    E = np.zeros(1)
+    o = _Out(null, null, _dptr(Ei), _dptr(F), _dptr(vir), _dptr(E), ldg)
+    if _load().or_compute_owned(ctypes.byref(m.st), ctypes.byref(s.st), int(nbmode), int(n_own), ctypes.byref(o)):
+        raise RuntimeError("oracle compute_owned failed")
+    return {"energy": float(E[0]), "Ei": Ei, "F": F, "virial": vir.reshape(3, 3)}
 
 
 def compute_subset(model, pos, types, box, idx, nbmode=NB_AUTO):

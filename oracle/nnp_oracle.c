@@ -518,8 +518,11 @@ double or_mlp(const or_model* m, int e, const double* x, double* dEdx)
 /* Core evaluation.  'target' (nullable) restricts the outputs: per-atom outputs
  * are produced for target atoms only, forces only for target atoms (summing the
  * contributions of every atom whose energy depends on them).  With target == NULL
- * everything is produced for every atom. */
-static int compute_core(const or_model* m, const or_system* s, int nbmode, const unsigned char* target, or_out* out)
+ * everything is produced for every atom.  n_sum: the energy and the virial sum
+ * the energies E_i of atoms i < n_sum only (n for the whole system): the energy
+ * sum_{i < n_sum} E_i and its strain derivative -sum_{i < n_sum} sum_j d_ij g_ij. */
+static int compute_core(const or_model* m, const or_system* s, int nbmode, const unsigned char* target, int n_sum,
+                        or_out* out)
 {
     const int n = s->n;
     const int W = max_width(m);
@@ -580,7 +583,7 @@ static int compute_core(const or_model* m, const or_system* s, int nbmode, const
         if (out->Ei) for (int i = 0; i < n; ++i) if (!target || target[i]) out->Ei[i] = Ei[i];
         if (out->energy && !target) {
             double E = 0.0;
-            for (int i = 0; i < n; ++i) E += Ei[i];
+            for (int i = 0; i < n_sum; ++i) E += Ei[i];
             out->energy[0] = E;
         }
         if (out->F) {
@@ -599,7 +602,7 @@ static int compute_core(const or_model* m, const or_system* s, int nbmode, const
         }
         if (out->virial && !target) {
             for (int k = 0; k < 9; ++k) out->virial[k] = 0.0;
-            for (int i = 0; i < n; ++i)
+            for (int i = 0; i < n_sum; ++i)
                 for (int a = 0; a < lists[i].n; ++a)
                     for (int p = 0; p < 3; ++p)
                         for (int q = 0; q < 3; ++q)
@@ -616,13 +619,22 @@ static int compute_core(const or_model* m, const or_system* s, int nbmode, const
 
 int or_compute(const or_model* m, const or_system* s, int nbmode, or_out* out)
 {
-    return compute_core(m, s, nbmode, NULL, out);
+    return compute_core(m, s, nbmode, NULL, s->n, out);
+}
+
+/* As or_compute, with the energy and the virial summed over the energies of the
+ * first n_own atoms only (a spatial domain whose owned atoms come first, its
+ * halo copies after them); Ei and F for every atom. */
+int or_compute_owned(const or_model* m, const or_system* s, int nbmode, int n_own, or_out* out)
+{
+    if (n_own < 0 || n_own > s->n) return -1;
+    return compute_core(m, s, nbmode, NULL, n_own, out);
 }
 
 /* Outputs (Ei, F, G, dEdG) for the atoms with target[i] != 0 only. */
 int or_compute_subset(const or_model* m, const or_system* s, int nbmode, const unsigned char* target, or_out* out)
 {
-    return compute_core(m, s, nbmode, target, out);
+    return compute_core(m, s, nbmode, target, s->n, out);
 }
 
 /* Velocity-Verlet NVE: v += dt/2 F/m c; x += dt v; F = F(x); v += dt/2 F/m c.

@@ -53,6 +53,7 @@ SIGNATURES = {
     "nnp_num_params": (I, [V]),
     "nnp_set_weights": (I, [V, V, V]),
     "nnp_compute": (I, [V, I, V, V, c_double_p, D, V, V, V, V, V]),
+    "nnp_compute_domain": (I, [V, I, I, V, V, c_double_p, V, V, V, V, V]),
     "nnp_descriptors": (I, [V, I, V, V, c_double_p, V, V, V]),
     "nnp_descriptors_flat": (I, [V, I, V, V, c_double_p, V, V]),
     "nnp_step": (I, [V, I, V, V, V, c_double_p, D, I, V, V]),

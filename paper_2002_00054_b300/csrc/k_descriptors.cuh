@@ -906,7 +906,7 @@ template <int NETA, bool NARROW, int KP, int KN, bool STORED, bool RES>
 __global__ void __launch_bounds__(128, 5)
 k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g, int C,
         const float* __restrict__ dEdG, float4* __restrict__ gbuf, float4* __restrict__ Fown,
-        double* __restrict__ vir_part, int* __restrict__ flags, int* __restrict__ spill, int pass,
+        double* __restrict__ vir_part, int n_vir, int* __restrict__ flags, int* __restrict__ spill, int pass,
         const unsigned short* __restrict__ qpool, const unsigned int* __restrict__ qoff,
         float* __restrict__ Fscat, unsigned long long* __restrict__ Fq, const float4* __restrict__ stg,
         size_t stg_plane, unsigned long long qcap)
@@ -1400,19 +1400,21 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         long long qx = 0, qy = 0, qz = 0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) v[q] = 0.f;
-        // the virial only when the caller asked for it (vir_part != nullptr)
+        // the virial only when the caller asked for it (vir_part != nullptr), and
+        // only of the energies of atoms i < n_vir (a domain's owned atoms)
+        const bool vir_i = vir_part && i < n_vir;
         for (int m = lane; m < M; m += 32) {
             if (Fq) {
                 qx += fx_get64<NARROW>(w, 3 * m);
                 qy += fx_get64<NARROW>(w, 3 * m + 1);
                 qz += fx_get64<NARROW>(w, 3 * m + 2);
             }
-            if (!Fq || vir_part) {
+            if (!Fq || vir_i) {
                 const float gx = fx_get<NARROW>(w, 3 * m), gy = fx_get<NARROW>(w, 3 * m + 1), gz = fx_get<NARROW>(w, 3 * m + 2);
                 if (!Fq) {
                     fx += gx; fy += gy; fz += gz;
                 }
-                if (vir_part) {
+                if (vir_i) {
                     const float4 d = w.nd[m];
                     v[0] -= d.x * gx; v[1] -= d.x * gy; v[2] -= d.x * gz;
                     v[3] -= d.y * gx; v[4] -= d.y * gy; v[5] -= d.y * gz;
@@ -1420,7 +1422,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 }
             }
         }
-        if (vir_part) {
+        if (vir_i) {
 #pragma unroll
             for (int q = 0; q < 9; ++q) {
                 const float t = warp_sum(v[q]);

@@ -397,7 +397,7 @@ static int build_plan(const nnp_params* p, Plan& P, int& n_params, std::string& 
 typedef void (*SfKernel)(int, const float4*, Box, NbView, const Plan*, int, float*, float*, int*, unsigned long long*,
                          int*, int, unsigned short*, unsigned int*, unsigned long long, float4*, size_t);
 typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float4*, float4*,
-                            double*, int*, int*, int, const unsigned short*, const unsigned int*, float*,
+                            double*, int, int*, int*, int, const unsigned short*, const unsigned int*, float*,
                             unsigned long long*, const float4*, size_t, unsigned long long);
 
 typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*, int*, int);
@@ -752,8 +752,10 @@ static int ensure_sys(nnp_handle* h, int B)
 
 static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, const double* box, cudaStream_t st,
                     double* energy, float* Ei_out, float* F_out, double* vir_out, float* G_out, float* dEdG_out,
-                    int stop_after, const Batch* bt = nullptr)
+                    int stop_after, const Batch* bt = nullptr, int n_sum = -1)
 {
+    // energy and virial: sums over the energies of atoms i < n_sum (all by default)
+    if (n_sum < 0 || n_sum > n) n_sum = n;
     int rc = ensure_atoms(h, n);
     if (rc) return rc;
     const Plan& P = h->plan;
@@ -941,13 +943,13 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         const bool stored = P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW && !P.resolved && h->qpool;
         (stored ? kfs : kf)<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
             n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, vir_out ? h->vpart : nullptr,
-            h->flags, h->spill, 0,
+            n_sum, h->flags, h->spill, 0,
             stored ? h->qpool : nullptr, stored ? h->qoff : nullptr, Fsc, Fq, (stored && staged) ? h->stg : nullptr,
             stg_plane, stored ? (unsigned long long)h->cap_qpool : 0ull);
         kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride,
                                                                        h->dEdG, h->gbuf, h->Fown,
                                                                        vir_out ? h->vpart + (size_t)nvp_main * 9 : nullptr,
-                                                                       h->flags,
+                                                                       n_sum, h->flags,
                                                                        h->spill, 1, nullptr, nullptr, Fsc, Fq, nullptr, 0, 0ull);
     }
     if (h->fmode == FM_GATHER) {
@@ -962,7 +964,7 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         if (energy) k_sys_energy<<<bt->B, 256, 0, st>>>(h->sys_start_d, h->Ei, energy, h->flags);
     } else {
         KScope ks(h, KG_REDUCE, st, 2);
-        k_sum_partial<<<gred, T, 0, st>>>(n, h->Ei, h->epart, h->flags);
+        k_sum_partial<<<gred, T, 0, st>>>(n_sum, h->Ei, h->epart, h->flags);
         k_finalize<<<1, 256, 0, st>>>(gred, h->epart, energy ? energy : h->d_energy, vir_out ? nvp : 0, h->vpart,
                                       vir_out);
     }
@@ -1312,6 +1314,31 @@ int nnp_compute(nnp_handle* h, int n, const float* pos, const int* types, const 
     rc = begin_call(h, st);
     if (rc) return rc;
     rc = run_eval(h, n, pos, types, box, st, energy, atom_energy, forces, virial, nullptr, nullptr, 0);
+    if (rc) return rc;
+    return read_status(h, st);
+}
+
+int nnp_compute_domain(nnp_handle* h, int n, int n_owned, const float* pos, const int* types, const double* box,
+                       double* energy, float* atom_energy, float* forces, double* virial, void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    h->err.clear();
+    if (n_owned < 0 || n_owned > n) return set_err(h, NNP_EINVAL, "n_owned must be in 0..n_atoms");
+    int rc = common_args(h, n, pos, types, box);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (n == 0) {
+        if (energy) CK(h, cudaMemsetAsync(energy, 0, sizeof(double), st));
+        if (virial) CK(h, cudaMemsetAsync(virial, 0, 9 * sizeof(double), st));
+        CK(h, cudaStreamSynchronize(st));
+        return NNP_OK;
+    }
+    h->step_valid = false;
+    rc = begin_call(h, st);
+    if (rc) return rc;
+    rc = run_eval(h, n, pos, types, box, st, energy, atom_energy, forces, virial, nullptr, nullptr, 0, nullptr,
+                  n_owned);
     if (rc) return rc;
     return read_status(h, st);
 }
@@ -1790,9 +1817,9 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     h->kmlp<<<gmlp, 128, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);
     // no virial output: the force passes write no virial partials
     kf<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, dEdG, gbuf, Fown, nullptr,
-                                                     flags, spill, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0ull);
+                                                     0, flags, spill, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0ull);
     kf<<<h->grid_sp, 32 * h->wpb_force_sp, h->smem_force_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, dEdG, gbuf, Fown,
-                                                                   nullptr, flags, spill, 1, nullptr, nullptr, nullptr,
+                                                                   nullptr, 0, flags, spill, 1, nullptr, nullptr, nullptr,
                                                                    nullptr, nullptr, 0, 0ull);
     k_gather<<<rows_grid, 256, 0, st>>>(n, nv, rev, gbuf, Fown, forces ? forces : Fs, flags);
     k_sum_partial<<<gred, T, 0, st>>>(n, Ei, epart, flags);

@@ -122,6 +122,24 @@ class NNP:
             out["virial"] = out["virial"].view(3, 3)
         return out
 
+    def compute_domain(self, pos, types, box, n_owned, stream=None):
+        """One spatial domain (owned atoms first, then its 2 r_c halo): energy and
+        virial of the owned atoms' energies (fp64), Ei and F of every local atom."""
+        n = int(pos.shape[0]) if pos.dim() == 2 else 0
+        dev = torch.device("cuda", self.device)
+        _need(pos, torch.float32, (n, 3), "pos", self.device)
+        _need(types, torch.int32, (n,), "types", self.device)
+        out = {"energy": torch.empty(1, dtype=torch.float64, device=dev),
+               "Ei": torch.empty(n, dtype=torch.float32, device=dev),
+               "F": torch.empty((n, 3), dtype=torch.float32, device=dev),
+               "virial": torch.empty(9, dtype=torch.float64, device=dev)}
+        b, bp = self._box(box)
+        rc = self._lib.nnp_compute_domain(self.h, n, int(n_owned), _ptr(pos), _ptr(types), bp, _ptr(out["energy"]),
+                                          _ptr(out["Ei"]), _ptr(out["F"]), _ptr(out["virial"]), _stream(stream))
+        self._check(rc)
+        out["virial"] = out["virial"].view(3, 3)
+        return out
+
     def compute_into(self, pos, types, box, energy, Ei=None, F=None, virial=None, stream=None):
         """nnp_compute into caller-provided device tensors (no allocation)."""
         b, bp = self._box(box)

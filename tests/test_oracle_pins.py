@@ -287,6 +287,30 @@ def test_virial_matches_strain_fd():
         assert r0["virial"][b, a] == pytest.approx(-(ep - em) / (2 * h), rel=1e-6, abs=1e-7)
 
 
+def test_owned_virial_is_the_strain_derivative_of_the_owned_energy():
+    """compute_owned: W_A = -dE_A/d eps for E_A = sum of the first n_own atoms'
+    energies (finite differences of those energies under strain), and the parts
+    for A and its complement add up to the whole system's virial."""
+    m = workloads.water_model()
+    pos, types, box = workloads.water_random()
+    n_own = 100
+    r = oracle.compute_owned(m, pos, types, box, n_own)
+    assert r["energy"] == pytest.approx(r["Ei"][:n_own].sum(), rel=1e-14)
+    h = 1e-6
+    for a in range(3):
+        s = np.ones(3); s[a] += h
+        ep = oracle.compute(m, pos * s, types, box * s)["Ei"][:n_own].sum()
+        s[a] -= 2 * h
+        em = oracle.compute(m, pos * s, types, box * s)["Ei"][:n_own].sum()
+        assert r["virial"][a, a] == pytest.approx(-(ep - em) / (2 * h), rel=1e-6, abs=1e-6)
+    # the complement: atoms n_own.. moved to the front
+    order = np.r_[np.arange(n_own, len(pos)), np.arange(n_own)]
+    rb = oracle.compute_owned(m, pos[order], types[order], box, len(pos) - n_own)
+    full = oracle.compute(m, pos, types, box)
+    np.testing.assert_allclose(r["virial"] + rb["virial"], full["virial"], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(r["F"], full["F"], rtol=0, atol=1e-12)
+
+
 # ------------------------------------------------------------------- network
 def test_mlp_matches_torch_sequential():
     torch = pytest.importorskip("torch")

@@ -31,21 +31,48 @@ def _static(nnp, p, t, box):
     return rc, buf.value.decode(), e, ei, f
 
 
+def _cluster(n=150, radius=5.4, min_sep=1.3, box=40.0, seed=77):
+    """A dense isolated ball: atoms near its centre have more neighbours inside
+    the cutoff than the handle's shared-memory capacity, so the call's
+    wide-capacity pass runs; every neighbour-list row stays below 192."""
+    rng = np.random.default_rng(seed)
+    c = np.full(3, box / 2)
+    pts = []
+    while len(pts) < n:
+        x = c + rng.uniform(-radius, radius, 3)
+        if np.linalg.norm(x - c) > radius:
+            continue
+        if all(np.linalg.norm(x - q) >= min_sep for q in pts):
+            pts.append(x)
+    return np.array(pts), np.zeros(n, np.int32), np.array([box, box, box])
+
+
 def _cases():
     L = (3 * 21 / workloads.WATER_DENSITY_ATOMS) ** (1 / 3)
     return [("water", workloads.water_model, workloads.water_random()),
             ("water", workloads.water_model, workloads.water_random(21, L, seed=121)),
-            ("fcc", workloads.fcc_model, workloads.fcc((2, 2, 2), sigma=0.1, seed=4))]
+            ("fcc", workloads.fcc_model, workloads.fcc((2, 2, 2), sigma=0.1, seed=4)),
+            # exactly NNP_STATIC_MAX_ATOMS atoms at the default max_neighbors
+            ("fcc", workloads.fcc_model, workloads.fcc((4, 8, 8), sigma=0.1, seed=5)),
+            ("fcc", workloads.fcc_model, _cluster())]
 
 
 def test_static_matches_compute_on_two_calls_in_a_row():
     from paper_2002_00054_b300 import NNP
     handles = {}
     for name, mk, (pos, types, box) in _cases():
-        nnp = handles.setdefault(name, NNP(mk()))
+        ref_nnp = handles.setdefault(name, NNP(mk()))
+        nnp = NNP(mk())   # fresh handle: its capacity has not been re-tuned by a call
         pos, box = f32(pos), f32(box)
         p, t = to_dev(pos, types)
-        ref = nnp.compute(p, t, box)
+        ref = ref_nnp.compute(p, t, box)
+        if len(pos) == 150:
+            # the cluster sends atoms through the wide-capacity pass: some atom has
+            # more neighbours inside the cutoff than the capacity the static call uses
+            C = nnp.stats()["rc_capacity"]
+            d = pos[:, None, :] - pos[None, :, :]
+            cnt = ((d ** 2).sum(-1) < nnp.cutoff ** 2).sum(1) - 1
+            assert cnt.max() > C, (cnt.max(), C)
         Ei_ref = ref["Ei"].double().cpu().numpy()
         first = None
         for call in range(2):
