@@ -506,16 +506,22 @@ def ablation_run(args, dev):
                      "kernels_ms": {k: round(v[0], 3) for k, v in kt.items() if v[1] > 0}}
         h.close()
     # descriptor pass: warp per atom (the kernels used everywhere) against one
-    # thread per atom (the flat level of the paper's parallelism study)
+    # thread per atom (the flat level of the paper's parallelism study) and one
+    # thread per (atom, neighbour) with atomic updates of G (its hierarchical level)
     h = NNP(model, device=dev.index, max_neighbors=max_nb)
     p = torch.from_numpy(pos_h).to(dev)
     Gf = h.descriptors_flat(p, t, box)
+    Gp = h.descriptors_pair(p, t, box)
     Gw, _ = h.descriptors(p, t, box, dEdG=False)
     h.profile(True)
     calls = 3
     for _ in range(calls):
         h.descriptors_flat(p, t, box)
     kt = h.kernel_times()
+    h.profile(True)
+    for _ in range(calls):
+        h.descriptors_pair(p, t, box)
+    kt_pair = h.kernel_times()
     # neighbour-list skin: rebuild frequency against list length (list capacity
     # scaled with the neighbour sphere's volume)
     rc = float(model["cutoff"])
@@ -537,9 +543,11 @@ def ablation_run(args, dev):
         out["skin"]["%.1f" % skin] = {"value": n * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
                                       "rebuilds": hs.stats()["rebuilds"] - r0, "max_neighbors": mn}
         hs.close()
+    rel = lambda G: float(((G - Gw).abs() / Gw.abs().clamp_min(1e-30)).max())
     out["descriptor_parallelism"] = {
         "warp_per_atom_ms": kt["descriptors"][0] / calls, "thread_per_atom_ms": kt["descriptors_flat"][0] / calls,
-        "max_rel_difference": float(((Gf - Gw).abs().max(0).values / Gw.abs().max(0).values.clamp_min(1e-30)).max())}
+        "thread_per_atom_neighbour_ms": kt_pair["descriptors_pair"][0] / calls,
+        "max_rel_difference_flat": rel(Gf), "max_rel_difference_pair": rel(Gp)}
     h.close()
     return out
 

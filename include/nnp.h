@@ -195,6 +195,18 @@ NNP_API int nnp_descriptors(nnp_handle* h, int n_atoms, const float* pos, const 
 NNP_API int nnp_descriptors_flat(nnp_handle* h, int n_atoms, const float* pos, const int* types, const double* box,
                                  float* G, void* stream);
 
+/* Raw descriptors G with one thread per (atom, neighbour-list slot): the
+ * hierarchical level of the paper's parallelism study (Sec. 4.3 / Fig. 6;
+ * threads over atoms and neighbours).  The thread for neighbour j of atom i adds
+ * the radial terms of j and the angular terms of the pairs (j, k), k after j in
+ * i's list, and adds those partial descriptors into G_i with float atomics (the
+ * extra atomic update of the symmetry functions the paper names for this level),
+ * so the last bits of G depend on scheduling.  For the ablation; otherwise as
+ * nnp_descriptors_flat.
+ *   G  device float [n_atoms][n_G], overwritten. */
+NNP_API int nnp_descriptors_pair(nnp_handle* h, int n_atoms, const float* pos, const int* types, const double* box,
+                                 float* G, void* stream);
+
 /* n_steps velocity-Verlet NVE steps (Sec. 4.2 energy conservation):
  *   v += dt/2 F/m;  x += dt v;  F = F(x);  v += dt/2 F/m
  * pos, vel: device float [n_atoms][3], updated in place (positions are not wrapped).

@@ -643,9 +643,9 @@ struct DeviceGuard {
     }
 };
 
-enum { KG_NEIGH = 0, KG_SF, KG_MLP, KG_FORCE, KG_GATHER, KG_REDUCE, KG_INTEGRATE, KG_FLAT, KG_N };
+enum { KG_NEIGH = 0, KG_SF, KG_MLP, KG_FORCE, KG_GATHER, KG_REDUCE, KG_INTEGRATE, KG_FLAT, KG_PAIR, KG_N };
 static const char* kKgName[KG_N] = {"neighbor_maintenance", "descriptors", "network", "force", "gather",
-                                    "reductions", "integrate", "descriptors_flat"};
+                                    "reductions", "integrate", "descriptors_flat", "descriptors_pair"};
 static_assert(KG_N <= 16, "kernel-group timers hold 16 groups");
 
 static cudaEvent_t ev_get(nnp_handle* h)
@@ -1384,6 +1384,39 @@ int nnp_descriptors_flat(nnp_handle* h, int n, const float* pos, const int* type
     {
         KScope ks(h, KG_FLAT, st);
         k_sf_flat<<<blocks_for(n, 128), 128, 0, st>>>(n, h->pos4, bx, nv, h->d_plan, G, h->flags);
+    }
+    return read_status(h, st);
+}
+
+int nnp_descriptors_pair(nnp_handle* h, int n, const float* pos, const int* types, const double* box, float* G,
+                         void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    h->err.clear();
+    if (!G) return set_err(h, NNP_EINVAL, "G must not be NULL");
+    if (h->plan.resolved)
+        return set_err(h, NNP_EUNSUPPORTED, "the atom-by-neighbour descriptors do not resolve angular pair classes");
+    int rc = common_args(h, n, pos, types, box);
+    if (rc) return rc;
+    if (n == 0) return NNP_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    h->step_valid = false;
+    rc = begin_call(h, st);
+    if (rc) return rc;
+    // neighbour list (and the warp-per-atom pass, which this call does not return)
+    rc = run_eval(h, n, pos, types, box, st, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1);
+    if (rc) return rc;
+    Box bx;
+    for (int a = 0; a < 3; ++a) bx.L[a] = (float)box[a];
+    NbView nv{h->nbr, h->ncount, h->stride};
+    // G rows are n_G floats; every element shares the model's n_G (widths[0])
+    CK(h, cudaMemsetAsync(G, 0, sizeof(float) * (size_t)n * h->plan.width[0], st));
+    {
+        KScope ks(h, KG_PAIR, st);
+        const long long items = (long long)n * h->stride;
+        const int grid = (int)std::min<long long>((items + 127) / 128, (long long)h->num_sms * 16);
+        k_sf_pair<<<grid, 128, 0, st>>>(n, h->pos4, bx, nv, h->d_plan, G, h->flags);
     }
     return read_status(h, st);
 }

@@ -264,8 +264,9 @@ def test_force_assembly_forms_agree(name, form, monkeypatch):
 
 @pytest.mark.parametrize("name", ["water", "fcc"])
 def test_thread_per_atom_descriptors(name):
-    """The thread-per-atom descriptor kernel (the parallelism ablation) gives the
-    same raw G as the warp-per-atom kernel and the oracle, to FP32 summation
+    """The other parallelism levels of the ablation (Fig. 6): one thread per atom,
+    and one thread per (atom, neighbour) with atomic updates of G_i, give the
+    raw G of the oracle (and of the warp-per-atom kernel) to FP32 summation
     order (plain float sums over ~2000 triplets per atom)."""
     from paper_2002_00054_b300 import NNP
     if name == "water":
@@ -276,13 +277,15 @@ def test_thread_per_atom_descriptors(name):
     p, t = to_dev(pos, types)
     nnp = NNP(m)
     Gf = nnp.descriptors_flat(p, t, box).double().cpu().numpy()
+    Gp = nnp.descriptors_pair(p, t, box).double().cpu().numpy()
     Gw, _ = nnp.descriptors(p, t, box, dEdG=False)
     Gw = Gw.double().cpu().numpy()
     ng = Gw.shape[1]
     gref = oracle.compute(m, pos, types, box)["G"][:, :ng]
-    scale = np.maximum(np.abs(gref).max(0), 1e-30)
-    assert (np.abs(Gf - gref) / scale).max() < 1e-5
-    assert (np.abs(Gf - Gw) / scale).max() < 1e-5
+    # plain float sums in both ablation kernels: element by element to ~1e-5
+    np.testing.assert_allclose(Gf, gref, rtol=1e-5, atol=0)
+    np.testing.assert_allclose(Gp, gref, rtol=1e-5, atol=0)
+    np.testing.assert_allclose(Gw, gref, rtol=2e-6, atol=0)
 
 
 @pytest.mark.parametrize("spill", [False, True])
