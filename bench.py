@@ -188,31 +188,100 @@ def fcc_precision_leg(dev, steps, warmup, with_oracle):
     return res
 
 
-def cpu_baseline(model_name, budget_s=12.0):
-    """The FP64 oracle, as it stands, on a 1,536-atom sample of the same workload
-    recipe (2x2x2 replica cells of the water lattice, or a 6x6x8 FCC box):
-    neighbour search + energy + forces per evaluation, repeated for ~budget_s."""
+def cpu_model():
+    """The host CPU's model name (/proc/cpuinfo) and its logical core count."""
+    name = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return name, os.cpu_count()
+
+
+def _oracle_rate(m, pos, types, box, seconds, repeats=5):
+    """Median over `repeats` of atom-evaluations/s, each repeat ~seconds of
+    back-to-back oracle evaluations (neighbour search + energy + forces)."""
+    import oracle
+    oracle.compute(m, pos, types, box)
+    rates = []
+    for _ in range(repeats):
+        n_eval, t0 = 0, time.perf_counter()
+        while True:
+            oracle.compute(m, pos, types, box)
+            n_eval += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+        rates.append(len(pos) * n_eval / el)
+    return float(np.median(rates)), rates
+
+
+def cpu_baseline(model_name, budget_s=20.0):
+    """The FP64 oracle, as it stands, timed on the host cores: on all cores, a
+    1,536-atom sample of the same workload recipe (2x2x2 replica cells of the
+    water lattice, or a 6x6x8 FCC box); on one core, the 192-atom water box (or
+    the 1,152-atom FCC box).  Median of 5 repeats each, ~budget_s in all."""
     import oracle
     if model_name == "water":
         pos, types, box = workloads.water_lattice((2, 2, 2))
         model = workloads.water_model()
+        p1, t1, b1 = workloads.water_random()
         sample = "1,536-atom water-like box (2x2x2 replicas of the same lattice recipe), E+F per evaluation"
+        sample1 = "192-atom water-like box"
     else:
         pos, types, box = workloads.fcc((6, 6, 8))
         model = workloads.fcc_model()
+        p1, t1, b1 = pos, types, box
         sample = "1,152-atom FCC box (same recipe), E+F per evaluation"
-    cores = oracle.set_threads(0)
+        sample1 = sample
     m = oracle.Model(model)
-    oracle.compute(m, pos, types, box)
-    n_eval, t0 = 0, time.perf_counter()
-    while True:
-        oracle.compute(m, pos, types, box)
-        n_eval += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s:
-            break
-    return {"value": len(pos) * n_eval / el, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%s; %d evaluations in %.1f s on %d threads" % (sample, n_eval, el, cores)}
+    name, logical = cpu_model()
+    cores = oracle.set_threads(logical or 0)
+    value, rates = _oracle_rate(m, pos, types, box, 0.6 * budget_s / 5)
+    oracle.set_threads(1)
+    single, rates1 = _oracle_rate(m, p1, t1, b1, 0.4 * budget_s / 5)
+    oracle.set_threads(cores)
+    return {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%s; median of 5 repeats of ~%.1f s on %d threads" % (sample, 0.6 * budget_s / 5, cores),
+            "repeats": [round(r, 1) for r in rates], "cpu_model": name, "logical_cores": logical,
+            "single_thread": {"value": single, "unit": UNIT, "cores": 1,
+                              "sample": "%s; median of 5 repeats of ~%.1f s" % (sample1, 0.4 * budget_s / 5),
+                              "repeats": [round(r, 1) for r in rates1]}}
+
+
+def cpu_plan_run(args):
+    """The CPU baseline in full (a separate mode: several minutes): the oracle on
+    the 192-atom water box and the 110,592-atom water box, on one thread and on
+    every host thread.  Median of 5 repeats on the small box; on the large box
+    median of 3 evaluations on all threads and one evaluation on one thread."""
+    import oracle
+    name, logical = cpu_model()
+    model = workloads.water_model()
+    m = oracle.Model(model)
+    out = {"mode": "cpu", "metric": METRIC, "unit": UNIT, "kind": "oracle", "cpu_model": name,
+           "logical_cores": logical, "legs": []}
+    small = workloads.water_random()
+    big = workloads.water_lattice((8, 8, 9))
+    for threads in (1, logical):
+        oracle.set_threads(threads)
+        v, rates = _oracle_rate(m, *small, 2.0)
+        out["legs"].append({"workload": "water 192 atoms", "threads": threads, "value": v,
+                            "repeats": [round(r, 1) for r in rates]})
+        reps = 3 if threads > 1 else 1
+        times = []
+        oracle.compute(m, *big) if threads > 1 else None
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            oracle.compute(m, *big)
+            times.append(time.perf_counter() - t0)
+        t = float(np.median(times))
+        out["legs"].append({"workload": "water 110,592 atoms", "threads": threads, "value": len(big[0]) / t,
+                            "seconds_per_evaluation": [round(x, 2) for x in times]})
+    return out
 
 
 def reference_arm(args, rank):
@@ -564,7 +633,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
     ap.add_argument("--no-fcc", action="store_true", help="skip the FCC precision-form leg")
-    ap.add_argument("--mode", default="standard", choices=["standard", "combined", "domains", "ablation"])
+    ap.add_argument("--mode", default="standard", choices=["standard", "combined", "domains", "ablation", "cpu"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -590,6 +659,10 @@ def main():
     if args.mode == "domains":
         if rank == 0:
             print(json.dumps(domains_run(args, dev)), flush=True)
+        return
+    if args.mode == "cpu":
+        if rank == 0:
+            print(json.dumps(cpu_plan_run(args)), flush=True)
         return
     if args.mode == "ablation":
         if rank == 0:

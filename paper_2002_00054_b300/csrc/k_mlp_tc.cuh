@@ -212,6 +212,7 @@ __global__ void k_elem_fill(int n, const float4* __restrict__ pos4, int n_elem, 
 
 struct TcShape {
     int K0, H1, H2;   // padded to multiples of 16
+    int GS;           // row stride (floats) of the G~ and dE/dG buffers, a multiple of 4
 };
 
 // shared-memory image, per element: W1 [H1][K0], W2 [H2][H1], W2t [H1][H2], W1t [K0][H1]
@@ -220,11 +221,13 @@ __host__ __device__ inline int tc_elem_bytes(const TcShape& s)
 {
     return 2 * (s.H1 * s.K0 + s.H2 * s.H1 + s.H1 * s.H2 + s.K0 * s.H1) + 4 * (s.H1 + 2 * s.H2 + 4 + s.K0);
 }
-// activation tiles: X [128][K0], H [128][max(H1,H2)] twice (h1 / d1, d2)
+// activation tiles: X [128][K0], H [128][max(H1,H2)] twice (h1 / d1, d2), then the
+// FP32 staging of the next tile's G~ rows, [128][GS + 4] (the pad keeps the
+// threads' 16-byte reads of their own rows on distinct banks)
 __host__ __device__ inline int tc_tile_bytes(const TcShape& s)
 {
     const int H = s.H1 > s.H2 ? s.H1 : s.H2;
-    return 2 * TC_TILE * (s.K0 + 2 * H);
+    return 2 * TC_TILE * (s.K0 + 2 * H) + 4 * TC_TILE * (s.GS + 4);
 }
 
 __global__ void __launch_bounds__(128, 1)
@@ -241,6 +244,8 @@ k_mlp_tc(int n, const Plan* __restrict__ plan_g, const float* __restrict__ weigh
     unsigned char* tX = smem_tc + ((P.n_elem * eb + 1023) & ~1023);
     unsigned char* tA = tX + 2 * TC_TILE * K0;    // h1, then d1
     unsigned char* tB = tA + 2 * TC_TILE * HH;    // d2
+    float* tS = reinterpret_cast<float*>(tB + 2 * TC_TILE * HH);   // staged G~ rows of the next tile
+    const int SS = sh.GS + 4;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
 
@@ -301,30 +306,53 @@ k_mlp_tc(int n, const Plan* __restrict__ plan_g, const float* __restrict__ weigh
     uint32_t phase = 0;
     bool ok = true;
     const int n_tiles = tile_off[P.n_elem];
+    // element of tile tl and the atom of this thread's row in it (-1: padding)
+    auto tile_atom = [&](int tl, int& e_out) {
+        int e = 0;
+        while (e + 1 < P.n_elem && tile_off[e + 1] <= tl) ++e;
+        e_out = e;
+        const int row = elem_off[e] + (tl - tile_off[e]) * TC_TILE + t;
+        return (row < elem_off[e + 1]) ? idx[row] : -1;
+    };
+    // asynchronous copy of this thread's G~ row into its staging row (one group)
+    auto prefetch = [&](int a) {
+        if (a >= 0) {
+            const float* src = Gs + (size_t)a * P.gs;
+            const uint32_t dst = tc::smem_u32(tS + t * SS);
+            for (int c = 0; c < P.gs; c += 4)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 4 * c), "l"(src + c) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    int e_next = 0, atom_next = -1;
+    if ((int)blockIdx.x < n_tiles) {
+        atom_next = tile_atom(blockIdx.x, e_next);
+        prefetch(atom_next);
+    }
 
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        int e = 0;
-        while (e + 1 < P.n_elem && tile_off[e + 1] <= tile) ++e;
-        const int start = elem_off[e] + (tile - tile_off[e]) * TC_TILE;
-        const int end = elem_off[e + 1];
-        const int row = start + t;
-        const int atom = (row < end) ? idx[row] : -1;
+        const int e = e_next, atom = atom_next;
         const unsigned char* img = wimg + e * eb;
         const float* fb = reinterpret_cast<const float*>(img + 2 * (H1 * K0 + H2 * H1 + H1 * H2 + K0 * H1));
         const uint32_t w1a = tc::smem_u32(img), w2a = w1a + 2 * H1 * K0, w2ta = w2a + 2 * H2 * H1,
                        w1ta = w2ta + 2 * H1 * H2;
         const uint32_t xa = tc::smem_u32(tX), aa = tc::smem_u32(tA), ba = tc::smem_u32(tB);
 
-        // X row: G~ of this atom (zeros for padding rows and columns)
+        // X row: G~ of this atom from its staging row (zeros for padding rows and
+        // columns); then the next tile's rows are copied in while this one runs
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         for (int k0 = 0; k0 < K0; k0 += 8) {
             float v[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int k = k0 + u;
-                v[u] = (atom >= 0 && k < P.width[0]) ? Gs[(size_t)atom * P.gs + k] : 0.f;
+                v[u] = (atom >= 0 && k < P.width[0]) ? tS[t * SS + k] : 0.f;
             }
             tc::put8(tX, t, k0, K0, v);
         }
+        atom_next = -1;
+        if (tile + (int)gridDim.x < n_tiles) atom_next = tile_atom(tile + gridDim.x, e_next);
+        prefetch(atom_next);
         tc::fence_async_smem();
         tc::fence_before();
         __syncthreads();
@@ -409,10 +437,14 @@ k_mlp_tc(int n, const Plan* __restrict__ plan_g, const float* __restrict__ weigh
         for (int c0 = 0; c0 < K0; c0 += 32) {
             tc::tmem_ld32(lane_addr + D4 + c0, tmp);
             if (atom >= 0) {
+                // 16-byte stores up to the row stride (1/s is zero past n_G)
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
+                for (int q = 0; q < 32; q += 4) {
                     const int k = c0 + q;
-                    if (k < P.width[0]) dEdG[(size_t)atom * P.gs + k] = tmp[q] * fb[H1 + 2 * H2 + 4 + k];
+                    if (k < P.gs)
+                        *reinterpret_cast<float4*>(dEdG + (size_t)atom * P.gs + k) =
+                            make_float4(tmp[q] * fb[H1 + 2 * H2 + 4 + k], tmp[q + 1] * fb[H1 + 2 * H2 + 5 + k],
+                                        tmp[q + 2] * fb[H1 + 2 * H2 + 6 + k], tmp[q + 3] * fb[H1 + 2 * H2 + 7 + k]);
                 }
             }
         }
@@ -420,6 +452,7 @@ k_mlp_tc(int n, const Plan* __restrict__ plan_g, const float* __restrict__ weigh
         __syncthreads();   // TMEM and tiles are reused by the next tile
         tc::fence_after();
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy left in flight
     if (!ok && t == 0) atomicOr(&flags[FLAG_ERR], ERR_TIMEOUT);
     tc::fence_before();
     __syncthreads();

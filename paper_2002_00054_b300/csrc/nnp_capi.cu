@@ -1202,7 +1202,7 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     CKC(cudaFuncSetAttribute((const void*)h->kmlp, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     if (h->precision == NNP_BF16) {
         auto r16 = [](int x) { return (x + 15) & ~15; };
-        h->tcs = TcShape{r16(P.width[0]), r16(P.width[1]), r16(P.width[2])};
+        h->tcs = TcShape{r16(P.width[0]), r16(P.width[1]), r16(P.width[2]), P.gs};
         h->smem_tc = (size_t)((P.n_elem * tc_elem_bytes(h->tcs) + 1023) & ~1023) + tc_tile_bytes(h->tcs);
         if (h->smem_tc > (size_t)max_smem) {
             set_err(h, NNP_EUNSUPPORTED, "BF16 network weights do not fit in shared memory");
