@@ -62,6 +62,14 @@ TRAFFIC_SRC_SHA = "e349efb0b720"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
+def load_peaks():
+    """The machine's measured peaks (HBM GB/s, BF16 TFLOP/s), or {} when absent."""
+    if not os.path.exists(MEASURED_PEAKS):
+        return {}
+    with open(MEASURED_PEAKS) as f:
+        return json.load(f)
+
+
 def src_sha():
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2002_00054_b300", "csrc")
@@ -804,6 +812,18 @@ def main():
             "force_rms_err_vs_fp32_ev_per_A": float(dF.pow(2).mean().sqrt().item()),
             "force_max_err_vs_fp32_ev_per_A": float(dF.abs().max().item()),
             "energy_err_vs_fp32_ev_per_atom": float(abs(b16_out["energy"].item() - f32_out["energy"].item()) / n)}
+        # tensor-core work of one network evaluation: four M = 128 MMAs per tile at the
+        # padded widths (K0 = n_G, H1, H2 rounded up to 16), 2 flops per multiply-add
+        r16 = lambda x: (x + 15) // 16 * 16
+        k0, h1, h2 = (r16(w) for w in model["widths"][:3])
+        tiles = sum((int((types_h == e).sum()) + 127) // 128 for e in range(len(model["sf"])))
+        flops = 2.0 * 128 * tiles * (k0 * h1 + h1 * h2 + h2 * h1 + h1 * k0)
+        net_ms = out["bf16_mlp"]["network_ms_per_step"]
+        peak = load_peaks().get("bf16_tflops")
+        out["bf16_mlp"]["tensor"] = {"flops_per_evaluation": flops, "achieved_tflops": flops / (net_ms * 1e-3) / 1e12,
+                                     "peak_tflops": peak, "peak_source": "measured (MEASURED_PEAKS.json bf16_tflops)",
+                                     "frac": (flops / (net_ms * 1e-3) / 1e12 / peak) if peak else None,
+                                     "ncu_tensor_pipe_active": "0.76 % (profiles/, 110,592-atom capture)"}
         bf.close()
     if not args.no_train:
         out["training_step"] = training_leg(dev, max(3, args.steps // 2), args.warmup)
