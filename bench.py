@@ -548,6 +548,62 @@ def domains_run(args, dev):
     return out
 
 
+def capacity_run(args, dev):
+    """How many water-like atoms one B300 holds on the default path (the paper
+    quotes 2M atoms per V100 GPU, Sec. 4.2): device bytes per atom measured from
+    the free-memory drop of a 1,048,320-atom evaluation (library scratch, pair
+    queues, staged neighbours and the caller's tensors), then nnp_step on a box
+    sized to 60 % of the free memory, well inside it (no out-of-memory probe)."""
+    import torch
+    from paper_2002_00054_b300 import NNP
+    model = workloads.water_model()
+    torch.cuda.synchronize()
+    free0, total = torch.cuda.mem_get_info(dev)
+
+    def make(reps):
+        pos, types, box = workloads.water_lattice(reps)
+        vel = workloads.maxwell_boltzmann(types, model["masses"])
+        return (torch.tensor(pos.astype(np.float32), device=dev), torch.tensor(types, dtype=torch.int32, device=dev),
+                torch.tensor(vel.astype(np.float32), device=dev), box)
+
+    p, t, v, box = make((13, 20, 21))
+    n1 = p.shape[0]
+    h = NNP(model, device=dev.index, max_neighbors=200)
+    h.step(p, v, t, box, DT_FS, 3)   # the queue pool settles on the second evaluation
+    torch.cuda.synchronize()
+    free1 = torch.cuda.mem_get_info(dev)[0]
+    per_atom = (free0 - free1) / n1
+    h.close()
+    del p, t, v
+    torch.cuda.synchronize()
+    free2 = torch.cuda.mem_get_info(dev)[0]
+    target = 0.6 * free2 / per_atom
+    # a near-cubic replica count of the 192-atom cell
+    k = max(1, int((target / 192) ** (1.0 / 3.0)))
+    reps = (k, k, max(1, int(target / (192 * k * k))))
+    p, t, v, box = make(reps)
+    n = p.shape[0]
+    h = NNP(model, device=dev.index, max_neighbors=200)
+    h.step(p, v, t, box, DT_FS, args.warmup)
+    torch.cuda.synchronize()
+    free3 = torch.cuda.mem_get_info(dev)[0]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    h.step(p, v, t, box, DT_FS, args.steps)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / args.steps
+    st = h.stats()
+    h.close()
+    return {"mode": "capacity", "device_total_GB": total / 1e9, "free_at_start_GB": free0 / 1e9,
+            "bytes_per_atom_measured": per_atom, "measured_on_atoms": n1,
+            "atoms_that_fit_estimate": int(free0 / per_atom),
+            "run": {"atoms": n, "replicas": reps, "box_A": [float(x) for x in box], "steps": args.steps,
+                    "ms_per_step": ms, "atom_steps_per_s": n / (ms * 1e-3),
+                    "device_used_GB": (free2 - free3) / 1e9, "free_left_GB": free3 / 1e9,
+                    "spilled_atoms": st["spilled_atoms"], "rc_capacity": st["rc_capacity"]}}
+
+
 def ablation_run(args, dev):
     """Force assembly, three forms on the same workload and steps: 64-bit
     fixed-point integer atomics (the default: order-independent sums, no reverse
@@ -641,7 +697,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
     ap.add_argument("--no-fcc", action="store_true", help="skip the FCC precision-form leg")
-    ap.add_argument("--mode", default="standard", choices=["standard", "combined", "domains", "ablation", "cpu"])
+    ap.add_argument("--mode", default="standard", choices=["standard", "combined", "domains", "ablation", "cpu", "capacity"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -667,6 +723,10 @@ def main():
     if args.mode == "domains":
         if rank == 0:
             print(json.dumps(domains_run(args, dev)), flush=True)
+        return
+    if args.mode == "capacity":
+        if rank == 0:
+            print(json.dumps(capacity_run(args, dev)), flush=True)
         return
     if args.mode == "cpu":
         if rank == 0:
