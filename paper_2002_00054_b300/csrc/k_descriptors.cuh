@@ -291,7 +291,7 @@ __device__ __forceinline__ void radial_g(const WarpSmem& w, const Plan& P, const
     auto rad = [&](int rr) {
         const float4 t = w.rtab[rr];
         const float x = r - t.z;
-        const float ex = gauss2_acc(t.x, t.y, x * x);
+        const float ex = gauss2(t.x, t.y, x * x);   // forces: float accuracy suffices
         gr += w.rw[rr] * ex * fmaf(t.w * x, fc, dfc);
     };
     for (int rr = 0; rr < E.rad_nall; ++rr) rad(rr);
@@ -357,26 +357,42 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
         if (keep && at < C) {
             if (r2 < 1e-8f) atomicOr(&flags[FLAG_ERR], ERR_CLOSE);
             if (!FORCE) r2min = fminf(r2min, r2);
-            // r^2 = r2h + r2l (exact to 2^-48), r = r + rl, the cutoff as fch + fcl
-            float r2h, r2l;
-            dd_norm2(dx, dy, dz, r2h, r2l);
-            const float r = sqrtf(r2h);
-            const float ir = 1.0f / r;
-            const float rl = (fmaf(-r, r, r2h) + r2l) * (0.5f * ir);
-            float fch, fcl, dfc;
-            cutoff_dd(r, rl, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, P.cs64, fch, fcl, dfc);
-            const float fc = fch + fcl;
-            // P_q = exp(-eta_q r^2) f_c: both factors as hi + lo, one final rounding
+            // ACC: the descriptor pass, and the force pass wherever the descriptor pass
+            // stores its staged values for it (narrow kind, at most 2 eta), which must
+            // then be reproduced bit for bit; other force passes need float accuracy only.
+            constexpr bool ACC = !FORCE || (N && NETA <= 2);
+            float r2h, r2l = 0.f, r, ir, rl = 0.f, fch, fcl = 0.f, dfc;
             float pq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
+            if (ACC) {
+                // r^2 = r2h + r2l (exact to 2^-48), r = r + rl, the cutoff as fch + fcl
+                dd_norm2(dx, dy, dz, r2h, r2l);
+                r = sqrtf(r2h);
+                ir = 1.0f / r;
+                rl = (fmaf(-r, r, r2h) + r2l) * (0.5f * ir);
+                cutoff_dd(r, rl, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, P.cs64, fch, fcl, dfc);
+            } else {
+                r2h = r2;
+                r = sqrtf(r2);
+                ir = 1.0f / r;
+                cutoff_fn(r, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, fch, dfc);
+            }
+            const float fc = fch + fcl;
 #pragma unroll
             for (int q = 0; q < NETA; ++q) {
-                const float ah = khi[q] * r2h;
-                const float al = fmaf(khi[q], r2h, -ah) + fmaf(klo[q], r2h, khi[q] * r2l);
-                float eh, el;
-                exp2_dd(ah, al, eh, el);
-                const float ph = eh * fch;
-                pq[q] = ph + (fmaf(eh, fch, -ph) + fmaf(eh, fcl, el * fch));
-                dq[q] = eh * (dfc - 2.0f * etav[q] * r * fc);
+                if (ACC) {
+                    // P_q = exp(-eta_q r^2) f_c: both factors as hi + lo, one final rounding
+                    const float ah = khi[q] * r2h;
+                    const float al = fmaf(khi[q], r2h, -ah) + fmaf(klo[q], r2h, khi[q] * r2l);
+                    float eh, el;
+                    exp2_dd(ah, al, eh, el);
+                    const float ph = eh * fch;
+                    pq[q] = ph + (fmaf(eh, fch, -ph) + fmaf(eh, fcl, el * fch));
+                    dq[q] = eh * (dfc - 2.0f * etav[q] * r * fc);
+                } else {
+                    const float ex = gauss2(khi[q], klo[q], r2);
+                    pq[q] = ex * fc;
+                    dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
+                }
             }
             const float hh = live_h(r2, P.rc2);
             if (!FORCE) {
@@ -758,12 +774,13 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                             } else {
                                 // wide kind, accurate b: with unit vectors, 1 - c = |u_j - u_k|^2 / 2 and
                                 // 1 + c = |u_j + u_k|^2 / 2 (times 1 + g_j + g_k for the norm defects),
-                                // each to about an ulp relative, without forming c.  The smaller of
-                                // the two is b for one lambda as it stands; the larger is 2 - the
-                                // smaller (exact subtraction; bl = its rounding, exact), which is
-                                // accurate where cos -> +-1 and b -> 2.  A power b^(2^k) amplifies b's
-                                // relative error 2^k times: the top power (zeta up to 16) gets the
-                                // first-order term 2^k bl b^(2^k - 1).
+                                // each to about an ulp of its own size, without forming c.  b = 2 -
+                                // the other one (bl = the rounding of that subtraction, exact): where
+                                // cos -> +-1 and b -> 2 the other one is small and accurate, so b is
+                                // exact to first order; a small b carries ~2 ulp absolute, which is
+                                // what its terms need in a sum dominated by b near 2.  A power
+                                // b^(2^k) amplifies b's relative error 2^k times: the top power
+                                // (zeta up to 16) gets the first-order term 2^k bl b^(2^k - 1).
                                 const float2 wx = fma2(f2(b.x, b.x), f2(-1.f, 1.f), f2(a.x, a.x));
                                 const float2 wy = fma2(f2(b.y, b.y), f2(-1.f, 1.f), f2(a.y, a.y));
                                 const float2 wz = fma2(f2(b.z, b.z), f2(-1.f, 1.f), f2(a.z, a.z));
@@ -773,12 +790,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                                 const float gg = a.w + b.w;
                                 const float2 hf = mul2(n2, f2(0.5f, 0.5f));
                                 const float2 sm = fma2(hf, f2(gg, gg), hf);              // (1 - c, 1 + c)
-                                const bool cpos = sm.x < sm.y;                           // c > 0
-                                const float small = cpos ? sm.x : sm.y;
-                                const float big = 2.0f - small;
-                                const float bigl = (2.0f - big) - small;
-                                PP[0] = cpos ? f2(big, small) : f2(small, big);         // (1 + c, 1 - c)
-                                const float2 bl = cpos ? f2(bigl, 0.f) : f2(0.f, bigl);
+                                PP[0] = fma2(sm, f2(-1.f, -1.f), f2(2.f, 2.f));          // (1 + c, 1 - c)
+                                const float2 bl = fma2(sm, f2(-1.f, -1.f), fma2(PP[0], f2(-1.f, -1.f), f2(2.f, 2.f)));
                                 float2 T = PP[0];
 #pragma unroll
                                 for (int kk = 1; kk <= KLO; ++kk) {

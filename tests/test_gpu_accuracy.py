@@ -94,15 +94,14 @@ def test_trimer_wide_angular_to_a_few_ulp(fcc, theta_deg):
             if want < 1e-30:
                 continue
             b = 1 + lam * cos
-            # Error model of a term, in ulp: 1 -/+ cos = |u_j -/+ u_k|^2 / 2 is formed to
-            # ~2.5 ulp of its own size (s_small, the smaller of the two); the larger b
-            # is 2 - s_small, so its absolute error is ~2.5 ulp x s_small, which vanishes
-            # for (anti)collinear triplets, the ones that dominate zeta = 16; the smaller
-            # b also carries the unit vectors' direction rounding, ~0.5 ulp absolute.
-            # The power multiplies b's relative error by zeta, its chain of squarings
-            # adds up to (zeta - 1)/2 ulp, and the other factors and the output ~3 ulp.
-            s_small = min(1 - cos, 1 + cos)
-            tol = 3.0 + 0.5 * z + z * 2.5 * s_small / b + (z * 0.5 / b if b < 1.0 else 0.0)
+            # Error model of a term, in ulp: b = 2 - s with s = 1 -/+ cos formed as
+            # |u_j -/+ u_k|^2 / 2 to ~2.5 ulp of its own size, so b's absolute error is
+            # ~2.5 ulp x (2 - b), which vanishes for (anti)collinear triplets, the ones
+            # that dominate zeta = 16, plus the unit vectors' direction rounding for
+            # small b (~0.5 ulp absolute).  The power multiplies b's relative error by
+            # zeta, its chain of squarings adds up to (zeta - 1)/2 ulp, and the other
+            # factors and the output ~3 ulp.
+            tol = 3.0 + 0.5 * z + z * 2.5 * (2.0 - b) / b + (z * 0.5 / b if b < 1.0 else 0.0)
             errs.append((abs(G[s] - want) / want / U, tol))
     assert len(errs) > 0
     e = np.array(errs)
