@@ -303,6 +303,23 @@ __device__ __forceinline__ void radial_g(const WarpSmem& w, const Plan& P, const
     fx_set<N>(w, 3 * at + 2, gs * dz);
 }
 
+// (r - r_s)^2 as xh + xl from a staged (r^2 hi, r^2 lo, ...) record: r^2 itself
+// for r_s = 0, else r = sqrt(r^2) as hi + lo and the square of r - r_s.
+__device__ __forceinline__ void radial_x2(const float4 nr, float rs, float& xh, float& xl)
+{
+    xh = nr.x;
+    xl = nr.y;
+    if (rs != 0.f) {
+        const float rh = sqrtf(nr.x);
+        const float rlo = (fmaf(-rh, rh, nr.x) + nr.y) * (0.5f / rh);
+        float dh, dl;
+        two_sum(rh, -rs, dh, dl);
+        dl += rlo;
+        xh = dh * dh;
+        xl = fmaf(dh, dh, -xh) + 2.0f * dh * dl;
+    }
+}
+
 // Stages the neighbours of atom i within the cutoff, compacted in list order.
 // Returns M.  FORCE: nd.w = 1/r, dP/dr, the radial part of g (into sg), slot map.
 // N: the force pass's fixed-point units (FxU<N>); in the descriptor pass, the
@@ -630,11 +647,49 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             if (qoff && lane == 0) qoff[i] = QOFF_SPILLED;
             continue;
         }
-        // radial: lane <-> descriptor (two neighbour halves when n_rad <= 16), loop over
-        // neighbours with broadcast reads; Kahan-compensated sums (they feed
-        // G~ = (G - mu)/s with |mu/s| up to ~20).  The Gaussian's argument is
-        // formed in double-float from r^2 = r2h + r2l (from (r - r_s)^2 for r_s != 0)
-        {
+        // radial.  The Gaussian's argument is formed in double-float from
+        // r^2 = r2h + r2l (from (r - r_s)^2 for r_s != 0) by radial_x2.
+        //   Every descriptor resolved by neighbour element (no element-blind ones,
+        //   at most 16): lane <-> neighbour, each lane computing only its
+        //   neighbour's element group and adding into its own row of a [32][16]
+        //   table (the pair queue's space, unused until the angular part; columns
+        //   XOR-swizzled so that a column read is conflict free), then lane <->
+        //   descriptor sums its column with Kahan compensation.
+        //   Otherwise: lane <-> descriptor (two neighbour halves when n_rad <= 16),
+        //   loop over neighbours with broadcast reads; Kahan-compensated sums (they
+        //   feed G~ = (G - mu)/s with |mu/s| up to ~20).
+        if (E.rad_nall == 0 && E.n_rad > 0 && E.n_rad <= 16) {
+            float* tab = reinterpret_cast<float*>(w.queue);
+            *reinterpret_cast<float4*>(tab + 16 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(tab + 16 * lane + 4) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(tab + 16 * lane + 8) = make_float4(0.f, 0.f, 0.f, 0.f);
+            *reinterpret_cast<float4*>(tab + 16 * lane + 12) = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int m = lane; m < M; m += 32) {
+                const float4 nr = w.nrad[m];
+                const int el = __float_as_int(nr.w);
+                for (int rr = E.rad_beg[el], re = E.rad_end[el]; rr < re; ++rr) {
+                    float xh, xl;
+                    radial_x2(nr, E.rad_rs[rr], xh, xl);
+                    const float kh = E.rad_khi[rr];
+                    const float ah = kh * xh;
+                    const float al = fmaf(kh, xh, -ah) + fmaf(E.rad_klo[rr], xh, kh * xl);
+                    tab[16 * lane + (rr ^ (lane & 15))] += exp2_acc2(ah, al) * nr.z;
+                }
+            }
+            __syncwarp();
+            if (lane < E.n_rad) {
+                float sum = 0.f, comp = 0.f;
+#pragma unroll 8
+                for (int l = 0; l < 32; ++l) {
+                    const float y = tab[16 * l + (lane ^ (l & 15))] - comp;
+                    const float t = sum + y;
+                    comp = (t - sum) - y;
+                    sum = t;
+                }
+                sG[E.rad_out[lane]] = (double)sum - (double)comp;
+            }
+            __syncwarp();
+        } else {
             const int halves = (E.n_rad <= 16) ? 2 : 1;
             const int per = 32 / halves;
             const int hf = lane / per, slot = lane % per;
@@ -648,16 +703,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 for (int m = hf; m < M; m += halves) {
                     const float4 nr = w.nrad[m];
                     if (el == -1 || el == __float_as_int(nr.w)) {
-                        float xh = nr.x, xl = nr.y;
-                        if (rs != 0.f) {
-                            const float rh = sqrtf(nr.x);
-                            const float rlo = (fmaf(-rh, rh, nr.x) + nr.y) * (0.5f / rh);
-                            float dh, dl;
-                            two_sum(rh, -rs, dh, dl);
-                            dl += rlo;
-                            xh = dh * dh;
-                            xl = fmaf(dh, dh, -xh) + 2.0f * dh * dl;
-                        }
+                        float xh, xl;
+                        radial_x2(nr, rs, xh, xl);
                         const float ah = kh * xh;
                         const float al = fmaf(kh, xh, -ah) + fmaf(kl, xh, kh * xl);
                         const float y = exp2_acc2(ah, al) * nr.z - comp;
