@@ -97,7 +97,7 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
                 float pq[4] = {0.f, 0.f, 0.f, 0.f}, dq[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                 for (int q = 0; q < NETA; ++q) {
-                    const float ex = gauss2_acc(khi[q], klo[q], r2);
+                    const float ex = gauss2(khi[q], klo[q], r2);
                     pq[q] = ex * fc;
                     dq[q] = ex * (dfc - 2.0f * etav[q] * r * fc);
                 }
@@ -122,7 +122,7 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
                 const float4 fe = nfe[m];
                 if (el < 0 || el == __float_as_int(fe.z)) {
                     const float x = nd[m].w - rs;
-                    const float ex = gauss2_acc(kh, kl, x * x);
+                    const float ex = gauss2(kh, kl, x * x);
                     acc = fmaf(ex * (fe.y - 2.0f * eta * x * fe.x), ndv[m].w, acc);
                 }
             }
