@@ -34,6 +34,11 @@ struct NbView {
     int stride;
     const int* sys_of = nullptr;      // batches: system of each atom (nullptr: one system)
     const float4* sys_box = nullptr;  // batches: box edges of each system
+    // main pass visiting order (nullptr: atom order): the atoms sorted by cell at
+    // the last list rebuild, so that the atoms a block's warps take at one time are
+    // spatial neighbours and share their neighbours' cache lines, whatever order
+    // the caller keeps its atoms in
+    const int* order = nullptr;
 };
 
 // box edges seen by atom i
@@ -58,9 +63,9 @@ __device__ __forceinline__ int atom_count(int pass, int n, const int* spill)
 {
     return pass ? spill[0] : n;
 }
-__device__ __forceinline__ int atom_at(int pass, int it, const int* spill)
+__device__ __forceinline__ int atom_at(int pass, int it, const int* spill, const int* order = nullptr)
 {
-    return pass ? spill[1 + it] : it;
+    return pass ? spill[1 + it] : (order ? order[it] : it);
 }
 // Pair-queue records.  The descriptor pass stores each atom's live-pair queue
 // (every 32 x 32 block, in walk order) so that the force pass does not rebuild
@@ -623,7 +628,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     const int nw = gridDim.x * wpb;
     const int n_items = atom_count(pass, n, spill);
     for (int it = blockIdx.x * wpb + wib; it < n_items; it += nw) {
-        const int i = atom_at(pass, it, spill);
+        const int i = atom_at(pass, it, spill, nv.order);
         const float4 pi = pos4[i];
         const int ti = __float_as_int(pi.w);
         const ElemPlan& E = P.e[ti];
@@ -1010,7 +1015,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     const int n_items = atom_count(pass, n, spill);
     unsigned long long c_spill = 0;
     for (int it = blockIdx.x * wpb + wib; it < n_items; it += nw) {
-        const int i = atom_at(pass, it, spill);
+        const int i = atom_at(pass, it, spill, nv.order);
         const float4 pi = pos4[i];
         const int ti = __float_as_int(pi.w);
         const ElemPlan& E = P.e[ti];
@@ -1037,7 +1042,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         // round, so their first reads would otherwise wait on DRAM (prefetching the
         // next atom's staged neighbours as well measured slower)
         unsigned o_next = QOFF_NONE;
-        if (staged && it + nw < n_items) o_next = qoff[atom_at(pass, it + nw, spill)];
+        if (staged && it + nw < n_items) o_next = qoff[atom_at(pass, it + nw, spill, nv.order)];
         if (staged) {
             // the descriptor pass's staging of this atom; its queue record gives M
             const unsigned o = (NETA > 0) ? qoff[i] : QOFF_NONE;

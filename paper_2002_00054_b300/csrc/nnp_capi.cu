@@ -163,6 +163,7 @@ struct nnp_handle {
     // staged neighbours written by the descriptor pass for the force pass: three
     // planes of cap_stg float4 (atom i, staged index m at i * C + m)
     bool use_stg = true;
+    bool cell_order = true;   // main passes visit atoms in cell order (NNP_CELL_ORDER=0: atom order)
     float4* stg = nullptr;
     size_t cap_stg = 0;
     // nnp_step: the per-step launch sequence captured as a CUDA graph and replayed
@@ -857,6 +858,7 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         nv.sys_of = h->sys_of;
         nv.sys_box = h->sys_box;
     }
+    if (!bt && h->cell_path && h->cell_order) nv.order = h->cell_atoms;   // atoms sorted by cell
     SfKernel ksf;
     ForceKernel kf;
     TangentKernel kt_unused;
@@ -1129,6 +1131,8 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
         // reading the descriptor pass's staged records
         const char* senv = getenv("NNP_STAGE_REUSE");
         h->use_stg = !(senv && senv[0] == '0');
+        const char* oenv = std::getenv("NNP_CELL_ORDER");
+        h->cell_order = !(oenv && oenv[0] == '0');
     }
     DeviceGuard g(device);
     auto fail = [&](int code) {

@@ -288,6 +288,24 @@ def test_thread_per_atom_descriptors(name):
     np.testing.assert_allclose(Gw, gref, rtol=2e-6, atol=0)
 
 
+def test_cell_order_visiting_is_bitwise(monkeypatch):
+    """The main passes visit atoms in cell order (default) or in atom order
+    (NNP_CELL_ORDER=0): every atom's arithmetic is its own and the force sums are
+    integers, so energies and forces are bit for bit the same, on a box whose
+    atoms are stored in a random order."""
+    from paper_2002_00054_b300 import NNP
+    m = workloads.water_model()
+    pos, types, box = workloads.water_lattice((2, 3, 2), seed=9)
+    o = np.random.default_rng(3).permutation(len(pos))
+    p, t = to_dev(f32(pos[o]), types[o])
+    a = NNP(m).compute(p, t, f32(box))
+    monkeypatch.setenv("NNP_CELL_ORDER", "0")
+    b = NNP(m).compute(p, t, f32(box))
+    assert torch.equal(a["F"], b["F"]) and torch.equal(a["Ei"], b["Ei"])
+    assert a["energy"].item() == b["energy"].item()
+    np.testing.assert_allclose(a["virial"].cpu().numpy(), b["virial"].cpu().numpy(), rtol=1e-12, atol=1e-12)
+
+
 @pytest.mark.parametrize("spill", [False, True])
 def test_staged_reuse_is_bitwise(spill, monkeypatch):
     """The force pass reads the neighbours the descriptor pass staged (same
