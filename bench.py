@@ -657,6 +657,11 @@ def ablation_run(args, dev):
     for _ in range(calls):
         h.descriptors_pair(p, t, box)
     kt_pair = h.kernel_times()
+    Gc = h.descriptors_cell(p, t, box)
+    h.profile(True)
+    for _ in range(calls):
+        h.descriptors_cell(p, t, box)
+    kt_cell = h.kernel_times()
     # neighbour-list skin: rebuild frequency against list length (list capacity
     # scaled with the neighbour sphere's volume)
     rc = float(model["cutoff"])
@@ -682,7 +687,8 @@ def ablation_run(args, dev):
     out["descriptor_parallelism"] = {
         "warp_per_atom_ms": kt["descriptors"][0] / calls, "thread_per_atom_ms": kt["descriptors_flat"][0] / calls,
         "thread_per_atom_neighbour_ms": kt_pair["descriptors_pair"][0] / calls,
-        "max_rel_difference_flat": rel(Gf), "max_rel_difference_pair": rel(Gp)}
+        "cta_per_cell_ms": kt_cell["descriptors_cell"][0] / calls,
+        "max_rel_difference_flat": rel(Gf), "max_rel_difference_pair": rel(Gp), "max_rel_difference_cell": rel(Gc)}
     h.close()
     return out
 

@@ -207,6 +207,18 @@ NNP_API int nnp_descriptors_flat(nnp_handle* h, int n_atoms, const float* pos, c
 NNP_API int nnp_descriptors_pair(nnp_handle* h, int n_atoms, const float* pos, const int* types, const double* box,
                                  float* G, void* stream);
 
+/* Raw descriptors G with one CTA per cell of the cell binning (the CTA-per-cell
+ * mapping of the parallelism ablation): the CTA copies the atoms of the cell's
+ * 27-cell stencil into shared memory once, and each of its warps finds the
+ * neighbours of one of the cell's atoms in that copy (no Verlet list) and walks
+ * all of its neighbour pairs with its lanes.  Needs at least 3 cells of
+ * cutoff + skin per box edge (NNP_EUNSUPPORTED otherwise) and at most 2,048
+ * atoms in a stencil (NNP_ENEIGH_OVERFLOW otherwise).  For the ablation;
+ * otherwise as nnp_descriptors_flat.
+ *   G  device float [n_atoms][n_G]. */
+NNP_API int nnp_descriptors_cell(nnp_handle* h, int n_atoms, const float* pos, const int* types, const double* box,
+                                 float* G, void* stream);
+
 /* n_steps velocity-Verlet NVE steps (Sec. 4.2 energy conservation):
  *   v += dt/2 F/m;  x += dt v;  F = F(x);  v += dt/2 F/m
  * pos, vel: device float [n_atoms][3], updated in place (positions are not wrapped).

@@ -57,6 +57,7 @@ SIGNATURES = {
     "nnp_descriptors": (I, [V, I, V, V, c_double_p, V, V, V]),
     "nnp_descriptors_flat": (I, [V, I, V, V, c_double_p, V, V]),
     "nnp_descriptors_pair": (I, [V, I, V, V, c_double_p, V, V]),
+    "nnp_descriptors_cell": (I, [V, I, V, V, c_double_p, V, V]),
     "nnp_step": (I, [V, I, V, V, V, c_double_p, D, I, V, V]),
     "nnp_get_stats": (I, [V, ctypes.POINTER(Stats)]),
     "nnp_profile": (I, [V, I]),

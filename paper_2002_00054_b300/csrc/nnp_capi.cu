@@ -644,9 +644,10 @@ struct DeviceGuard {
     }
 };
 
-enum { KG_NEIGH = 0, KG_SF, KG_MLP, KG_FORCE, KG_GATHER, KG_REDUCE, KG_INTEGRATE, KG_FLAT, KG_PAIR, KG_N };
+enum { KG_NEIGH = 0, KG_SF, KG_MLP, KG_FORCE, KG_GATHER, KG_REDUCE, KG_INTEGRATE, KG_FLAT, KG_PAIR, KG_CELL, KG_N };
 static const char* kKgName[KG_N] = {"neighbor_maintenance", "descriptors", "network", "force", "gather",
-                                    "reductions", "integrate", "descriptors_flat", "descriptors_pair"};
+                                    "reductions", "integrate", "descriptors_flat", "descriptors_pair",
+                                    "descriptors_cell"};
 static_assert(KG_N <= 16, "kernel-group timers hold 16 groups");
 
 static cudaEvent_t ev_get(nnp_handle* h)
@@ -1203,6 +1204,8 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
         CKC(cudaFuncSetAttribute((const void*)fs3, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     }
     CKC(cudaFuncSetAttribute((const void*)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+    CKC(cudaFuncSetAttribute((const void*)k_sf_cell, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sf_cell_smem_bytes(4)));
     CKC(cudaFuncSetAttribute((const void*)h->kmlp, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     if (h->precision == NNP_BF16) {
         auto r16 = [](int x) { return (x + 15) & ~15; };
@@ -1421,6 +1424,38 @@ int nnp_descriptors_pair(nnp_handle* h, int n, const float* pos, const int* type
         const long long items = (long long)n * h->stride;
         const int grid = (int)std::min<long long>((items + 127) / 128, (long long)h->num_sms * 16);
         k_sf_pair<<<grid, 128, 0, st>>>(n, h->pos4, bx, nv, h->d_plan, G, h->flags);
+    }
+    return read_status(h, st);
+}
+
+int nnp_descriptors_cell(nnp_handle* h, int n, const float* pos, const int* types, const double* box, float* G,
+                         void* stream)
+{
+    if (!h) return NNP_EINVAL;
+    h->err.clear();
+    if (!G) return set_err(h, NNP_EINVAL, "G must not be NULL");
+    if (h->plan.resolved)
+        return set_err(h, NNP_EUNSUPPORTED, "the CTA-per-cell descriptors do not resolve angular pair classes");
+    int rc = common_args(h, n, pos, types, box);
+    if (rc) return rc;
+    if (n == 0) return NNP_OK;
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    h->step_valid = false;
+    rc = begin_call(h, st);
+    if (rc) return rc;
+    // neighbour list and cell binning (and the warp-per-atom pass, not returned)
+    rc = run_eval(h, n, pos, types, box, st, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, 1);
+    if (rc) return rc;
+    if (!h->cell_path)
+        return set_err(h, NNP_EUNSUPPORTED, "the CTA-per-cell descriptors need at least 3 cells of cutoff + skin per edge");
+    Box bx;
+    for (int a = 0; a < 3; ++a) bx.L[a] = (float)box[a];
+    {
+        KScope ks(h, KG_CELL, st);
+        const int ncell = h->nc[0] * h->nc[1] * h->nc[2];
+        k_sf_cell<<<std::min(ncell, h->num_sms * 4), 128, sf_cell_smem_bytes(4), st>>>(
+            h->nc[0], h->nc[1], h->nc[2], h->pos4, bx, h->cell_start, h->cell_atoms, h->d_plan, G, h->flags);
     }
     return read_status(h, st);
 }

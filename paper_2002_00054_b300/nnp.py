@@ -180,6 +180,17 @@ class NNP:
         self._check(self._lib.nnp_descriptors_pair(self.h, n, _ptr(pos), _ptr(types), bp, _ptr(G), _stream(stream)))
         return G
 
+    def descriptors_cell(self, pos, types, box, stream=None):
+        """Raw descriptors G with one CTA per cell, neighbours found in a shared
+        copy of the cell's stencil (the CTA-per-cell level of the ablation)."""
+        n = int(pos.shape[0])
+        _need(pos, torch.float32, (n, 3), "pos", self.device)
+        _need(types, torch.int32, (n,), "types", self.device)
+        G = torch.empty((n, self.n_g), dtype=torch.float32, device=torch.device("cuda", self.device))
+        b, bp = self._box(box)
+        self._check(self._lib.nnp_descriptors_cell(self.h, n, _ptr(pos), _ptr(types), bp, _ptr(G), _stream(stream)))
+        return G
+
     def step(self, pos, vel, types, box, dt, n_steps, log=True, stream=None):
         """n_steps velocity-Verlet steps in place; returns the (PE, KE) log [n_steps+1, 2] (fp64)."""
         n = int(pos.shape[0])

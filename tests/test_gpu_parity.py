@@ -264,10 +264,11 @@ def test_force_assembly_forms_agree(name, form, monkeypatch):
 
 @pytest.mark.parametrize("name", ["water", "fcc"])
 def test_thread_per_atom_descriptors(name):
-    """The other parallelism levels of the ablation (Fig. 6): one thread per atom,
-    and one thread per (atom, neighbour) with atomic updates of G_i, give the
-    raw G of the oracle (and of the warp-per-atom kernel) to FP32 summation
-    order (plain float sums over ~2000 triplets per atom)."""
+    """The other mappings of the parallelism ablation (Fig. 6): one thread per
+    atom, one thread per (atom, neighbour) with atomic updates of G_i, and one
+    CTA per cell with the stencil staged in shared memory, give the raw G of the
+    oracle (and of the warp-per-atom kernel) to FP32 summation order (plain
+    float sums over ~2000 triplets per atom)."""
     from paper_2002_00054_b300 import NNP
     if name == "water":
         m, (pos, types, box) = workloads.water_model(), workloads.water_lattice((2, 2, 2), seed=7)
@@ -278,6 +279,7 @@ def test_thread_per_atom_descriptors(name):
     nnp = NNP(m)
     Gf = nnp.descriptors_flat(p, t, box).double().cpu().numpy()
     Gp = nnp.descriptors_pair(p, t, box).double().cpu().numpy()
+    Gc = nnp.descriptors_cell(p, t, box).double().cpu().numpy()
     Gw, _ = nnp.descriptors(p, t, box, dEdG=False)
     Gw = Gw.double().cpu().numpy()
     ng = Gw.shape[1]
@@ -285,6 +287,7 @@ def test_thread_per_atom_descriptors(name):
     # plain float sums in both ablation kernels: element by element to ~1e-5
     np.testing.assert_allclose(Gf, gref, rtol=1e-5, atol=0)
     np.testing.assert_allclose(Gp, gref, rtol=1e-5, atol=0)
+    np.testing.assert_allclose(Gc, gref, rtol=1e-5, atol=0)
     np.testing.assert_allclose(Gw, gref, rtol=2e-6, atol=0)
 
 
