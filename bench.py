@@ -57,8 +57,8 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # profiles/ (a 2M-atom launch moves the same bytes per atom: list rows,
 # positions, pair-queue and staged-neighbour records all scale with atoms).
 # Valid only for the kernel sources with this hash; otherwise traffic is null.
-TRAFFIC = {"force": (911.896832e6 + 6.448128e6) / 110592, "descriptors": (90.58176e6 + 785.458688e6) / 110592}
-TRAFFIC_SRC_SHA = "9ed18cbef270"
+TRAFFIC = {"force": (912.177664e6 + 5.734656e6) / 110592, "descriptors": (90.822144e6 + 785.412096e6) / 110592}
+TRAFFIC_SRC_SHA = "22f579869d42"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
