@@ -52,7 +52,9 @@ __device__ __forceinline__ void atom_box(const NbView& nv, const Box& bx, int i,
     }
 }
 
-#define PAIR_QUEUE 1024   // live pairs of one 32 x 32 block, as (l | s << 5)
+// Live pairs waiting in a warp's queue: up to 31 left over from earlier block
+// pairs, the up to 1024 of one 32 x 32 block, and the 16-byte copy granule.
+#define PAIR_QUEUE 1088
 
 // Atoms with more neighbours inside the cutoff than the shared-memory capacity C
 // of the main launch.  The descriptor kernel's main pass (pass 0) appends them to
@@ -68,14 +70,14 @@ __device__ __forceinline__ int atom_at(int pass, int it, const int* spill, const
     return pass ? spill[1 + it] : (order ? order[it] : it);
 }
 // Pair-queue records.  The descriptor pass stores each atom's live-pair queue
-// (every 32 x 32 block, in walk order) so that the force pass does not rebuild
-// it.  Record layout (u16): M, the staging fingerprint (2 words), 0, one total
-// per block pair, then from the next multiple of 8 the entries of each block,
-// each block padded to a multiple of 8 (16-byte vector stores).  Records are
-// 8-entry aligned and addressed by qoff[i] = offset / 8 (QOFF_NONE: not stored;
-// the force pass rebuilds the queue).  Each warp claims chunks of QCHUNK
-// entries of the pool with one atomic; the pool counter also records the
-// demand when the pool is too small.
+// (every 32 x 32 block pair, in walk order) so that the force pass does not
+// rebuild it.  Record layout (u16): M, the staging fingerprint (2 words), the
+// number of entries, one count per block pair, then from the next multiple of 8
+// the entries of all block pairs back to back, each entry j | k << 8 (so records
+// exist only for M <= 256).  Records are 8-entry aligned and addressed by
+// qoff[i] = offset / 8 (QOFF_NONE: not stored; the force pass rebuilds the
+// queue).  Each warp claims chunks of QCHUNK entries of the pool with one
+// atomic; the pool counter also records the demand when the pool is too small.
 #define QOFF_NONE 0xffffffffu
 #define QOFF_SPILLED 0xfffffffeu   // not stored: already queued for the wide-capacity pass
 #define QCHUNK 65536ull
@@ -332,13 +334,21 @@ __device__ __forceinline__ void radial_x2(const float4 nr, float rs, float& xh, 
 // Both passes compute r, 1/r, f_c, f_c', P_q and dP_q/dr from the same
 // double-float intermediates (|d|^2, r, the cutoff's cos), so the staged values
 // the descriptor pass writes for the force pass are bitwise the force pass's own.
+// Two sweeps: the list entries (lanes over list slots) select the neighbours
+// inside the cutoff and park their displacement, element and atom index at their
+// compact position; the per-neighbour functions then run with lanes over the
+// compacted neighbours (about 60 % of the list entries lie inside the cutoff, so
+// the costly part takes ceil(M/32) rounds instead of ceil(n_list/32)).
+// rtab (descriptor pass; nullptr: not fused): the radial descriptors resolved by
+// neighbour element, at most 16, summed per lane into row `lane` of a [32][16]
+// table, columns XOR-swizzled by (lane & 15); the caller sums the columns.
 template <int NETA, bool FORCE, bool N = false>
 __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box& bx, const NbView& nv,
                                                const float4* __restrict__ pos4, const Plan& P, const ElemPlan& E,
                                                const float* khi, const float* klo, const float* etav, int C,
                                                const WarpSmem& w, const float* sW, int lane, int* flags, int& n_list,
                                                unsigned& sig, float& r2min, float4* __restrict__ stg = nullptr,
-                                               size_t stg_plane = 0)
+                                               size_t stg_plane = 0, float* rtab = nullptr)
 {
     const int cnt = nv.ncount[i];
     n_list = cnt;
@@ -361,7 +371,6 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
         e_nn = (s + 64 < cnt) ? row[s + 64] : 0u;
         bool keep = false;
         float dx = 0.f, dy = 0.f, dz = 0.f, r2 = 0.f;
-        int ej = 0;
         if (s < cnt) {
             float ox, oy, oz;
             nb_shift(e, Lx, Ly, Lz, ox, oy, oz);
@@ -369,7 +378,6 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
             dy = pair_disp(pj.y, pi.y, oy);
             dz = pair_disp(pj.z, pi.z, oz);
             r2 = dist2_fma(dx, dy, dz);   // explicit roundings: every pass keeps the same neighbours
-            ej = __float_as_int(pj.w);
             keep = r2 < P.rc2;
         }
         const unsigned m = __ballot_sync(FULL, keep);
@@ -379,6 +387,25 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
         if (keep && at < C) {
             if (r2 < 1e-8f) atomicOr(&flags[FLAG_ERR], ERR_CLOSE);
             if (!FORCE) r2min = fminf(r2min, r2);
+            // parked until the second sweep: (d, element) and the atom index
+            w.nd[at] = make_float4(dx, dy, dz, pj.w);
+            reinterpret_cast<uint32_t*>(w.npf + at)[3] = e & NB_INDEX_MASK;
+        }
+        M += __popc(m);
+    }
+    __syncwarp();
+    if (rtab) {
+        float4* t4 = reinterpret_cast<float4*>(rtab + 16 * lane);
+        t4[0] = t4[1] = t4[2] = t4[3] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const int Mc = M < C ? M : C;
+    for (int at = lane; at < Mc; at += 32) {
+        const float4 pk = w.nd[at];
+        const uint32_t aidx = reinterpret_cast<const uint32_t*>(w.npf + at)[3];
+        const float dx = pk.x, dy = pk.y, dz = pk.z;
+        const int ej = __float_as_int(pk.w);
+        const float r2 = dist2_fma(dx, dy, dz);   // the first sweep's value, bit for bit
+        {
             // ACC: the descriptor pass, and the force pass wherever the descriptor pass
             // stores its staged values for it (narrow kind, at most 2 eta), which must
             // then be reproduced bit for bit; other force passes need float accuracy only.
@@ -436,6 +463,19 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                     w.nd[at] = make_float4(ux, uy, uz, 0.5f * ((1.0f - sh) - sl));
                 }
                 w.nrad[at] = make_float4(r2h, r2l, fc, __int_as_float(ej));
+                if (rtab) {
+                    // the Gaussian's argument in double-float from r^2 = r2h + r2l (r_s = 0
+                    // here, else (r - r_s)^2 by radial_x2)
+                    const float4 nr = make_float4(r2h, r2l, fc, 0.f);
+                    for (int rr = E.rad_beg[ej], re = E.rad_end[ej]; rr < re; ++rr) {
+                        float xh, xl;
+                        radial_x2(nr, E.rad_rs[rr], xh, xl);
+                        const float kh = E.rad_khi[rr];
+                        const float ah = kh * xh;
+                        const float al = fmaf(kh, xh, -ah) + fmaf(E.rad_klo[rr], xh, kh * xl);
+                        rtab[16 * lane + (rr ^ (lane & 15))] += exp2_acc2(ah, al) * fc;
+                    }
+                }
             } else {
                 w.nd[at] = make_float4(dx, dy, dz, ir);
                 if (w.nh) w.nh[at] = hh;
@@ -455,10 +495,9 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                 stg[idx] = make_float4(dx, dy, dz, ir);
                 stg[stg_plane + idx] = make_float4(pq[0], pq[1], dq[0], dq[1]);
                 stg[2 * stg_plane + idx] =
-                    make_float4(r, fc, dfc, __int_as_float((int)((e & NB_INDEX_MASK) | ((uint32_t)ej << 24))));
+                    make_float4(r, fc, dfc, __int_as_float((int)(aidx | ((uint32_t)ej << 24))));
             }
         }
-        M += __popc(m);
     }
     __syncwarp();
     return M;
@@ -554,12 +593,33 @@ __device__ __forceinline__ unsigned transpose32(unsigned m, int lane)
     return m;
 }
 
+// Column s of the transposed block for lane `lane`: lane s holds partner step s.
+// The diagonal block uses steps 1..16 only: there lane s keeps the pairs with
+// l < 16 and lane s + 16 those with l >= 16 of step s (s < 16), so that 31 lanes
+// share the writes instead of 16.  Returns the column bits (bit l) and sets s.
+__device__ __forceinline__ unsigned block_column(unsigned mask, int lane, bool diag, int& s)
+{
+    unsigned col = transpose32(mask, lane);
+    s = lane;
+    if (diag) {
+        const unsigned o = __shfl_sync(FULL, col, lane & 15);
+        if (lane > 16) {
+            col = o & 0xffff0000u;
+            s = lane - 16;
+        } else {
+            col &= 0x0000ffffu;   // lane 16: step 16 has l < 16 only; lane 0: no step 0
+        }
+    }
+    return col;
+}
+
 // Writes the live pairs (l, s) of one block, s-major, into the warp queue and
 // returns their number.  Consecutive entries share s, so j and k are distinct
 // across the lanes of a batch of 32 (up to where the batch crosses an s boundary).
-__device__ __forceinline__ int enqueue_block(unsigned mask, int lane, unsigned short* queue)
+__device__ __forceinline__ int enqueue_block(unsigned mask, int lane, unsigned short* queue, bool diag)
 {
-    unsigned col = transpose32(mask, lane);
+    int s;
+    unsigned col = block_column(mask, lane, diag, s);
     const int cnt = __popc(col);
     int off = cnt;   // inclusive scan over lanes
 #pragma unroll
@@ -572,7 +632,36 @@ __device__ __forceinline__ int enqueue_block(unsigned mask, int lane, unsigned s
     while (col) {
         const int l = __ffs(col) - 1;
         col &= col - 1u;
-        queue[off++] = (unsigned short)(l | (lane << 5));
+        queue[off++] = (unsigned short)(l | (s << 5));
+    }
+    __syncwarp();
+    return total;
+}
+
+// The same, with each entry written as the neighbour pair itself, j | k << 8
+// (j = jb + l, k = kb + (l + s) mod 32; staged indices below 256), so that the
+// entries of several block pairs can share one queue.
+__device__ __forceinline__ int enqueue_block_jk(unsigned mask, int lane, unsigned short* queue, int jb, int kb)
+{
+    int s;
+    unsigned col = block_column(mask, lane, jb == kb, s);
+    const int cnt = __popc(col);
+    int off = cnt;   // inclusive scan over lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(FULL, off, o);
+        if (lane >= o) off += t;
+    }
+    const int total = __shfl_sync(FULL, off, 31);
+    off -= cnt;
+    // entry l of column s pairs j = jb + l with k = kb + ((l + s) & 31): with
+    // x = (jb + l) + ((s + l) << 8), bit 13 of x is the carry of s + l past 31,
+    // and kb (a multiple of 32) fills bits 13..15
+    const int js = jb + (s << 8), kb8 = kb << 8;
+    while (col) {
+        const int l = __ffs(col) - 1;
+        col &= col - 1u;
+        queue[off++] = (unsigned short)(((l * 257 + js) & ~0x2000) | kb8);
     }
     __syncwarp();
     return total;
@@ -583,7 +672,7 @@ __device__ __forceinline__ int enqueue_block(unsigned mask, int lane, unsigned s
 // terms beyond them are compiled out.
 // RES: angular descriptors resolved by neighbour-element pair (one pass over
 // the pairs per class).
-template <int NETA, bool NARROW, int KP, int KN, bool RES>
+template <int NETA, bool NARROW, int KP, int KN, bool RES, bool MG>
 __global__ void __launch_bounds__(128, 6)
 k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __restrict__ plan_g,
      int C, float* __restrict__ Gs, float* __restrict__ Graw, int* __restrict__ flags,
@@ -642,8 +731,13 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         int n_list;
         unsigned sig;
         float r2_atom = INFINITY;
+        // radial descriptors all resolved by neighbour element (none element-blind,
+        // at most 16): summed during the staging, lanes over neighbours, into a
+        // [32][16] table in the pair queue's space (unused until the angular part)
+        const bool rad_tab = E.rad_nall == 0 && E.n_rad > 0 && E.n_rad <= 16;
         const int M = stage_neighbors<NETA, false, NARROW>(i, pi, bx, nv, pos4, P, E, khi, klo, etav, C, w, nullptr, lane,
-                                                   flags, n_list, sig, r2_atom, pass == 0 ? stg : nullptr, stg_plane);
+                                                   flags, n_list, sig, r2_atom, pass == 0 ? stg : nullptr, stg_plane,
+                                                   rad_tab ? reinterpret_cast<float*>(w.queue) : nullptr);
         // closest staged neighbour: kept per warp in shared memory, not in a register
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) r2_atom = fminf(r2_atom, __shfl_xor_sync(FULL, r2_atom, o));
@@ -654,34 +748,14 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         }
         // radial.  The Gaussian's argument is formed in double-float from
         // r^2 = r2h + r2l (from (r - r_s)^2 for r_s != 0) by radial_x2.
-        //   Every descriptor resolved by neighbour element (no element-blind ones,
-        //   at most 16): lane <-> neighbour, each lane computing only its
-        //   neighbour's element group and adding into its own row of a [32][16]
-        //   table (the pair queue's space, unused until the angular part; columns
-        //   XOR-swizzled so that a column read is conflict free), then lane <->
-        //   descriptor sums its column with Kahan compensation.
+        //   Table (see above): lane <-> descriptor sums its column with Kahan
+        //   compensation (the columns are XOR-swizzled, so a column read is
+        //   conflict free).
         //   Otherwise: lane <-> descriptor (two neighbour halves when n_rad <= 16),
         //   loop over neighbours with broadcast reads; Kahan-compensated sums (they
         //   feed G~ = (G - mu)/s with |mu/s| up to ~20).
-        if (E.rad_nall == 0 && E.n_rad > 0 && E.n_rad <= 16) {
-            float* tab = reinterpret_cast<float*>(w.queue);
-            *reinterpret_cast<float4*>(tab + 16 * lane) = make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<float4*>(tab + 16 * lane + 4) = make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<float4*>(tab + 16 * lane + 8) = make_float4(0.f, 0.f, 0.f, 0.f);
-            *reinterpret_cast<float4*>(tab + 16 * lane + 12) = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int m = lane; m < M; m += 32) {
-                const float4 nr = w.nrad[m];
-                const int el = __float_as_int(nr.w);
-                for (int rr = E.rad_beg[el], re = E.rad_end[el]; rr < re; ++rr) {
-                    float xh, xl;
-                    radial_x2(nr, E.rad_rs[rr], xh, xl);
-                    const float kh = E.rad_khi[rr];
-                    const float ah = kh * xh;
-                    const float al = fmaf(kh, xh, -ah) + fmaf(E.rad_klo[rr], xh, kh * xl);
-                    tab[16 * lane + (rr ^ (lane & 15))] += exp2_acc2(ah, al) * nr.z;
-                }
-            }
-            __syncwarp();
+        if (rad_tab) {
+            const float* tab = reinterpret_cast<const float*>(w.queue);
             if (lane < E.n_rad) {
                 float sum = 0.f, comp = 0.f;
 #pragma unroll 8
@@ -752,7 +826,10 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
             const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             // where this atom's queue record goes (nullptr: not stored)
             unsigned short* rec = nullptr;
-            if (!RES && NARROW && qcan) {
+            // MG (capacity C <= 256, staged indices in 8 bits): the block pairs share
+            // one queue (entries j | k << 8); otherwise one block pair at a time
+            constexpr bool merged = MG;
+            if (!RES && NARROW && qcan && merged) {
                 const unsigned need8 = (unsigned)((queue_record_bound(M) + 7) >> 3);
                 if (qend - qcur < need8) {
                     const unsigned long long sz = (need8 > QCHUNK / 8 ? need8 : QCHUNK / 8) * 8ull;
@@ -774,9 +851,11 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 rec[0] = (unsigned short)M;
                 rec[1] = (unsigned short)(sig & 0xffffu);
                 rec[2] = (unsigned short)(sig >> 16);
-                rec[3] = 0;
             }
-            int bp = QHDR, qpos = queue_entries_start(nb);
+            // pend: entries waiting in the queue; done: entries taken so far (a
+            // multiple of 32 until the last block pair), the record position of queue[0]
+            int bp = QHDR, pend = 0, done = 0;
+            const int q0 = queue_entries_start(nb);
             for (int A = 0; A < nb; ++A) {
                 const int jl = 32 * A + lane;
                 const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -788,21 +867,35 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                         const int kl = 32 * B + lane;
                         mask &= class_mask(ej, kl < M ? __float_as_int(w.nrad[kl].w) : -1, ce1, ce2, lane);
                     }
-                    const int total = enqueue_block(mask, lane, w.queue);
+                    const int total = merged ? enqueue_block_jk(mask, lane, w.queue + pend, 32 * A, 32 * B)
+                                             : enqueue_block(mask, lane, w.queue, A == B);
                     if (rec) {
-                        const int n8 = (total + 7) >> 3;   // 8 entries per 16-byte store
+                        // 16-byte copies of queue[pend, pend + total) rounded out to 8 entries:
+                        // the first rewrites stored entries with their own values, the last
+                        // runs past the end into space the next copy (or nothing) reuses
+                        const int v0 = pend >> 3, v1 = (pend + total + 7) >> 3;
                         const uint4* src = reinterpret_cast<const uint4*>(w.queue);
-                        uint4* dst = reinterpret_cast<uint4*>(rec + qpos);
-                        for (int v = lane; v < n8; v += 32) dst[v] = src[v];
+                        uint4* dst = reinterpret_cast<uint4*>(rec + q0 + done);
+                        for (int v = v0 + lane; v < v1; v += 32) dst[v] = src[v];
                         if (lane == 0) rec[bp] = (unsigned short)total;
-                        qpos += n8 * 8;
                     }
-                    for (int e0 = 0; e0 < total; e0 += 32) {
+                    // take every full batch of 32 (everything at the last block pair, or
+                    // one block pair at a time); the rest waits for the next block pair
+                    const int avail = pend + total;
+                    const int take = (merged && !(A == nb - 1 && B == nb - 1)) ? (avail & ~31) : avail;
+                    for (int e0 = 0; e0 < take; e0 += 32) {
                         const int e = e0 + lane;
-                        if (e < total) {
+                        if (e < take) {
                             const int ent = w.queue[e];
-                            const int l = ent & 31, sidx = ent >> 5;
-                            const int j = 32 * A + l, k = 32 * B + ((l + sidx) & 31);
+                            int j, k;
+                            if (merged) {
+                                j = ent & 255;
+                                k = ent >> 8;
+                            } else {
+                                const int l = ent & 31, sidx = ent >> 5;
+                                j = 32 * A + l;
+                                k = 32 * B + ((l + sidx) & 31);
+                            }
                             const float4 a = w.nd[j], b = w.nd[k];
                             const float4 pa4 = w.npf[j], pb4 = w.npf[k];
                             const float2 PA[2] = {f2(pa4.x, pa4.y), f2(pa4.z, pa4.w)};
@@ -901,8 +994,17 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                         }
                     }
                     __syncwarp();
+                    // the leftover (fewer than 32) moves to the front of the queue
+                    const int left = avail - take;
+                    const unsigned short lv = (lane < left) ? w.queue[take + lane] : (unsigned short)0;
+                    __syncwarp();
+                    if (lane < left) w.queue[lane] = lv;
+                    __syncwarp();
+                    pend = left;
+                    done += take;
                 }
             }
+            if (rec && lane == 0) rec[3] = (unsigned short)done;
             // lane partials: compensated reduce-scatter, lane t gets accumulator 32c + t;
             // prefactor 2^(1 - zeta), zeta = 2^k
 #pragma unroll
@@ -928,7 +1030,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 }
             }
             if (cls == 0 && lane == 2) cnt += (unsigned long long)M * (M - 1) / 2;
-            if (rec) qcur += (unsigned)(qpos >> 3);   // qpos is a multiple of 8
+            if (rec) qcur += (unsigned)((q0 + done + 7) >> 3);   // q0 is a multiple of 8
         }
         if (NETA == 0 && qoff && lane == 0) qoff[i] = QOFF_NONE;
         __syncwarp();
@@ -1179,25 +1281,28 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 D0[p] = add2(WPp[p][0], mul2(WPm[p][0], f2(-1.f, -1.f)));
             }
             const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
-            int bp = QHDR, qpos = queue_entries_start(nb);
-            for (int A = 0; A < nb; ++A) {
+            // STORED: one sweep over the record's entries (every block pair, back to
+            // back, as j | k << 8); otherwise one 32 x 32 block pair at a time.
+            // bend: record position where block pair bp ends (carries, below)
+            const int nbp = nb * (nb + 1) / 2;
+            int bp = QHDR, bend = STORED ? (int)rec[QHDR] : 0;
+            for (int A = 0; A < (STORED ? 1 : nb); ++A) {
                 const int jl = 32 * A + lane;
                 const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
                 const int ej = (RES && jl < M) ? (int)w.nel[jl] : -1;
-                for (int B = A; B < nb; ++B, ++bp) {
+                for (int B = A; B < (STORED ? 1 : nb); ++B) {
                     int total;
                     const unsigned short* qsrc;
                     if (STORED) {
-                        total = rec[bp];
-                        qsrc = rec + qpos;
-                        qpos += (total + 7) & ~7;
+                        total = rec[3];
+                        qsrc = rec + queue_entries_start(nb);
                     } else {
                         unsigned mask = live_mask<NARROW, 1>(A, B, lane, M, al, (jl < M) ? w.nh[jl] : 0.f, w.nd, w.nh);
                         if (RES && ce1 >= 0) {
                             const int kl = 32 * B + lane;
                             mask &= class_mask(ej, kl < M ? (int)w.nel[kl] : -1, ce1, ce2, lane);
                         }
-                        total = enqueue_block(mask, lane, w.queue);
+                        total = enqueue_block(mask, lane, w.queue, A == B);
                         qsrc = w.queue;
                     }
                     // stored queues come from global memory: load one round ahead
@@ -1210,9 +1315,16 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             ent_next = (e + 32 < total) ? qsrc[e + 32] : 0;
                         }
                         if (e < total) {
-                            if (!STORED) ent = qsrc[e];
-                            const int l = ent & 31, s = ent >> 5;
-                            const int j = 32 * A + l, k = 32 * B + ((l + s) & 31);
+                            int j, k;
+                            if (STORED) {
+                                j = ent & 255;
+                                k = ent >> 8;
+                            } else {
+                                ent = qsrc[e];
+                                const int l = ent & 31, s = ent >> 5;
+                                j = 32 * A + l;
+                                k = 32 * B + ((l + s) & 31);
+                            }
                             const float4 a = w.nd[j], b = w.nd[k];
                             const float ia = a.w, ib = b.w;
                             // P_q and dP_q/dr of both neighbours as eta pairs (zero past NETA)
@@ -1402,9 +1514,24 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             }
                             }
                         }
+                        if (STORED && FxU<NARROW>::CARRY && nb > 3 && bend <= e0 + 32) {
+                            // a block pair ended in this batch: unless it was the last, carry
+                            // every slot.  A block pair adds at most 32 times into a slot, and
+                            // the batches since the previous carry hold one block pair's
+                            // entries and then at most 32 more: 64 adds of |lo| <= 2^24 and
+                            // the residue below 2^25 stay below 2^31.
+                            while (bp < QHDR + nbp - 1 && bend <= e0 + 32) bend += rec[++bp];
+                            if (bend <= e0 + 32) {
+                                bend = 0x7fffffff;
+                            } else {
+                                __syncwarp();
+                                for (int t = lane; t < 3 * M; t += 32) fx_carry<NARROW>(w, t);
+                                __syncwarp();
+                            }
+                        }
                     }
                     __syncwarp();
-                    if (FxU<NARROW>::CARRY && nb > 3) {
+                    if (!STORED && FxU<NARROW>::CARRY && nb > 3) {
                         // the slots of blocks A and B took at most 32 adds each: carry.
                         // With at most 3 blocks a slot meets at most 3 block pairs: 96 adds
                         // of |lo| <= 2^24 and the radial value stay below 2^31 uncarried.

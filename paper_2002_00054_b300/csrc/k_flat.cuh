@@ -218,7 +218,7 @@ k_sf_cell(int ncx, int ncy, int ncz, const float4* __restrict__ pos4, Box bx, co
     float4* nd = reinterpret_cast<float4*>(smem_cell + (size_t)CELL_STENCIL_CAP * 16) + (size_t)wib * CELL_NB_CAP;
     float2* nfe = reinterpret_cast<float2*>(smem_cell + (size_t)CELL_STENCIL_CAP * 16 + (size_t)wpb * CELL_NB_CAP * 16) +
                   (size_t)wib * CELL_NB_CAP;
-    __shared__ int s_cell[27], s_beg[27], s_cnt[27], s_pre[28];
+    __shared__ int s_beg[27], s_cnt[27], s_pre[28];
     __shared__ float s_sh[27][3];
     const bool narrow = P.ang_kind == NNP_SF_ANG_NARROW;
     const int ncell = ncx * ncy * ncz;
@@ -232,7 +232,6 @@ k_sf_cell(int ncx, int ncy, int ncz, const float4* __restrict__ pos4, Box bx, co
             if (y < 0) { y += ncy; sy = -bx.L[1]; } else if (y >= ncy) { y -= ncy; sy = bx.L[1]; }
             if (z < 0) { z += ncz; sz = -bx.L[2]; } else if (z >= ncz) { z -= ncz; sz = bx.L[2]; }
             const int cc = (z * ncy + y) * ncx + x;
-            s_cell[t] = cc;
             s_beg[t] = cell_start[cc];
             s_cnt[t] = cell_start[cc + 1] - cell_start[cc];
             s_sh[t][0] = sx; s_sh[t][1] = sy; s_sh[t][2] = sz;

@@ -161,7 +161,7 @@ k_tangent(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan*
                         const int kl = 32 * B + lane;
                         mask &= class_mask(ej, kl < M ? __float_as_int(nfe[kl].z) : -1, ce1, ce2, lane);
                     }
-                    const int total = enqueue_block(mask, lane, queue);
+                    const int total = enqueue_block(mask, lane, queue, A == B);
                     for (int e0 = 0; e0 < total; e0 += 32) {
                         const int e = e0 + lane;
                         if (e >= total) continue;

@@ -403,10 +403,16 @@ typedef void (*ForceKernel)(int, const float4*, Box, NbView, const Plan*, int, c
 
 typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int, const float*, float*, int*, int*, int);
 
+// The descriptor kernel in two forms: up to SF_MERGED_MAX staged neighbours
+// (indices in 8 bits) the block pairs of an atom share one pair queue and the
+// pair-queue records exist; beyond, one block pair at a time (sf_for).
+#define SF_MERGED_MAX 256
+
 template <int NETA, bool NARROW, int KP, int KN, bool RES = false>
-static void pick(SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs)
+static void pick(SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs, SfKernel& sw)
 {
-    s = k_sf<NETA, NARROW, KP, KN, RES>;
+    s = k_sf<NETA, NARROW, KP, KN, RES, true>;
+    sw = k_sf<NETA, NARROW, KP, KN, RES, false>;
     f = k_force<NETA, NARROW, KP, KN, false, RES>;
     t = k_tangent<NETA, NARROW, KP, KN, RES>;
     if constexpr (RES) fs = f;   // resolved models do not store pair queues
@@ -429,34 +435,49 @@ static int kmax_of(const Plan& P, int l)
 // eta, lambda +1 up to zeta 16, lambda -1 up to zeta 4) and FCC-like (wide,
 // three eta, both lambda up to zeta 16) models; every other set runs the
 // generic instantiation with all powers up to zeta 16.
-static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs)
+static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs,
+                         SfKernel& sw)
 {
     const bool nar = (P.ang_kind == NNP_SF_ANG_NARROW);
     const int kp = kmax_of(P, 0), kn = kmax_of(P, 1);
     if (P.resolved) {
         // angular descriptors resolved by neighbour-element pair: generic terms
         switch (P.n_eta_max) {
-        case 1: if (nar) pick<1, true, 4, 4, true>(s, f, t, fs); else pick<1, false, 4, 4, true>(s, f, t, fs); break;
-        case 2: if (nar) pick<2, true, 4, 4, true>(s, f, t, fs); else pick<2, false, 4, 4, true>(s, f, t, fs); break;
-        case 3: if (nar) pick<3, true, 4, 4, true>(s, f, t, fs); else pick<3, false, 4, 4, true>(s, f, t, fs); break;
-        default: if (nar) pick<4, true, 4, 4, true>(s, f, t, fs); else pick<4, false, 4, 4, true>(s, f, t, fs); break;
+        case 1: if (nar) pick<1, true, 4, 4, true>(s, f, t, fs, sw); else pick<1, false, 4, 4, true>(s, f, t, fs, sw); break;
+        case 2: if (nar) pick<2, true, 4, 4, true>(s, f, t, fs, sw); else pick<2, false, 4, 4, true>(s, f, t, fs, sw); break;
+        case 3: if (nar) pick<3, true, 4, 4, true>(s, f, t, fs, sw); else pick<3, false, 4, 4, true>(s, f, t, fs, sw); break;
+        default: if (nar) pick<4, true, 4, 4, true>(s, f, t, fs, sw); else pick<4, false, 4, 4, true>(s, f, t, fs, sw); break;
         }
         return;
     }
-    if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f, t, fs); return; }
-    if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f, t, fs); return; }
+    if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f, t, fs, sw); return; }
+    if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f, t, fs, sw); return; }
     switch (P.n_eta_max) {
-    case 0: pick<0, false, 4, 4>(s, f, t, fs); break;
-    case 1: if (nar) pick<1, true, 4, 4>(s, f, t, fs); else pick<1, false, 4, 4>(s, f, t, fs); break;
-    case 2: if (nar) pick<2, true, 4, 4>(s, f, t, fs); else pick<2, false, 4, 4>(s, f, t, fs); break;
-    case 3: if (nar) pick<3, true, 4, 4>(s, f, t, fs); else pick<3, false, 4, 4>(s, f, t, fs); break;
-    default: if (nar) pick<4, true, 4, 4>(s, f, t, fs); else pick<4, false, 4, 4>(s, f, t, fs); break;
+    case 0: pick<0, false, 4, 4>(s, f, t, fs, sw); break;
+    case 1: if (nar) pick<1, true, 4, 4>(s, f, t, fs, sw); else pick<1, false, 4, 4>(s, f, t, fs, sw); break;
+    case 2: if (nar) pick<2, true, 4, 4>(s, f, t, fs, sw); else pick<2, false, 4, 4>(s, f, t, fs, sw); break;
+    case 3: if (nar) pick<3, true, 4, 4>(s, f, t, fs, sw); else pick<3, false, 4, 4>(s, f, t, fs, sw); break;
+    default: if (nar) pick<4, true, 4, 4>(s, f, t, fs, sw); else pick<4, false, 4, 4>(s, f, t, fs, sw); break;
     }
+}
+static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs)
+{
+    SfKernel sw;
+    pick_kernels(P, s, f, t, fs, sw);
 }
 static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t)
 {
     ForceKernel fs;
     pick_kernels(P, s, f, t, fs);
+}
+// The descriptor kernel for capacity C (the merged form up to SF_MERGED_MAX).
+static SfKernel sf_for(const Plan& P, int C)
+{
+    SfKernel s, sw;
+    ForceKernel f, fs;
+    TangentKernel t;
+    pick_kernels(P, s, f, t, fs, sw);
+    return C <= SF_MERGED_MAX ? s : sw;
 }
 static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f)
 {
@@ -500,7 +521,7 @@ static int set_capacity(nnp_handle* h, int C)
     h->smem_force = pf * h->wpb_force;
     h->smem_tan = pt * h->wpb_tan;
     int bs = 0;
-    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)ksf, 32 * h->wpb_sf, h->smem_sf));
+    CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)sf_for(h->plan, C), 32 * h->wpb_sf, h->smem_sf));
     h->grid_sf = std::max(1, bs) * h->num_sms;
     CK(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, (const void*)kf, 32 * h->wpb_force, h->smem_force));
     h->grid_force = std::max(1, bs) * h->num_sms;
@@ -901,11 +922,11 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         KScope ks(h, KG_SF, st, 2);
         CK(h, cudaMemsetAsync(h->spill, 0, sizeof(int), st));
         const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
-        ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->G, G_out, h->flags,
+        sf_for(P, h->cap_rc)<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->G, G_out, h->flags,
                                                      h->counters, h->spill, 0, store ? h->qpool : nullptr,
                                                      store ? h->qoff : nullptr, (unsigned long long)h->cap_qpool,
                                                      staged ? h->stg : nullptr, stg_plane);
-        ksf<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride, h->G, G_out,
+        sf_for(P, h->stride)<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, h->pos4, bx, nv, h->d_plan, h->stride, h->G, G_out,
                                                                  h->flags, h->counters, h->spill, 1, nullptr, nullptr,
                                                                  0ull, nullptr, 0);
     }
@@ -1197,11 +1218,12 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     CKC(cudaFuncSetAttribute((const void*)ksf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     CKC(cudaFuncSetAttribute((const void*)kf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     {
-        SfKernel s3;
+        SfKernel s3, sw3;
         ForceKernel f3, fs3;
         TangentKernel t3;
-        pick_kernels(P, s3, f3, t3, fs3);
+        pick_kernels(P, s3, f3, t3, fs3, sw3);
         CKC(cudaFuncSetAttribute((const void*)fs3, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        CKC(cudaFuncSetAttribute((const void*)sw3, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     }
     CKC(cudaFuncSetAttribute((const void*)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     CKC(cudaFuncSetAttribute((const void*)k_sf_cell, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1881,9 +1903,9 @@ extern "C" int nnp_compute_static(const nnp_handle* h, int n, const float* pos, 
     ForceKernel kf;
     pick_kernels(P, ksf, kf);
     const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
-    ksf<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, G, nullptr, flags, counters,
+    sf_for(P, h->cap_rc)<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, pos4, bx, nv, h->d_plan, h->cap_rc, G, nullptr, flags, counters,
                                                  spill, 0, nullptr, nullptr, 0ull, nullptr, 0);
-    ksf<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, G, nullptr, flags, counters,
+    sf_for(P, S)<<<h->grid_sp, 32 * h->wpb_sf_sp, h->smem_sf_sp, st>>>(n, pos4, bx, nv, h->d_plan, S, G, nullptr, flags, counters,
                                                              spill, 1, nullptr, nullptr, 0ull, nullptr, 0);
     const int gmlp = std::min(blocks_for(n, 128), h->grid_mlp);
     h->kmlp<<<gmlp, 128, h->smem_mlp, st>>>(n, pos4, h->d_plan, h->d_w, G, Ei, dEdG);

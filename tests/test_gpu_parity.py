@@ -96,6 +96,25 @@ def test_water_ragged_small_boxes(water_nnp, n_mol):
     check(out, ref, what="water %d" % (3 * n_mol))
 
 
+def test_dense_water_over_256_neighbours():
+    """Water compressed to 0.62 of its edge (~4.2x the density): ~360 neighbours
+    inside the cutoff, so the shared-memory capacity exceeds 256 staged neighbours
+    and the descriptor pass runs its one-block-pair-at-a-time form (staged indices
+    no longer fit 8 bits, no stored pair queues); the force pass rebuilds the
+    queues."""
+    from paper_2002_00054_b300 import NNP
+    m = workloads.water_model()
+    pos, types, box = workloads.water_random()
+    pos, box = pos * 0.62, box * 0.62
+    nnp = NNP(m, max_neighbors=1024)
+    ref, out, p, t, fb = _case(nnp, m, pos, types, box)
+    assert nnp.stats()["max_cutoff_row"] > 256, nnp.stats()
+    check(out, ref, what="dense water")
+    out2 = nnp.compute(p, t, fb)   # capacity retuned above 256 for the main pass
+    assert nnp.stats()["rc_capacity"] > 256, nnp.stats()
+    check(out2, ref, what="dense water, second call")
+
+
 def test_fcc_4000_cell_path(fcc_nnp):
     m = workloads.fcc_model()
     ref, out, *_ = _case(fcc_nnp, m, *workloads.fcc((10, 10, 10)))
