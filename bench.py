@@ -3,7 +3,8 @@ energy and forces every step, on the 2,064,384-atom water-like workload.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload water_2m|water_110k|water_1m|fcc_1m] [--no-cpu-baseline]
-                  [--no-bf16] [--no-train] [--no-fcc] [--mode standard|combined]
+                  [--no-bf16] [--no-train] [--no-fcc] [--no-combined] [--combined-steps S]
+                  [--mode standard|combined|domains|ablation|cpu|capacity]
 
 Prints one JSON line (rank 0).  The timed region is one nnp_step call of K steps
 (device-resident inputs; neighbour-list maintenance included), bracketed by a
@@ -13,8 +14,11 @@ path).  Further legs on the same line: end to end through host buffers (e2e),
 the roofline of the dominant kernel, the BF16 tensor-core network on the same
 workload (bf16_mlp), the force-matching training step (training_step), FP32 and
 BF16 on the 1,048,576-atom FCC crystal with errors against the oracle on the
-4,000-atom FCC box (fcc_precision), and the oracle timed on the host cores
-(cpu_baseline).  --mode combined runs the 1,048,320-atom BF16 autograd NVE run.
+4,000-atom FCC box (fcc_precision), the combined form (1,000 NVE steps of the
+1,048,320-atom box with the BF16 network and forces from the autograd backward:
+throughput and FP64 conserved-energy drift), and the oracle timed on the host
+cores (cpu_baseline).  --mode combined runs the combined form alone, with the
+FP32 integrator's drift from the same start beside it.
 --impl reference times the FP64 CPU oracle on a bounded sample of the same
 workload (the reference arm: the paper ships no code to install).
 """
@@ -399,7 +403,7 @@ def training_leg(dev, steps, warmup):
     return out
 
 
-def combined_run(args, dev):
+def combined_run(args, dev, fp32_run=True):
     """1,048,320-atom water-like box, BF16 tensor-core network, forces from the
     autograd backward (NNPEnergy), velocity Verlet for --steps steps at 0.5 fs;
     conserved-energy drift in FP64, force RMS against the FP32 path.  The same
@@ -464,6 +468,19 @@ def combined_run(args, dev):
     ms = a0.elapsed_time(a1)
     e1 = etot(E)
     drift = (e1 - e0) / n / (args.steps * dt * 1e-6)   # eV per atom per ns
+    res = {"metric": METRIC, "mode": "combined", "value": n * args.steps / (ms * 1e-3), "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "ms_per_step": ms / args.steps, "higher_is_better": True,
+           "dtype": "bf16-network/f32", "data": "synthetic",
+           "config": {"workload": "water_1m", "atoms": n, "dt_fs": dt,
+                      "forces": "NNPEnergy autograd backward, BF16 tensor-core network"},
+           "conserved_energy_drift_ev_per_atom_per_ns": drift, "energy_log_every_100_steps": log,
+           "initial_force_rms_vs_fp32_ev_per_A": f_rms,
+           "max_list_row": max_row, "spilled_atom_evaluations": spilled,
+           "min_pair_distance_A": r_min}
+    nnp.close()
+    if not fp32_run:
+        ref.close()
+        return res
     # the FP32 path's own integrator from the same start
     x, v = x0.clone(), v0.clone()
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -473,19 +490,12 @@ def combined_run(args, dev):
     torch.cuda.synchronize()
     et = lg.sum(1)
     fp32_drift = (et[-1] - et[0]) / n / (args.steps * dt * 1e-6)
-    return {"metric": METRIC, "mode": "combined", "value": n * args.steps / (ms * 1e-3), "unit": UNIT,
-            "n_gpus": 1, "steps": args.steps, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "dtype": "bf16-network/f32", "data": "synthetic",
-            "config": {"workload": "water_1m", "atoms": n, "dt_fs": dt,
-                       "forces": "NNPEnergy autograd backward, BF16 tensor-core network"},
-            "conserved_energy_drift_ev_per_atom_per_ns": drift, "energy_log_every_100_steps": log,
-            "initial_force_rms_vs_fp32_ev_per_A": f_rms,
-            "max_list_row": max_row, "spilled_atom_evaluations": spilled,
-            "min_pair_distance_A": r_min,
-            "fp32_nnp_step": {"conserved_energy_drift_ev_per_atom_per_ns": float(fp32_drift),
-                              "final_temperature_K": float(2 * lg[-1, 1] / (3 * n * workloads.KB_EV)),
-                              "ms_per_step": b0.elapsed_time(b1) / args.steps,
-                              "energy_log_every_100_steps": [float(e) for e in et[100::100]]}}
+    res["fp32_nnp_step"] = {"conserved_energy_drift_ev_per_atom_per_ns": float(fp32_drift),
+                            "final_temperature_K": float(2 * lg[-1, 1] / (3 * n * workloads.KB_EV)),
+                            "ms_per_step": b0.elapsed_time(b1) / args.steps,
+                            "energy_log_every_100_steps": [float(e) for e in et[100::100]]}
+    ref.close()
+    return res
 
 
 def domains_run(args, dev):
@@ -705,6 +715,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-train", action="store_true", help="skip the training-step leg")
     ap.add_argument("--no-fcc", action="store_true", help="skip the FCC precision-form leg")
+    ap.add_argument("--no-combined", action="store_true", help="skip the combined-form leg")
+    ap.add_argument("--combined-steps", type=int, default=1000, help="NVE steps of the combined-form leg")
     ap.add_argument("--mode", default="standard", choices=["standard", "combined", "domains", "ablation", "cpu", "capacity"])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -920,6 +932,18 @@ def main():
     if not args.no_fcc and args.workload != "fcc_1m":
         out["fcc_precision"] = fcc_precision_leg(dev, args.steps, args.warmup,
                                                  rank == 0 and world == 1 and not args.no_cpu_baseline)
+    if not args.no_combined and args.workload == "water_2m" and world == 1:
+        # the combined form: 1,000 NVE steps of the 1,048,320-atom box with the BF16
+        # network and forces from the autograd backward (--mode combined also runs
+        # the FP32 integrator from the same start for its drift)
+        nnp.close()
+        cargs = argparse.Namespace(**vars(args))
+        cargs.steps = args.combined_steps
+        c = combined_run(cargs, dev, fp32_run=False)
+        out["combined"] = {k: c[k] for k in ("value", "unit", "steps", "ms_per_step", "dtype", "config",
+                                             "conserved_energy_drift_ev_per_atom_per_ns",
+                                             "initial_force_rms_vs_fp32_ev_per_A", "max_list_row",
+                                             "spilled_atom_evaluations", "min_pair_distance_A")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(model["name"])
     if rank == 0:
