@@ -21,6 +21,10 @@
 
 #define FLAG_ERR 0
 #define FLAG_REBUILD 1
+// atom counters of the descriptor and force kernels' main passes (cleared by the
+// host before every evaluation, see AtomWalk)
+#define FLAG_WALK_SF 2
+#define FLAG_WALK_FORCE 3
 
 // work counters (counters[])
 #define CNT_LIST 0

@@ -102,6 +102,40 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int lan
     if (lane == 31 && bytes > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(c + bytes - 1));
 }
 
+// The atoms a warp evaluates.  Main passes (ctr != nullptr): chunks of up to
+// ATOM_CHUNK consecutive positions of the visiting order, claimed from a counter
+// that the host clears before the launch, so that the warps of a launch finish
+// together however the atoms' costs vary (with a fixed stride the warp slots
+// idled ~5 % of a 1M-atom launch waiting for the slowest warps).  Launches with
+// fewer than 16 chunks per warp, and the other passes, take a fixed stride over
+// the grid's warps.  Positions are warp-uniform.
+#define ATOM_CHUNK 8
+struct AtomWalk {
+    int* ctr;
+    int it0, step, n, lane;
+    int end = 0;
+    __device__ int claim()
+    {
+        int b = 0;
+        if (lane == 0) b = atomicAdd(ctr, ATOM_CHUNK);
+        b = __shfl_sync(FULL, b, 0);
+        end = min(b + ATOM_CHUNK, n);
+        return b;
+    }
+    __device__ int first()
+    {
+        if (ctr && n < 16 * ATOM_CHUNK * step) ctr = nullptr;   // small launch: the stride
+        return ctr ? claim() : it0;
+    }
+    __device__ int next(int it) { return ctr ? ((it + 1 < end) ? it + 1 : claim()) : it + step; }
+    // the position after it when already known (-1 otherwise)
+    __device__ int peek(int it) const
+    {
+        const int t = ctr ? ((it + 1 < end) ? it + 1 : -1) : it + step;
+        return t < n ? t : -1;
+    }
+};
+
 // true when atom i must be skipped by this pass (M > C)
 __device__ __forceinline__ bool over_capacity(int M, int C, int pass, int i, int* spill, bool enqueue, int lane,
                                               int* flags, unsigned long long& c_spill)
@@ -716,7 +750,8 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     bool qcan = NARROW && (pass == 0) && (qpool != nullptr);   // wide queues are not stored
     const int nw = gridDim.x * wpb;
     const int n_items = atom_count(pass, n, spill);
-    for (int it = blockIdx.x * wpb + wib; it < n_items; it += nw) {
+    AtomWalk walk{pass == 0 ? flags + FLAG_WALK_SF : nullptr, blockIdx.x * wpb + wib, nw, n_items, lane};
+    for (int it = walk.first(); it < n_items; it = walk.next(it)) {
         const int i = atom_at(pass, it, spill, nv.order);
         const float4 pi = pos4[i];
         const int ti = __float_as_int(pi.w);
@@ -1124,7 +1159,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
     const int nw = gridDim.x * wpb;
     const int n_items = atom_count(pass, n, spill);
     unsigned long long c_spill = 0;
-    for (int it = blockIdx.x * wpb + wib; it < n_items; it += nw) {
+    AtomWalk walk{pass == 0 ? flags + FLAG_WALK_FORCE : nullptr, blockIdx.x * wpb + wib, nw, n_items, lane};
+    for (int it = walk.first(); it < n_items; it = walk.next(it)) {
         const int i = atom_at(pass, it, spill, nv.order);
         const float4 pi = pos4[i];
         const int ti = __float_as_int(pi.w);
@@ -1152,7 +1188,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         // round, so their first reads would otherwise wait on DRAM (prefetching the
         // next atom's staged neighbours as well measured slower)
         unsigned o_next = QOFF_NONE;
-        if (staged && it + nw < n_items) o_next = qoff[atom_at(pass, it + nw, spill, nv.order)];
+        const int it_next = walk.peek(it);
+        if (staged && it_next >= 0) o_next = qoff[atom_at(pass, it_next, spill, nv.order)];
         if (staged) {
             // the descriptor pass's staging of this atom; its queue record gives M
             const unsigned o = (NETA > 0) ? qoff[i] : QOFF_NONE;

@@ -921,6 +921,7 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         stg_plane = (size_t)n * h->cap_rc;
         KScope ks(h, KG_SF, st, 2);
         CK(h, cudaMemsetAsync(h->spill, 0, sizeof(int), st));
+        CK(h, cudaMemsetAsync(h->flags + FLAG_WALK_SF, 0, 2 * sizeof(int), st));   // main passes' atom counters
         const int gsf = std::min(blocks_for(n, h->wpb_sf), h->grid_sf);
         sf_for(P, h->cap_rc)<<<gsf, 32 * h->wpb_sf, h->smem_sf, st>>>(n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->G, G_out, h->flags,
                                                      h->counters, h->spill, 0, store ? h->qpool : nullptr,
