@@ -109,7 +109,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes, int lan
 // idled ~5 % of a 1M-atom launch waiting for the slowest warps).  Launches with
 // fewer than 16 chunks per warp, and the other passes, take a fixed stride over
 // the grid's warps.  Positions are warp-uniform.
-#define ATOM_CHUNK 8
+#define ATOM_CHUNK 4
 struct AtomWalk {
     int* ctr;
     int it0, step, n, lane;

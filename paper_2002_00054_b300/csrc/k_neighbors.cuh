@@ -153,6 +153,10 @@ __global__ void k_cell_sort(int ncell, const int* __restrict__ cell_start, int* 
     }
 }
 
+// |d|^2 of a list candidate with explicit roundings: both row builders take the
+// same decisions, and d_ji = -d_ij (pair_disp) gives symmetric rows.
+__device__ __forceinline__ float dist2_list(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
+
 // Row of atom i from the 27-cell stencil (cells of edge >= cutoff + skin, >= 3 per side).
 // Entry order: stencil order (z, y, x from -1 to 1), then ascending atom index.
 // seg[i][t] (t = 0..26, stencil cell t = (dz+1)*9 + (dy+1)*3 + (dx+1)) is the
@@ -162,7 +166,7 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
                             const int* __restrict__ cell_start, const int* __restrict__ cell_atoms,
                             const float4* __restrict__ cpos,
                             float rcut2, int stride, uint32_t* __restrict__ nbr, int* __restrict__ ncount,
-                            unsigned short* __restrict__ seg, int* __restrict__ flags)
+                            unsigned short* __restrict__ seg, int* __restrict__ flags, const int* __restrict__ only)
 {
     if (!flags[FLAG_REBUILD]) return;
     // per warp: how many stencil cells start at each position of the current round
@@ -170,7 +174,10 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
     const int lane = threadIdx.x & 31;
     int* hc = hist[threadIdx.x >> 5];
     const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < n; i += nw) {
+    // only (not nullptr): the atoms only[1 .. only[0]] (those k_rows_blk left), else all
+    const int n_items = only ? only[0] : n;
+    for (int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); it < n_items; it += nw) {
+        const int i = only ? only[1 + it] : it;
         const float4 pi = pos4[i];
         const int cx = cell_coord(pi.x, box.L[0], ncx), cy = cell_coord(pi.y, box.L[1], ncy),
                   cz = cell_coord(pi.z, box.L[2], ncz);
@@ -230,7 +237,7 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
                 const float4 pj = cpos[tb0 + (f - tpre)];
                 const float ddx = pair_disp(pj.x, pi.x, tox), ddy = pair_disp(pj.y, pi.y, toy),
                             ddz = pair_disp(pj.z, pi.z, toz);
-                const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                const float r2 = dist2_list(ddx, ddy, ddz);
                 keep = (r2 < rcut2) && !(j == i && tcode == 62);
             }
             const unsigned m = __ballot_sync(FULL, keep);
@@ -247,6 +254,123 @@ __global__ void k_rows_cell(int n, const float4* __restrict__ pos4, Box box, int
             ncount[i] = min(cnt, stride);
             seg[(size_t)i * NB_SEG + 27] = (unsigned short)min(cnt, stride);
         }
+    }
+}
+
+// Rows of the cell path, one block per cell: the atoms of the 27 stencil cells are
+// staged once in shared memory (position and list entry j | image code << 24, and
+// the image shift), and each atom of the centre cell (a warp per atom) takes its
+// row from there: the candidates in stencil order, ascending index within a cell,
+// the displacement by pair_disp and the distance by dist2_list, so the rows, their
+// order and the stencil segments are those of k_rows_cell; no per-candidate cell
+// search and no global loads in the candidate loop.  A cell whose stencil holds
+// more than ROWS_SMAX atoms queues its own atoms in rest (count, then indices)
+// for k_rows_cell.
+#define ROWS_SMAX 1280
+__host__ __device__ inline size_t rows_blk_smem_bytes() { return (size_t)ROWS_SMAX * 2 * sizeof(float4); }
+__global__ void __launch_bounds__(128) k_rows_blk(int ncell, Box box, int ncx, int ncy, int ncz,
+                                                  const int* __restrict__ cell_start, const int* __restrict__ cell_atoms,
+                                                  const float4* __restrict__ cpos, float rcut2, int stride,
+                                                  uint32_t* __restrict__ nbr, int* __restrict__ ncount,
+                                                  unsigned short* __restrict__ seg, int* __restrict__ rest,
+                                                  int* __restrict__ flags)
+{
+    if (!flags[FLAG_REBUILD]) return;
+    extern __shared__ __align__(16) unsigned char rows_smem[];
+    float4* srec = reinterpret_cast<float4*>(rows_smem);   // (x, y, z, entry)
+    float4* ssh = srec + ROWS_SMAX;                          // image shift of the record
+    __shared__ int s_b0[27], s_off[28];
+    __shared__ float4 s_shift[27];   // (ox, oy, oz, image code)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
+        if (wid == 0) {
+            // lane t < 27: stencil cell t = (dz+1)*9 + (dy+1)*3 + (dx+1), its atom range
+            // and periodic shift; an exclusive scan of the cell sizes gives the offsets
+            const int cx = c % ncx, cy = (c / ncx) % ncy, cz = c / (ncx * ncy);
+            int b0 = 0, len = 0, code = 62;
+            float ox = 0.f, oy = 0.f, oz = 0.f;
+            if (lane < 27) {
+                const int dz = lane / 9 - 1, dy = (lane / 3) % 3 - 1, dx = lane % 3 - 1;
+                int x = cx + dx, y = cy + dy, z = cz + dz, sx = 0, sy = 0, sz = 0;
+                if (x < 0) { x += ncx; sx = -1; } else if (x >= ncx) { x -= ncx; sx = 1; }
+                if (y < 0) { y += ncy; sy = -1; } else if (y >= ncy) { y -= ncy; sy = 1; }
+                if (z < 0) { z += ncz; sz = -1; } else if (z >= ncz) { z -= ncz; sz = 1; }
+                const int cn = (z * ncy + y) * ncx + x;
+                b0 = cell_start[cn];
+                len = cell_start[cn + 1] - b0;
+                code = (sx + 2) * 25 + (sy + 2) * 5 + (sz + 2);
+                ox = (float)sx * box.L[0];
+                oy = (float)sy * box.L[1];
+                oz = (float)sz * box.L[2];
+            }
+            int pre = len;   // inclusive scan over lanes
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, pre, o);
+                if (lane >= o) pre += t;
+            }
+            if (lane < 27) {
+                s_b0[lane] = b0;
+                s_off[lane] = pre - len;
+                s_shift[lane] = make_float4(ox, oy, oz, __int_as_float(code));
+            }
+            if (lane == 26) s_off[27] = pre;
+        }
+        __syncthreads();
+        const int total = s_off[27], c0 = s_off[13], c1 = s_off[14];   // stencil cell 13: the cell itself
+        if (total > ROWS_SMAX) {
+            for (int k = threadIdx.x; k < c1 - c0; k += blockDim.x) rest[1 + atomicAdd(rest, 1)] = cell_atoms[s_b0[13] + k];
+            __syncthreads();
+            continue;
+        }
+        for (int f = threadIdx.x; f < total; f += blockDim.x) {
+            // stencil cell of record f: the last t with s_off[t] <= f (empty cells skipped)
+            int lo = 0, hi = 26;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= f) lo = mid;
+                else hi = mid - 1;
+            }
+            const int src = s_b0[lo] + (f - s_off[lo]);
+            const float4 pj = cpos[src], sh = s_shift[lo];
+            const uint32_t ent = (uint32_t)cell_atoms[src] | ((uint32_t)__float_as_int(sh.w) << 24);
+            srec[f] = make_float4(pj.x, pj.y, pj.z, __uint_as_float(ent));
+            ssh[f] = sh;
+        }
+        __syncthreads();
+        const int my_pre = (lane < 27) ? s_off[lane] : 0;
+        for (int k = c0 + wid; k < c1; k += nwb) {
+            const float4 pi = srec[k];   // shift 0
+            const uint32_t ei = __float_as_uint(pi.w);   // i | 62 << 24: i itself at shift 0
+            const int i = (int)(ei & NB_INDEX_MASK);
+            int cnt = 0, my_seg = 0;
+            for (int f0 = 0; f0 < total; f0 += 32) {
+                const int f = f0 + lane;
+                bool keep = false;
+                uint32_t ent = 0u;
+                if (f < total) {
+                    const float4 pj = srec[f], sh = ssh[f];
+                    const float ddx = pair_disp(pj.x, pi.x, sh.x), ddy = pair_disp(pj.y, pi.y, sh.y),
+                                ddz = pair_disp(pj.z, pi.z, sh.z);
+                    ent = __float_as_uint(pj.w);
+                    keep = (dist2_list(ddx, ddy, ddz) < rcut2) && ent != ei;
+                }
+                const unsigned m = __ballot_sync(FULL, keep);
+                // segment start of stencil cell `lane` (its first candidate falls in this round)
+                if (lane < 27 && my_pre >= f0 && my_pre < f0 + 32) my_seg = cnt + __popc(m & ((1u << (my_pre - f0)) - 1u));
+                const int at = cnt + __popc(m & ((1u << lane) - 1u));
+                if (keep && at < stride) nbr[(size_t)i * stride + at] = ent;
+                cnt += __popc(m);
+            }
+            if (lane < 27 && my_pre >= total) my_seg = cnt;   // empty trailing cells
+            if (lane < 27) seg[(size_t)i * NB_SEG + lane] = (unsigned short)min(my_seg, stride);
+            if (lane == 0) {
+                if (cnt > stride) atomicOr(&flags[FLAG_ERR], ERR_NEIGH_OVERFLOW);
+                ncount[i] = min(cnt, stride);
+                seg[(size_t)i * NB_SEG + 27] = (unsigned short)min(cnt, stride);
+            }
+        }
+        __syncthreads();
     }
 }
 

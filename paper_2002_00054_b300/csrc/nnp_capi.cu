@@ -858,12 +858,19 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
             k_cell_fill<<<blocks_for(n, T), T, 0, st>>>(n, h->cell_of, h->cursor, h->cell_atoms, h->flags);
             k_cell_sort<<<std::min(blocks_for(ncell, 8), h->num_sms * 8), 256, 0, st>>>(
                 ncell, h->cell_start, h->cell_atoms, h->pos4, h->cpos, h->flags);
+            // rows a block per cell from the staged stencil; cells with more than
+            // ROWS_SMAX stencil atoms leave their atoms (queued in spill, which the
+            // descriptor pass clears again) to the warp-per-atom builder
+            CK(h, cudaMemsetAsync(h->spill, 0, sizeof(int), st));
+            k_rows_blk<<<std::min(ncell, 5 * h->num_sms), 128, rows_blk_smem_bytes(), st>>>(
+                ncell, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_start, h->cell_atoms, h->cpos, P.rcut2, h->stride,
+                h->nbr, h->ncount, h->seg, h->spill, h->flags);
             k_rows_cell<<<rows_grid, 256, 0, st>>>(n, h->pos4, bx, h->nc[0], h->nc[1], h->nc[2], h->cell_start,
                                                    h->cell_atoms, h->cpos, P.rcut2, h->stride, h->nbr, h->ncount,
-                                                   h->seg, h->flags);
+                                                   h->seg, h->flags, h->spill);
             if (h->fmode == FM_GATHER) k_rev_cell<<<rows_grid, 256, 0, st>>>(n, h->nbr, h->ncount, h->stride, h->seg, h->rev,
                                                                    h->flags);
-            h->launches += (h->fmode == FM_GATHER) ? 6 : 5;
+            h->launches += (h->fmode == FM_GATHER) ? 7 : 6;
         } else {
             k_rows_brute<<<rows_grid, 256, 0, st>>>(n, h->pos4, bt ? h->sys_of : nullptr, bt ? h->sys_start_d : nullptr,
                                                     h->sys_box, P.rcut2, h->stride, h->nbr, h->ncount, h->flags);
