@@ -127,6 +127,28 @@ def test_fcc_small_box_images(fcc_nnp):
     check(out, ref, what="fcc 32")
 
 
+def test_cell_path_mixed_row_builders():
+    """A 30 A box (4 cells of 7.5 A per side) whose x in [0, 20) is squeezed into
+    [0, 10) (twice the density there, half beyond): half the cells have more than
+    1,280 atoms in their 27-cell stencil and keep the warp-per-atom row builder,
+    the others take the block-per-cell builder that stages the stencil in shared
+    memory.
+    One evaluation with both builders matches the oracle, and so do the steps
+    after (rebuilds with both)."""
+    from paper_2002_00054_b300 import NNP
+    m = workloads.water_model()
+    pos, types, box = workloads.water_random(900, 30.0, seed=31)
+    x = np.mod(pos[:, 0], 30.0)
+    pos = pos.copy()
+    pos[:, 0] = np.where(x < 20.0, x * 0.5, 10.0 + (x - 20.0) * 2.0)
+    nnp = NNP(m, max_neighbors=320)
+    ref, out, p, t, fb = _case(nnp, m, pos, types, box)
+    check(out, ref, what="mixed stencils")
+    v = torch.zeros_like(p)
+    nnp.step(p, v, t, fb, 0.5, 3)
+    check(nnp.compute(p, t, fb), oracle.compute(m, p.double().cpu().numpy(), types, fb), what="mixed stencils, steps")
+
+
 def test_single_atom_sees_only_itself(fcc_nnp):
     m = workloads.fcc_model()
     ref, out, *_ = _case(fcc_nnp, m, np.array([[0.4, 1.1, 2.0]]), np.array([0], np.int32), np.array([4.0, 4.0, 4.0]))
