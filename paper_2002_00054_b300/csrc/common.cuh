@@ -241,6 +241,27 @@ __device__ __forceinline__ float exp2_acc2(float ah, float al)
     return p * __int_as_float(((int)n + 127) << 23);
 }
 
+// exp2_acc2 of two arguments at once: the same operations per component, the
+// reduced arguments and the series carried as packed f32x2 pairs (one instruction
+// for both), so each result is bitwise the scalar one.
+__device__ __forceinline__ float2 exp2_acc2x2(float2 ah, float2 al)
+{
+    ah.x = fminf(fmaxf(ah.x, -125.0f), 127.0f);
+    ah.y = fminf(fmaxf(ah.y, -125.0f), 127.0f);
+    const float nx = rintf(ah.x), ny = rintf(ah.y);
+    const float2 f = __fadd2_rn(__fadd2_rn(ah, make_float2(-nx, -ny)), al);
+    float2 p = make_float2(1.3215486790144305e-06f, 1.3215486790144305e-06f);
+    p = __ffma2_rn(p, f, make_float2(1.5252733804059838e-05f, 1.5252733804059838e-05f));
+    p = __ffma2_rn(p, f, make_float2(1.5403530393381606e-04f, 1.5403530393381606e-04f));
+    p = __ffma2_rn(p, f, make_float2(1.3333558146428441e-03f, 1.3333558146428441e-03f));
+    p = __ffma2_rn(p, f, make_float2(9.6181291076284772e-03f, 9.6181291076284772e-03f));
+    p = __ffma2_rn(p, f, make_float2(5.5504108664821576e-02f, 5.5504108664821576e-02f));
+    p = __ffma2_rn(p, f, make_float2(2.4022650695910071e-01f, 2.4022650695910071e-01f));
+    p = __ffma2_rn(p, f, make_float2(6.9314718055994531e-01f, 6.9314718055994531e-01f));
+    p = __ffma2_rn(p, f, make_float2(1.0f, 1.0f));
+    return __fmul2_rn(p, make_float2(__int_as_float(((int)nx + 127) << 23), __int_as_float(((int)ny + 127) << 23)));
+}
+
 // 2^(ah + al) as h + l to ~2^-27 relative: the same reduction and series, with
 // the leading terms 1 + f ln2 carried in double-float (ln 2 as hi + lo).
 __device__ __forceinline__ void exp2_dd(float ah, float al, float& h, float& l)
@@ -268,6 +289,42 @@ __device__ __forceinline__ void exp2_dd(float ah, float al, float& h, float& l)
     const float sc = __int_as_float(((int)n + 127) << 23);
     h = rh * sc;
     l = rlo * sc;
+}
+
+// exp2_dd of two arguments at once (packed pairs, each component bitwise the
+// scalar result).
+__device__ __forceinline__ void exp2_dd2(float2 ah, float2 al, float2& h, float2& l)
+{
+    ah.x = fminf(fmaxf(ah.x, -125.0f), 127.0f);
+    ah.y = fminf(fmaxf(ah.y, -125.0f), 127.0f);
+    const float nx = rintf(ah.x), ny = rintf(ah.y);
+    // f + fl = (ah - n) + al exactly (TwoSum per component)
+    const float2 a = __fadd2_rn(ah, make_float2(-nx, -ny));
+    const float2 f = __fadd2_rn(a, al);
+    const float2 bb = __fadd2_rn(f, make_float2(-a.x, -a.y));
+    const float2 t = __fadd2_rn(f, make_float2(-bb.x, -bb.y));
+    const float2 fl = __fadd2_rn(__fadd2_rn(a, make_float2(-t.x, -t.y)), __fadd2_rn(al, make_float2(-bb.x, -bb.y)));
+    float2 q = make_float2(1.3215486790144305e-06f, 1.3215486790144305e-06f);
+    q = __ffma2_rn(q, f, make_float2(1.5252733804059838e-05f, 1.5252733804059838e-05f));
+    q = __ffma2_rn(q, f, make_float2(1.5403530393381606e-04f, 1.5403530393381606e-04f));
+    q = __ffma2_rn(q, f, make_float2(1.3333558146428441e-03f, 1.3333558146428441e-03f));
+    q = __ffma2_rn(q, f, make_float2(9.6181291076284772e-03f, 9.6181291076284772e-03f));
+    q = __ffma2_rn(q, f, make_float2(5.5504108664821576e-02f, 5.5504108664821576e-02f));
+    q = __ffma2_rn(q, f, make_float2(2.4022650695910071e-01f, 2.4022650695910071e-01f));
+    const float2 ln2h = make_float2(6.93147182464599609375e-01f, 6.93147182464599609375e-01f);
+    const float2 ln2l = make_float2(-1.9046542999577e-09f, -1.9046542999577e-09f);
+    const float2 th = __fmul2_rn(f, ln2h);
+    const float2 tl = __fadd2_rn(__ffma2_rn(f, ln2h, make_float2(-th.x, -th.y)),
+                                 __ffma2_rn(f, ln2l, __ffma2_rn(fl, ln2h, __fmul2_rn(__fmul2_rn(f, f), q))));
+    const float2 one = make_float2(1.0f, 1.0f);
+    const float2 sh = __fadd2_rn(one, th);
+    const float2 sl = __fadd2_rn(__fadd2_rn(__fadd2_rn(one, make_float2(-sh.x, -sh.y)), th), tl);
+    const float2 rh = __fadd2_rn(sh, sl);
+    const float2 rd = __fadd2_rn(rh, make_float2(-sh.x, -sh.y));
+    const float2 rlo = __fadd2_rn(sl, make_float2(-rd.x, -rd.y));
+    const float2 sc = make_float2(__int_as_float(((int)nx + 127) << 23), __int_as_float(((int)ny + 127) << 23));
+    h = __fmul2_rn(rh, sc);
+    l = __fmul2_rn(rlo, sc);
 }
 
 // cos(pi x) as h + l, x = xh + xl in [0, 1/2], to ~2^-28 absolute, and

@@ -460,8 +460,26 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                 cutoff_fn(r, P.inv_2rc, P.inv_2rc_lo, P.hpi_rc, fch, dfc);
             }
             const float fc = fch + fcl;
+            constexpr bool PK = ACC && NETA == 2 && !FORCE;
+            if (PK) {
+                // descriptor pass: both eta as packed pairs, each value bitwise the
+                // loop's below (which the force passes run)
+                const float2 KH = f2(khi[0], khi[1]), KLo = f2(klo[0], klo[1]);
+                const float2 R2H = f2(r2h, r2h), R2L = f2(r2l, r2l);
+                const float2 ah = mul2(KH, R2H);
+                const float2 al = add2(fma2(KH, R2H, f2(-ah.x, -ah.y)), fma2(KLo, R2H, mul2(KH, R2L)));
+                float2 eh, el;
+                exp2_dd2(ah, al, eh, el);
+                const float2 FCH = f2(fch, fch);
+                const float2 ph = mul2(eh, FCH);
+                const float2 pp = add2(ph, add2(fma2(eh, FCH, f2(-ph.x, -ph.y)), fma2(eh, f2(fcl, fcl), mul2(el, FCH))));
+                pq[0] = pp.x;
+                pq[1] = pp.y;
+                dq[0] = eh.x * (dfc - 2.0f * etav[0] * r * fc);
+                dq[1] = eh.y * (dfc - 2.0f * etav[1] * r * fc);
+            }
 #pragma unroll
-            for (int q = 0; q < NETA; ++q) {
+            for (int q = 0; q < NETA && !PK; ++q) {
                 if (ACC) {
                     // P_q = exp(-eta_q r^2) f_c: both factors as hi + lo, one final rounding
                     const float ah = khi[q] * r2h;
@@ -501,7 +519,22 @@ __device__ __forceinline__ int stage_neighbors(int i, const float4 pi, const Box
                     // the Gaussian's argument in double-float from r^2 = r2h + r2l (r_s = 0
                     // here, else (r - r_s)^2 by radial_x2)
                     const float4 nr = make_float4(r2h, r2l, fc, 0.f);
-                    for (int rr = E.rad_beg[ej], re = E.rad_end[ej]; rr < re; ++rr) {
+                    int rr = E.rad_beg[ej];
+                    const int re = E.rad_end[ej];
+                    // two descriptors at a time (packed pairs, each bitwise the scalar form)
+                    for (; rr + 1 < re; rr += 2) {
+                        float xh0, xl0, xh1, xl1;
+                        radial_x2(nr, E.rad_rs[rr], xh0, xl0);
+                        radial_x2(nr, E.rad_rs[rr + 1], xh1, xl1);
+                        const float2 kh = f2(E.rad_khi[rr], E.rad_khi[rr + 1]), kl = f2(E.rad_klo[rr], E.rad_klo[rr + 1]);
+                        const float2 xh = f2(xh0, xh1), xl = f2(xl0, xl1);
+                        const float2 ah = mul2(kh, xh);
+                        const float2 al = add2(fma2(kh, xh, f2(-ah.x, -ah.y)), fma2(kl, xh, mul2(kh, xl)));
+                        const float2 e = exp2_acc2x2(ah, al);
+                        rtab[16 * lane + (rr ^ (lane & 15))] += e.x * fc;
+                        rtab[16 * lane + ((rr + 1) ^ (lane & 15))] += e.y * fc;
+                    }
+                    if (rr < re) {
                         float xh, xl;
                         radial_x2(nr, E.rad_rs[rr], xh, xl);
                         const float kh = E.rad_khi[rr];
