@@ -172,9 +172,9 @@ __device__ __forceinline__ void cutoff_fn_fast(float r, float hpi_rc, float& fc,
 
 // Units of the force pass's fixed-point sums, per angular kind: the high word
 // counts 2^-HB eV/A, the low word (and the int64 force sums) 2^-LB eV/A.  The
-// narrow kind's coarse high word is zero for contributions below 1/8 eV/A, so a
+// narrow kind's coarse high word is zero for contributions below 1/16 eV/A, so a
 // warp can skip its atomics; the wide kind keeps the finer low word.
-#define FX_HB_NARROW 2
+#define FX_HB_NARROW 3
 #define FX_LB_NARROW 27
 #define FX_HB_WIDE 6
 #define FX_LB_WIDE 27

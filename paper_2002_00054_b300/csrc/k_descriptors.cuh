@@ -195,20 +195,23 @@ __host__ __device__ inline size_t force_warp_bytes(int C, int S, bool pack, bool
 // it is exact), and each part is added into its own int32 word with a native
 // shared-memory integer atomic.  Per add |hi| < 2^21 and |lo| <= 2^(L-H-1).  Without
 // CARRY (L - H <= 21) the up to 1024 adds a neighbour receives (list stride <= 1024)
-// cannot overflow either word; with CARRY the force kernel bounds the adds between
-// carries (see FxU).  The only rounding is 2^-(L+1) eV/A per add, and the sums do
+// cannot overflow either word; with CARRY (the narrow kind, |lo| <= 2^23) a low word
+// stays below 2^31 for up to FX_MAXADDS adds: the pass over stored queues, where a
+// slot takes at most M adds, leaves atoms with M > FX_MAXADDS to the wide-capacity
+// pass, which carries the low words into the high words between block pairs when
+// a slot could take more.  The only rounding is 2^-(L+1) eV/A per add, and the sums do
 // not depend on the order of the adds.  hi is zero for |v| < 2^-(H+1).  L stays at
 // 27: with a coarser low unit the contributions below half a unit, which share a
 // radial sign, round away and bias the virial.
 #define FX_LIMIT 32000.0f
+#define FX_MAXADDS 255   // adds of |lo| <= 2^23 into a low word without a carry: 255 * 2^23 < 2^31
 template <bool N>
 struct FxU {
     static constexpr int HB = N ? FX_HB_NARROW : FX_HB_WIDE, LB = N ? FX_LB_NARROW : FX_LB_WIDE;
     // CARRY: lo is rounded with a conversion instruction (|r 2^LB| up to 2^(LB-HB-1)),
-    // and the force kernel carries the low words into the high words after every
-    // 32 x 32 block pair, so a low word takes at most 32 adds between carries
+    // and a low word holds at most FX_MAXADDS adds between carries
     static constexpr bool CARRY = LB - HB > 21;
-    static_assert((!CARRY && LB - HB <= 21) || (CARRY && LB - HB <= 25), "fixed-point word ranges");
+    static_assert((!CARRY && LB - HB <= 21) || (CARRY && LB - HB <= 24), "fixed-point word ranges");
     static_assert(HB >= 0 && HB <= 6, "fixed-point word ranges");
 };
 // The roundings to integers use the 1.5 * 2^23 shift: for |x| < 2^22, x + 1.5 * 2^23
@@ -308,6 +311,31 @@ template <bool N>
 __device__ __forceinline__ long long fx_get64(const WarpSmem& w, int idx)
 {
     return (long long)w.sgh[idx] * (1ll << (FxU<N>::LB - FxU<N>::HB)) + (long long)w.sgl[idx];
+}
+
+// A batch of the narrow kind with a contribution of at least 2^-(HB+1) eV/A (rare):
+// every contribution of the lane split into its high and low words and added,
+// out of line so that the common path (low words only) keeps its registers.
+template <bool N>
+__device__ __noinline__ void fx_add6_split(int* __restrict__ sgh, int* __restrict__ sgl, int j, int k, float2 gaxy,
+                                           float2 gbxy, float2 gz)
+{
+    int h0, l0, h1, l1, h2, l2, h3, l3, h4, l4, h5, l5;
+    fx_split2<N>(gaxy, h0, l0, h1, l1);
+    fx_split2<N>(gbxy, h2, l2, h3, l3);
+    fx_split2<N>(gz, h4, l4, h5, l5);
+    atomicAdd(&sgl[3 * j + 0], l0);
+    atomicAdd(&sgl[3 * j + 1], l1);
+    atomicAdd(&sgl[3 * k + 0], l2);
+    atomicAdd(&sgl[3 * k + 1], l3);
+    atomicAdd(&sgl[3 * j + 2], l4);
+    atomicAdd(&sgl[3 * k + 2], l5);
+    if (h0) atomicAdd(&sgh[3 * j + 0], h0);
+    if (h1) atomicAdd(&sgh[3 * j + 1], h1);
+    if (h2) atomicAdd(&sgh[3 * k + 0], h2);
+    if (h3) atomicAdd(&sgh[3 * k + 1], h3);
+    if (h4) atomicAdd(&sgh[3 * j + 2], h4);
+    if (h5) atomicAdd(&sgh[3 * k + 2], h5);
 }
 
 // Narrow-kind live test r_jk < rc written with h = r^2 / 2 - rc^2 / 4 of each
@@ -1233,6 +1261,10 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             }
             rec = qpool + (size_t)o * 8;
             M = rec[0];
+            if (FxU<NARROW>::CARRY && M > FX_MAXADDS) {   // a slot could take more adds than a low word holds
+                if (lane == 0) spill[1 + atomicAdd(spill, 1)] = i;
+                continue;
+            }
             const size_t base = (size_t)i * C;
             for (int m = lane; m < M; m += 32) {
                 const float4 a = stg[base + m], pq = stg[stg_plane + base + m], ax = stg[2 * stg_plane + base + m];
@@ -1272,7 +1304,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             if (o != QOFF_NONE && o != QOFF_SPILLED) {
                 const unsigned short* r = qpool + (size_t)o * 8;
                 if (r[0] == (unsigned short)M && r[1] == (unsigned short)(sig & 0xffffu) &&
-                    r[2] == (unsigned short)(sig >> 16))
+                    r[2] == (unsigned short)(sig >> 16) && !(FxU<NARROW>::CARRY && M > FX_MAXADDS))
                     rec = r;
             }
             if (!rec) {
@@ -1361,9 +1393,6 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             const int ce1 = RES ? E.cls_e1[cls] : -1, ce2 = RES ? E.cls_e2[cls] : -1;
             // STORED: one sweep over the record's entries (every block pair, back to
             // back, as j | k << 8); otherwise one 32 x 32 block pair at a time.
-            // bend: record position where block pair bp ends (carries, below)
-            const int nbp = nb * (nb + 1) / 2;
-            int bp = QHDR, bend = STORED ? (int)rec[QHDR] : 0;
             for (int A = 0; A < (STORED ? 1 : nb); ++A) {
                 const int jl = 32 * A + lane;
                 const float4 al = (jl < M) ? w.nd[jl] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1565,54 +1594,29 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             } else {
                             const float vm = fmaxf(fmaxf(fmaxf(fabsf(gaxy.x), fabsf(gaxy.y)), fmaxf(fabsf(gbxy.x), fabsf(gbxy.y))),
                                                    fmaxf(fabsf(gz.x), fabsf(gz.y)));
-                            int h0 = 0, l0, h1 = 0, l1, h2 = 0, l2, h3 = 0, l3, h4 = 0, l4, h5 = 0, l5;
                             const bool small = __all_sync(__activemask(), vm < 0.5f / (float)(1 << FxU<NARROW>::HB));
                             if (small) {
+                                int l0, l1, l2, l3, l4, l5;
                                 fx_lo2<NARROW>(gaxy, l0, l1);
                                 fx_lo2<NARROW>(gbxy, l2, l3);
                                 fx_lo2<NARROW>(gz, l4, l5);
+                                atomicAdd(&w.sgl[3 * j + 0], l0);
+                                atomicAdd(&w.sgl[3 * j + 1], l1);
+                                atomicAdd(&w.sgl[3 * k + 0], l2);
+                                atomicAdd(&w.sgl[3 * k + 1], l3);
+                                atomicAdd(&w.sgl[3 * j + 2], l4);
+                                atomicAdd(&w.sgl[3 * k + 2], l5);
                             } else {
-                                fx_split2<NARROW>(gaxy, h0, l0, h1, l1);
-                                fx_split2<NARROW>(gbxy, h2, l2, h3, l3);
-                                fx_split2<NARROW>(gz, h4, l4, h5, l5);
+                                fx_add6_split<NARROW>(w.sgh, w.sgl, j, k, gaxy, gbxy, gz);
                             }
-                            atomicAdd(&w.sgl[3 * j + 0], l0);
-                            atomicAdd(&w.sgl[3 * j + 1], l1);
-                            atomicAdd(&w.sgl[3 * k + 0], l2);
-                            atomicAdd(&w.sgl[3 * k + 1], l3);
-                            atomicAdd(&w.sgl[3 * j + 2], l4);
-                            atomicAdd(&w.sgl[3 * k + 2], l5);
-                            if (!small) {
-                                if (h0) atomicAdd(&w.sgh[3 * j + 0], h0);
-                                if (h1) atomicAdd(&w.sgh[3 * j + 1], h1);
-                                if (h2) atomicAdd(&w.sgh[3 * k + 0], h2);
-                                if (h3) atomicAdd(&w.sgh[3 * k + 1], h3);
-                                if (h4) atomicAdd(&w.sgh[3 * j + 2], h4);
-                                if (h5) atomicAdd(&w.sgh[3 * k + 2], h5);
-                            }
-                            }
-                        }
-                        if (STORED && FxU<NARROW>::CARRY && nb > 3 && bend <= e0 + 32) {
-                            // a block pair ended in this batch: unless it was the last, carry
-                            // every slot.  A block pair adds at most 32 times into a slot, and
-                            // the batches since the previous carry hold one block pair's
-                            // entries and then at most 32 more: 64 adds of |lo| <= 2^24 and
-                            // the residue below 2^25 stay below 2^31.
-                            while (bp < QHDR + nbp - 1 && bend <= e0 + 32) bend += rec[++bp];
-                            if (bend <= e0 + 32) {
-                                bend = 0x7fffffff;
-                            } else {
-                                __syncwarp();
-                                for (int t = lane; t < 3 * M; t += 32) fx_carry<NARROW>(w, t);
-                                __syncwarp();
                             }
                         }
                     }
                     __syncwarp();
-                    if (!STORED && FxU<NARROW>::CARRY && nb > 3) {
+                    if (!STORED && FxU<NARROW>::CARRY && 32 * nb + 1 > FX_MAXADDS) {
                         // the slots of blocks A and B took at most 32 adds each: carry.
-                        // With at most 3 blocks a slot meets at most 3 block pairs: 96 adds
-                        // of |lo| <= 2^24 and the radial value stay below 2^31 uncarried.
+                        // A slot meets at most nb block pairs: with 32 nb adds and the
+                        // radial value within FX_MAXADDS no carry is needed.
                         for (int t = lane; t < 96; t += 32) {
                             if (96 * A + t < 3 * M) fx_carry<NARROW>(w, 96 * A + t);
                             if (B != A && 96 * B + t < 3 * M) fx_carry<NARROW>(w, 96 * B + t);
