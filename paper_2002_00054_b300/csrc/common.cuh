@@ -393,6 +393,32 @@ __device__ __forceinline__ double warp_reduce_scatter32(const float (&v)[32], in
     return (double)hi[0] + (double)lo[0];
 }
 
+// The same reduce-scatter, the total returned as the unevaluated pair (hi, lo).
+__device__ __forceinline__ float2 warp_reduce_scatter32_ff(const float (&v)[32], int lane)
+{
+    float hi[32], lo[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        hi[t] = v[t];
+        lo[t] = 0.f;
+    }
+#pragma unroll
+    for (int half = 16; half >= 1; half >>= 1) {
+        const bool upper = (lane & half) != 0;
+#pragma unroll
+        for (int t = 0; t < half; ++t) {
+            const float send_h = upper ? hi[t] : hi[t + half], send_l = upper ? lo[t] : lo[t + half];
+            const float keep_h = upper ? hi[t + half] : hi[t], keep_l = upper ? lo[t + half] : lo[t];
+            const float rh = __shfl_xor_sync(FULL, send_h, half), rl = __shfl_xor_sync(FULL, send_l, half);
+            float s, e;
+            two_sum(keep_h, rh, s, e);
+            hi[t] = s;
+            lo[t] = keep_l + rl + e;
+        }
+    }
+    return make_float2(hi[0], lo[0]);
+}
+
 __device__ __forceinline__ double warp_sum_d(double v)
 {
 #pragma unroll

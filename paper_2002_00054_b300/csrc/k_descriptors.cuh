@@ -785,7 +785,9 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
     w.nd = reinterpret_cast<float4*>(base);
     w.npf = w.nd + C;
     w.nrad = w.npf + C;
-    double* sG = reinterpret_cast<double*>(w.nrad + C);
+    // descriptor sums as unevaluated pairs (hi, lo): no FP64 arithmetic (a slow
+    // pipe on this GPU) in the per-atom epilogue
+    float2* sG = reinterpret_cast<float2*>(w.nrad + C);
     w.ninv = reinterpret_cast<float*>(sG + NNP_MAXG);
     w.queue = reinterpret_cast<unsigned short*>(w.ninv + (BIG ? C : 0));
     w.nh = nullptr;
@@ -861,7 +863,7 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                     comp = (t - sum) - y;
                     sum = t;
                 }
-                sG[E.rad_out[lane]] = (double)sum - (double)comp;
+                sG[E.rad_out[lane]] = make_float2(sum, -comp);
             }
             __syncwarp();
         } else {
@@ -888,9 +890,15 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                         sum = t;
                     }
                 }
-                double tot = (double)sum - (double)comp;
-                if (halves == 2) tot += __shfl_xor_sync(FULL, tot, 16);
-                if (act && hf == 0) sG[E.rad_out[rr]] = tot;
+                float th = sum, tl = -comp;
+                if (halves == 2) {
+                    const float oh = __shfl_xor_sync(FULL, th, 16), ol = __shfl_xor_sync(FULL, tl, 16);
+                    float s2, e2;
+                    two_sum(th, oh, s2, e2);
+                    th = s2;
+                    tl = (tl + ol) + e2;
+                }
+                if (act && hf == 0) sG[E.rad_out[rr]] = make_float2(th, tl);
             }
         }
         // angular (one pass per neighbour-element pair class)
@@ -1125,12 +1133,13 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                     }
                     v[t] = a;
                 }
-                const double tot = warp_reduce_scatter32(v, lane);
+                const float2 tot = warp_reduce_scatter32_ff(v, lane);
                 const int idx = c0 + lane;
                 if (idx < NA) {
                     const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
                     const int o = (q < E.n_eta) ? E.ang_out[cls][q][l][kk] : -1;
-                    if (o >= 0) sG[o] = tot * (double)exp2f((float)(1 - (1 << kk)));
+                    const float sc = exp2f((float)(1 - (1 << kk)));   // a power of two: exact
+                    if (o >= 0) sG[o] = make_float2(tot.x * sc, tot.y * sc);
                 }
             }
             if (cls == 0 && lane == 2) cnt += (unsigned long long)M * (M - 1) / 2;
@@ -1139,9 +1148,14 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         if (NETA == 0 && qoff && lane == 0) qoff[i] = QOFF_NONE;
         __syncwarp();
         for (int s = lane; s < E.n_g; s += 32) {
-            const double g = sG[s];
-            Gs[(size_t)i * P.gs + s] = (float)((g - (double)E.mu[s]) * (double)E.inv_s[s]);
-            if (Graw) Graw[(size_t)i * E.n_g + s] = (float)g;
+            // G~ = (G - mu) / s with G = hi + lo: the difference exact (TwoSum), one
+            // final rounding
+            const float2 g = sG[s];
+            float dh, dl;
+            two_sum(g.x, -E.mu[s], dh, dl);
+            dl += g.y;
+            Gs[(size_t)i * P.gs + s] = fmaf(dh, E.inv_s[s], dl * E.inv_s[s]);
+            if (Graw) Graw[(size_t)i * E.n_g + s] = g.x + g.y;
         }
         __syncwarp();
         if (lane == 0) cnt += (unsigned long long)n_list;
