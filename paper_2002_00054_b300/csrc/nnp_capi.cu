@@ -408,15 +408,22 @@ typedef void (*TangentKernel)(int, const float4*, Box, NbView, const Plan*, int,
 // pair-queue records exist; beyond, one block pair at a time (sf_for).
 #define SF_MERGED_MAX 256
 
+// fh: the MD step's form of the force pass over stored queues (staged neighbours,
+// fixed-point atomics, no virial), where it exists (at most 2 eta, not resolved).
 template <int NETA, bool NARROW, int KP, int KN, bool RES = false>
-static void pick(SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs, SfKernel& sw)
+static void pick(SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs, SfKernel& sw, ForceKernel& fh)
 {
     s = k_sf<NETA, NARROW, KP, KN, RES, true>;
     sw = k_sf<NETA, NARROW, KP, KN, RES, false>;
     f = k_force<NETA, NARROW, KP, KN, false, RES>;
     t = k_tangent<NETA, NARROW, KP, KN, RES>;
-    if constexpr (RES) fs = f;   // resolved models do not store pair queues
-    else fs = k_force<NETA, NARROW, KP, KN, true, false>;
+    fh = nullptr;
+    if constexpr (RES) {
+        fs = f;   // resolved models do not store pair queues
+    } else {
+        fs = k_force<NETA, NARROW, KP, KN, true, false>;
+        if constexpr (NARROW && NETA > 0 && NETA <= 2) fh = k_force<NETA, NARROW, KP, KN, true, false, true>;
+    }
 }
 
 // Largest k (zeta = 2^k) used with lambda = +1 (l = 0) or -1 (l = 1), -1 if none.
@@ -436,29 +443,35 @@ static int kmax_of(const Plan& P, int l)
 // three eta, both lambda up to zeta 16) models; every other set runs the
 // generic instantiation with all powers up to zeta 16.
 static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs,
-                         SfKernel& sw)
+                         SfKernel& sw, ForceKernel& fh)
 {
     const bool nar = (P.ang_kind == NNP_SF_ANG_NARROW);
     const int kp = kmax_of(P, 0), kn = kmax_of(P, 1);
     if (P.resolved) {
         // angular descriptors resolved by neighbour-element pair: generic terms
         switch (P.n_eta_max) {
-        case 1: if (nar) pick<1, true, 4, 4, true>(s, f, t, fs, sw); else pick<1, false, 4, 4, true>(s, f, t, fs, sw); break;
-        case 2: if (nar) pick<2, true, 4, 4, true>(s, f, t, fs, sw); else pick<2, false, 4, 4, true>(s, f, t, fs, sw); break;
-        case 3: if (nar) pick<3, true, 4, 4, true>(s, f, t, fs, sw); else pick<3, false, 4, 4, true>(s, f, t, fs, sw); break;
-        default: if (nar) pick<4, true, 4, 4, true>(s, f, t, fs, sw); else pick<4, false, 4, 4, true>(s, f, t, fs, sw); break;
+        case 1: if (nar) pick<1, true, 4, 4, true>(s, f, t, fs, sw, fh); else pick<1, false, 4, 4, true>(s, f, t, fs, sw, fh); break;
+        case 2: if (nar) pick<2, true, 4, 4, true>(s, f, t, fs, sw, fh); else pick<2, false, 4, 4, true>(s, f, t, fs, sw, fh); break;
+        case 3: if (nar) pick<3, true, 4, 4, true>(s, f, t, fs, sw, fh); else pick<3, false, 4, 4, true>(s, f, t, fs, sw, fh); break;
+        default: if (nar) pick<4, true, 4, 4, true>(s, f, t, fs, sw, fh); else pick<4, false, 4, 4, true>(s, f, t, fs, sw, fh); break;
         }
         return;
     }
-    if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f, t, fs, sw); return; }
-    if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f, t, fs, sw); return; }
+    if (nar && P.n_eta_max == 2 && kp == 4 && kn <= 2) { pick<2, true, 4, 2>(s, f, t, fs, sw, fh); return; }
+    if (!nar && P.n_eta_max == 3 && kp <= 4 && kn <= 4) { pick<3, false, 4, 4>(s, f, t, fs, sw, fh); return; }
     switch (P.n_eta_max) {
-    case 0: pick<0, false, 4, 4>(s, f, t, fs, sw); break;
-    case 1: if (nar) pick<1, true, 4, 4>(s, f, t, fs, sw); else pick<1, false, 4, 4>(s, f, t, fs, sw); break;
-    case 2: if (nar) pick<2, true, 4, 4>(s, f, t, fs, sw); else pick<2, false, 4, 4>(s, f, t, fs, sw); break;
-    case 3: if (nar) pick<3, true, 4, 4>(s, f, t, fs, sw); else pick<3, false, 4, 4>(s, f, t, fs, sw); break;
-    default: if (nar) pick<4, true, 4, 4>(s, f, t, fs, sw); else pick<4, false, 4, 4>(s, f, t, fs, sw); break;
+    case 0: pick<0, false, 4, 4>(s, f, t, fs, sw, fh); break;
+    case 1: if (nar) pick<1, true, 4, 4>(s, f, t, fs, sw, fh); else pick<1, false, 4, 4>(s, f, t, fs, sw, fh); break;
+    case 2: if (nar) pick<2, true, 4, 4>(s, f, t, fs, sw, fh); else pick<2, false, 4, 4>(s, f, t, fs, sw, fh); break;
+    case 3: if (nar) pick<3, true, 4, 4>(s, f, t, fs, sw, fh); else pick<3, false, 4, 4>(s, f, t, fs, sw, fh); break;
+    default: if (nar) pick<4, true, 4, 4>(s, f, t, fs, sw, fh); else pick<4, false, 4, 4>(s, f, t, fs, sw, fh); break;
     }
+}
+static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs,
+                         SfKernel& sw)
+{
+    ForceKernel fh;
+    pick_kernels(P, s, f, t, fs, sw, fh);
 }
 static void pick_kernels(const Plan& P, SfKernel& s, ForceKernel& f, TangentKernel& t, ForceKernel& fs)
 {
@@ -891,8 +904,9 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
     SfKernel ksf;
     ForceKernel kf;
     TangentKernel kt_unused;
-    ForceKernel kfs;
-    pick_kernels(P, ksf, kf, kt_unused, kfs);
+    ForceKernel kfs, kfh;
+    SfKernel ksw_unused;
+    pick_kernels(P, ksf, kf, kt_unused, kfs, ksw_unused, kfh);
     h->evals++;
     bool staged = false;
     size_t stg_plane = 0;
@@ -973,7 +987,10 @@ static int run_eval(nnp_handle* h, int n, const float* pos, const int* types, co
         KScope ks(h, KG_FORCE, st, 2);
         // main pass over the stored queues (atoms without one join the wide pass)
         const bool stored = P.n_eta_max > 0 && P.ang_kind == NNP_SF_ANG_NARROW && !P.resolved && h->qpool;
-        (stored ? kfs : kf)<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
+        // the MD step's form (staged neighbours, fixed-point atomics, no virial) has
+        // an instantiation of its own without the other forms' code
+        const bool hot = stored && staged && Fq && !vir_out && kfh;
+        (hot ? kfh : (stored ? kfs : kf))<<<gf, 32 * h->wpb_force, h->smem_force, st>>>(
             n, h->pos4, bx, nv, h->d_plan, h->cap_rc, h->dEdG, h->gbuf, h->Fown, vir_out ? h->vpart : nullptr,
             n_sum, h->flags, h->spill, 0,
             stored ? h->qpool : nullptr, stored ? h->qoff : nullptr, Fsc, Fq, (stored && staged) ? h->stg : nullptr,
