@@ -1244,10 +1244,11 @@ int nnp_create(const nnp_params* params, int device, nnp_handle** out)
     CKC(cudaFuncSetAttribute((const void*)kf, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     {
         SfKernel s3, sw3;
-        ForceKernel f3, fs3;
+        ForceKernel f3, fs3, fh3;
         TangentKernel t3;
-        pick_kernels(P, s3, f3, t3, fs3, sw3);
+        pick_kernels(P, s3, f3, t3, fs3, sw3, fh3);
         CKC(cudaFuncSetAttribute((const void*)fs3, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
+        if (fh3) CKC(cudaFuncSetAttribute((const void*)fh3, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
         CKC(cudaFuncSetAttribute((const void*)sw3, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
     }
     CKC(cudaFuncSetAttribute((const void*)kt, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem));
