@@ -61,8 +61,8 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # profiles/ (a 2M-atom launch moves the same bytes per atom: list rows,
 # positions, pair-queue and staged-neighbour records all scale with atoms).
 # Valid only for the kernel sources with this hash; otherwise traffic is null.
-TRAFFIC = {"force": (898.041856e6 + 5.804032e6) / 110592, "descriptors": (90.688256e6 + 780.495616e6) / 110592}
-TRAFFIC_SRC_SHA = "436f067437ee"
+TRAFFIC = {"force": (909.254912e6 + 6.266112e6) / 110592, "descriptors": (91.291648e6 + 781.606144e6) / 110592}
+TRAFFIC_SRC_SHA = "d29be3acb2e1"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
