@@ -327,12 +327,12 @@ NNP_API int nnp_kernel_times(nnp_handle* h, int max_groups, double* total_ms, lo
  * The handle's network must be NNP_FP32 (NNP_EUNSUPPORTED otherwise).
  *
  * The first call on a device looks up the array's device address (a runtime
- * call, made once per device with that device current); make that first call
- * before any stream capture.  The address is kept for the life of the process:
- * after cudaDeviceReset on a device, do not call this entry point on that
- * device again in the same process.  Every call shares the one array and leaves its
- * contents behind: calls whose work overlaps on the GPU (different streams or
- * host threads without ordering) race on it; serialise them.
+ * call, made once per device with that device current).  The address is kept
+ * for the life of the process: after cudaDeviceReset on a device, do not call
+ * this entry point on that device again in the same process.  Every call
+ * shares the one array and leaves its contents behind: calls whose work
+ * overlaps on the GPU (different streams or host threads without ordering)
+ * race on it; serialise them.
  *
  * Arguments as nnp_compute (energy, atom_energy, forces device pointers, each
  * nullable; box host double [3]); errbuf (nullable) receives a message of at
