@@ -433,6 +433,8 @@ __device__ __forceinline__ uint32_t nb_pack(int j, int sx, int sy, int sz)
 {
     return (uint32_t)j | ((uint32_t)((sx + 2) * 25 + (sy + 2) * 5 + (sz + 2)) << 24);
 }
+// image code of the shift (0, 0, 0): (0 + 2) * 25 + (0 + 2) * 5 + (0 + 2)
+#define NB_CODE_NOSHIFT 62u
 __device__ __forceinline__ void nb_shift(uint32_t e, float Lx, float Ly, float Lz, float& ox, float& oy, float& oz)
 {
     int code = (int)(e >> 24);
