@@ -53,6 +53,27 @@ __device__ __forceinline__ float gauss2(float khi, float klo, float x2)
     return exp2f(fmaf(khi, x2, klo * x2));
 }
 
+// n = rint(x) for |x| <= 2^22 and 2^n, both from t = x + 1.5 * 2^23: the float
+// sum is rounded to an integer, ties to even, as rintf rounds, and t - 1.5 * 2^23
+// is exact.  bits(t) = bits(1.5 * 2^23) + n, and bits(1.5 * 2^23) * 2^23 = 0 mod
+// 2^32, so bits(t) * 2^23 + 127 * 2^23 = (n + 127) << 23 (one integer multiply-
+// add instead of a conversion, an add and a shift); callers clamp x to [-125, 127].
+__device__ __forceinline__ float rint_pow2(float x, float& p2)
+{
+    const float M = 12582912.0f;
+    const float t = x + M;
+    p2 = __uint_as_float(__float_as_uint(t) * (1u << 23) + (127u << 23));
+    return t - M;
+}
+__device__ __forceinline__ float2 rint_pow2_2(float2 x, float2& p2)
+{
+    const float M = 12582912.0f;
+    const float2 t = __fadd2_rn(x, make_float2(M, M));
+    p2 = make_float2(__uint_as_float(__float_as_uint(t.x) * (1u << 23) + (127u << 23)),
+                     __uint_as_float(__float_as_uint(t.y) * (1u << 23) + (127u << 23)));
+    return __fadd2_rn(t, make_float2(-M, -M));
+}
+
 // 2^x to within ~0.5 ulp with no systematic bias, for the per-neighbour factors
 // exp(-eta r^2) f_c(r): every descriptor is a sum of them, and a bias common to
 // all terms survives the sum and the scaling G~ = (G - mu)/s, |mu/s| ~ 20 (a
@@ -65,7 +86,8 @@ __device__ __forceinline__ float gauss2(float khi, float klo, float x2)
 __device__ __forceinline__ float exp2_acc(float x)
 {
     x = fminf(fmaxf(x, -125.0f), 127.0f);
-    const float n = rintf(x);
+    float sc;
+    const float n = rint_pow2(x, sc);
     const float f = x - n;
     float p = 1.3215486790144305e-06f;
     p = fmaf(p, f, 1.5252733804059838e-05f);
@@ -76,7 +98,7 @@ __device__ __forceinline__ float exp2_acc(float x)
     p = fmaf(p, f, 2.4022650695910071e-01f);
     p = fmaf(p, f, 6.9314718055994531e-01f);
     p = fmaf(p, f, 1.0f);
-    return p * __int_as_float(((int)n + 127) << 23);
+    return p * sc;
 }
 __device__ __forceinline__ float gauss2_acc(float khi, float klo, float x2)
 {
@@ -227,7 +249,8 @@ __device__ __forceinline__ void dd_norm2(float x, float y, float z, float& h, fl
 __device__ __forceinline__ float exp2_acc2(float ah, float al)
 {
     ah = fminf(fmaxf(ah, -125.0f), 127.0f);
-    const float n = rintf(ah);
+    float sc;
+    const float n = rint_pow2(ah, sc);
     const float f = (ah - n) + al;
     float p = 1.3215486790144305e-06f;
     p = fmaf(p, f, 1.5252733804059838e-05f);
@@ -238,7 +261,7 @@ __device__ __forceinline__ float exp2_acc2(float ah, float al)
     p = fmaf(p, f, 2.4022650695910071e-01f);
     p = fmaf(p, f, 6.9314718055994531e-01f);
     p = fmaf(p, f, 1.0f);
-    return p * __int_as_float(((int)n + 127) << 23);
+    return p * sc;
 }
 
 // exp2_acc2 of two arguments at once: the same operations per component, the
@@ -248,8 +271,9 @@ __device__ __forceinline__ float2 exp2_acc2x2(float2 ah, float2 al)
 {
     ah.x = fminf(fmaxf(ah.x, -125.0f), 127.0f);
     ah.y = fminf(fmaxf(ah.y, -125.0f), 127.0f);
-    const float nx = rintf(ah.x), ny = rintf(ah.y);
-    const float2 f = __fadd2_rn(__fadd2_rn(ah, make_float2(-nx, -ny)), al);
+    float2 sc;
+    const float2 n = rint_pow2_2(ah, sc);
+    const float2 f = __fadd2_rn(__fadd2_rn(ah, make_float2(-n.x, -n.y)), al);
     float2 p = make_float2(1.3215486790144305e-06f, 1.3215486790144305e-06f);
     p = __ffma2_rn(p, f, make_float2(1.5252733804059838e-05f, 1.5252733804059838e-05f));
     p = __ffma2_rn(p, f, make_float2(1.5403530393381606e-04f, 1.5403530393381606e-04f));
@@ -259,7 +283,7 @@ __device__ __forceinline__ float2 exp2_acc2x2(float2 ah, float2 al)
     p = __ffma2_rn(p, f, make_float2(2.4022650695910071e-01f, 2.4022650695910071e-01f));
     p = __ffma2_rn(p, f, make_float2(6.9314718055994531e-01f, 6.9314718055994531e-01f));
     p = __ffma2_rn(p, f, make_float2(1.0f, 1.0f));
-    return __fmul2_rn(p, make_float2(__int_as_float(((int)nx + 127) << 23), __int_as_float(((int)ny + 127) << 23)));
+    return __fmul2_rn(p, sc);
 }
 
 // 2^(ah + al) as h + l to ~2^-27 relative: the same reduction and series, with
@@ -267,7 +291,8 @@ __device__ __forceinline__ float2 exp2_acc2x2(float2 ah, float2 al)
 __device__ __forceinline__ void exp2_dd(float ah, float al, float& h, float& l)
 {
     ah = fminf(fmaxf(ah, -125.0f), 127.0f);
-    const float n = rintf(ah);
+    float sc;
+    const float n = rint_pow2(ah, sc);
     float f, fl;
     two_sum(ah - n, al, f, fl);   // f + fl = (ah - n) + al exactly
     // q2 = (2^f - 1 - f ln2) / f^2, a float series (its terms are below 0.13 f)
@@ -286,7 +311,6 @@ __device__ __forceinline__ void exp2_dd(float ah, float al, float& h, float& l)
     // renormalise, so that h alone is 2^x to within an ulp (|sl| < 0.1 < sh)
     const float rh = sh + sl;
     const float rlo = sl - (rh - sh);
-    const float sc = __int_as_float(((int)n + 127) << 23);
     h = rh * sc;
     l = rlo * sc;
 }
@@ -297,9 +321,10 @@ __device__ __forceinline__ void exp2_dd2(float2 ah, float2 al, float2& h, float2
 {
     ah.x = fminf(fmaxf(ah.x, -125.0f), 127.0f);
     ah.y = fminf(fmaxf(ah.y, -125.0f), 127.0f);
-    const float nx = rintf(ah.x), ny = rintf(ah.y);
+    float2 sc;
+    const float2 n = rint_pow2_2(ah, sc);
     // f + fl = (ah - n) + al exactly (TwoSum per component)
-    const float2 a = __fadd2_rn(ah, make_float2(-nx, -ny));
+    const float2 a = __fadd2_rn(ah, make_float2(-n.x, -n.y));
     const float2 f = __fadd2_rn(a, al);
     const float2 bb = __fadd2_rn(f, make_float2(-a.x, -a.y));
     const float2 t = __fadd2_rn(f, make_float2(-bb.x, -bb.y));
@@ -322,7 +347,6 @@ __device__ __forceinline__ void exp2_dd2(float2 ah, float2 al, float2& h, float2
     const float2 rh = __fadd2_rn(sh, sl);
     const float2 rd = __fadd2_rn(rh, make_float2(-sh.x, -sh.y));
     const float2 rlo = __fadd2_rn(sl, make_float2(-rd.x, -rd.y));
-    const float2 sc = make_float2(__int_as_float(((int)nx + 127) << 23), __int_as_float(((int)ny + 127) << 23));
     h = __fmul2_rn(rh, sc);
     l = __fmul2_rn(rlo, sc);
 }
