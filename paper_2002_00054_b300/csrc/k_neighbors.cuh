@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(128) k_rows_blk(int ncell, Box box, int ncx, i
     extern __shared__ __align__(16) unsigned char rows_smem[];
     float4* srec = reinterpret_cast<float4*>(rows_smem);   // (x, y, z, entry)
     float4* ssh = srec + ROWS_SMAX;                          // image shift of the record
-    __shared__ int s_b0[27], s_off[28];
+    __shared__ int s_b0[27], s_off[28], s_noshift;
     __shared__ float4 s_shift[27];   // (ox, oy, oz, image code)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwb = blockDim.x >> 5;
     for (int c = blockIdx.x; c < ncell; c += gridDim.x) {
@@ -315,9 +315,13 @@ __global__ void __launch_bounds__(128) k_rows_blk(int ncell, Box box, int ncx, i
                 s_shift[lane] = make_float4(ox, oy, oz, __int_as_float(code));
             }
             if (lane == 26) s_off[27] = pre;
+            // every stencil cell at image shift (0, 0, 0): all but the cells at the box faces
+            const unsigned ns = __ballot_sync(FULL, lane >= 27 || code == 62);
+            if (lane == 0) s_noshift = (ns == FULL);
         }
         __syncthreads();
         const int total = s_off[27], c0 = s_off[13], c1 = s_off[14];   // stencil cell 13: the cell itself
+        const bool noshift = s_noshift != 0;
         if (total > ROWS_SMAX) {
             for (int k = threadIdx.x; k < c1 - c0; k += blockDim.x) rest[1 + atomicAdd(rest, 1)] = cell_atoms[s_b0[13] + k];
             __syncthreads();
@@ -349,9 +353,19 @@ __global__ void __launch_bounds__(128) k_rows_blk(int ncell, Box box, int ncx, i
                 bool keep = false;
                 uint32_t ent = 0u;
                 if (f < total) {
-                    const float4 pj = srec[f], sh = ssh[f];
-                    const float ddx = pair_disp(pj.x, pi.x, sh.x), ddy = pair_disp(pj.y, pi.y, sh.y),
-                                ddz = pair_disp(pj.z, pi.z, sh.z);
+                    const float4 pj = srec[f];
+                    float ddx, ddy, ddz;
+                    if (noshift) {
+                        // pair_disp with a zero shift returns pj - pi (TwoSum: t + e rounds to t)
+                        ddx = pj.x - pi.x;
+                        ddy = pj.y - pi.y;
+                        ddz = pj.z - pi.z;
+                    } else {
+                        const float4 sh = ssh[f];
+                        ddx = pair_disp(pj.x, pi.x, sh.x);
+                        ddy = pair_disp(pj.y, pi.y, sh.y);
+                        ddz = pair_disp(pj.z, pi.z, sh.z);
+                    }
                     ent = __float_as_uint(pj.w);
                     keep = (dist2_list(ddx, ddy, ddz) < rcut2) && ent != ei;
                 }
