@@ -61,8 +61,8 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # profiles/ (a 2M-atom launch moves the same bytes per atom: list rows,
 # positions, pair-queue and staged-neighbour records all scale with atoms).
 # Valid only for the kernel sources with this hash; otherwise traffic is null.
-TRAFFIC = {"force": (915.471104e6 + 6.4768e6) / 110592, "descriptors": (90.657792e6 + 780.431104e6) / 110592}
-TRAFFIC_SRC_SHA = "b12cd486d9de"
+TRAFFIC = {"force": (915.684352e6 + 6.436608e6) / 110592, "descriptors": (90.842112e6 + 781.032448e6) / 110592}
+TRAFFIC_SRC_SHA = "31cf164d2fa4"
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
