@@ -11,7 +11,8 @@ Prints one JSON line (rank 0).  The timed region is one nnp_step call of K steps
 barrier and device synchronisation on both sides, max over ranks.  Each rank
 runs its own copy of the workload (weak scaling, no collective on the data
 path).  Further legs on the same line: end to end through host buffers (e2e),
-the roofline of the dominant kernel, the BF16 tensor-core network on the same
+the roofline of the dominant kernel (FP32 flops, DRAM bytes and warp-instruction
+issue, each against its peak, for both big kernels), the BF16 tensor-core network on the same
 workload (bf16_mlp), the force-matching training step (training_step), FP32 and
 BF16 on the 1,048,576-atom FCC crystal with errors against the oracle on the
 4,000-atom FCC box (fcc_precision), the combined form (1,000 NVE steps of the
@@ -63,6 +64,13 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # Valid only for the kernel sources with this hash; otherwise traffic is null.
 TRAFFIC = {"force": (915.684352e6 + 6.436608e6) / 110592, "descriptors": (90.842112e6 + 781.032448e6) / 110592}
 TRAFFIC_SRC_SHA = "31cf164d2fa4"
+# Warp instructions per atom-evaluation of the same launches (ncu
+# smsp__inst_executed.sum over the atoms; the 2M-atom launches run the same
+# instruction streams, their chunked atom walk adds a few per atom), under the same
+# source hash.  Both big kernels are bound by instruction issue: 148 SMs x 4
+# schedulers x 2032 MHz, one warp instruction per scheduler per clock.
+INST_PER_ATOM = {"force": 982335969 / 110592, "descriptors": 1096655589 / 110592}
+ISSUE_PEAK_WINST = 148 * 4 * 2032e6
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
 
@@ -861,8 +869,14 @@ def main():
         if traffic is not None and peak_gbs:
             gbs = traffic * k_launch / (k_ms * 1e-3) / 1e9   # one timed group per evaluation
             hbm = {"achieved_gbs": gbs, "peak_gbs": peak_gbs, "frac": gbs / peak_gbs, "peak_source": "measured"}
+        issue = None
+        if TRAFFIC_SRC_SHA == sha and kname in INST_PER_ATOM:
+            ips = INST_PER_ATOM[kname] * n * k_launch / (k_ms * 1e-3)
+            issue = {"achieved_warp_inst_per_s": ips, "peak_warp_inst_per_s": ISSUE_PEAK_WINST,
+                     "frac": ips / ISSUE_PEAK_WINST, "inst_per_atom": INST_PER_ATOM[kname],
+                     "source": "ncu instruction count per atom (110,592-atom capture) x atoms / CUDA-event time"}
         return {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "hbm": hbm,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": traffic, "hbm": hbm, "issue": issue,
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 x 2032 MHz (unit counts and max clock)",
                 "mufu_gops": mu / (k_ms * 1e-3) / 1e9, "mufu_peak_gops": MUFU_PEAK_GOPS,
                 "ms_per_evaluation": k_ms / k_launch, "evaluations": k_launch,
