@@ -396,12 +396,20 @@ __device__ __forceinline__ double warp_reduce_scatter32(const float (&v)[32], in
 {
     float hi[32], lo[32];
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-        hi[t] = v[t];
-        lo[t] = 0.f;
+    for (int t = 0; t < 32; ++t) hi[t] = v[t];
+    {
+        // first step: the low words are still zero, so only the high words travel
+        const bool upper = (lane & 16) != 0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const float send_h = upper ? hi[t] : hi[t + 16];
+            const float keep_h = upper ? hi[t + 16] : hi[t];
+            const float rh = __shfl_xor_sync(FULL, send_h, 16);
+            two_sum(keep_h, rh, hi[t], lo[t]);
+        }
     }
 #pragma unroll
-    for (int half = 16; half >= 1; half >>= 1) {
+    for (int half = 8; half >= 1; half >>= 1) {
         const bool upper = (lane & half) != 0;
 #pragma unroll
         for (int t = 0; t < half; ++t) {
@@ -422,12 +430,20 @@ __device__ __forceinline__ float2 warp_reduce_scatter32_ff(const float (&v)[32],
 {
     float hi[32], lo[32];
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-        hi[t] = v[t];
-        lo[t] = 0.f;
+    for (int t = 0; t < 32; ++t) hi[t] = v[t];
+    {
+        // first step: the low words are still zero, so only the high words travel
+        const bool upper = (lane & 16) != 0;
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            const float send_h = upper ? hi[t] : hi[t + 16];
+            const float keep_h = upper ? hi[t + 16] : hi[t];
+            const float rh = __shfl_xor_sync(FULL, send_h, 16);
+            two_sum(keep_h, rh, hi[t], lo[t]);
+        }
     }
 #pragma unroll
-    for (int half = 16; half >= 1; half >>= 1) {
+    for (int half = 8; half >= 1; half >>= 1) {
         const bool upper = (lane & half) != 0;
 #pragma unroll
         for (int t = 0; t < half; ++t) {
