@@ -425,37 +425,65 @@ __device__ __forceinline__ double warp_reduce_scatter32(const float (&v)[32], in
     return (double)hi[0] + (double)lo[0];
 }
 
-// The same reduce-scatter, the total returned as the unevaluated pair (hi, lo).
-__device__ __forceinline__ float2 warp_reduce_scatter32_ff(const float (&v)[32], int lane)
+// One level of warp_reduce_scatter_n: the K (hi, lo) pairs a lane holds are
+// halved; lanes with bit HALF clear keep the first ceil(K/2), the others the rest
+// (the missing last one a zero pair), each adding its partner's copy.
+template <int HALF, int K>
+__device__ __forceinline__ void rs_level(float* hi, float* lo, int lane, int& base, int& cnt)
 {
-    float hi[32], lo[32];
+    constexpr int KP = (K + 1) / 2;
+    const bool up = (lane & HALF) != 0;
 #pragma unroll
-    for (int t = 0; t < 32; ++t) hi[t] = v[t];
+    for (int t = 0; t < KP; ++t) {
+        const float ah = hi[t], al = lo[t];
+        const float bh = (KP + t < K) ? hi[KP + t] : 0.f, bl = (KP + t < K) ? lo[KP + t] : 0.f;
+        const float rh = __shfl_xor_sync(FULL, up ? ah : bh, HALF), rl = __shfl_xor_sync(FULL, up ? al : bl, HALF);
+        float s, e;
+        two_sum(up ? bh : ah, rh, s, e);
+        hi[t] = s;
+        lo[t] = (up ? bl : al) + rl + e;
+    }
+    if (up) {
+        base += KP;
+        cnt -= KP;
+    } else {
+        cnt = min(cnt, KP);
+    }
+}
+
+// Reduce-scatter of N <= 32 per-lane values v[0, N) over the warp with
+// compensated (hi + lo) additions.  Each of the five levels halves the values a
+// lane still holds, so a level costs ceil(K/2) exchanges for K values: 21 in all
+// for N = 20, 31 for N = 32.  The first level moves high words only (the low
+// words are still zero).  Returns the total over the lanes of v[slot], with
+// slot = -1 on the lanes that end with none.
+template <int N>
+__device__ __forceinline__ float2 warp_reduce_scatter_n(const float (&v)[32], int lane, int& slot)
+{
+    static_assert(N >= 1 && N <= 32, "1 to 32 values");
+    constexpr int K1 = (N + 1) / 2, K2 = (K1 + 1) / 2, K3 = (K2 + 1) / 2, K4 = (K3 + 1) / 2;
+    float hi[K1], lo[K1];
+    int base = 0, cnt = N;
     {
-        // first step: the low words are still zero, so only the high words travel
-        const bool upper = (lane & 16) != 0;
+        const bool up = (lane & 16) != 0;
 #pragma unroll
-        for (int t = 0; t < 16; ++t) {
-            const float send_h = upper ? hi[t] : hi[t + 16];
-            const float keep_h = upper ? hi[t + 16] : hi[t];
-            const float rh = __shfl_xor_sync(FULL, send_h, 16);
-            two_sum(keep_h, rh, hi[t], lo[t]);
+        for (int t = 0; t < K1; ++t) {
+            const float a = v[t], b = (K1 + t < N) ? v[K1 + t] : 0.f;
+            const float r = __shfl_xor_sync(FULL, up ? a : b, 16);
+            two_sum(up ? b : a, r, hi[t], lo[t]);
+        }
+        if (up) {
+            base += K1;
+            cnt -= K1;
+        } else {
+            cnt = min(cnt, K1);
         }
     }
-#pragma unroll
-    for (int half = 8; half >= 1; half >>= 1) {
-        const bool upper = (lane & half) != 0;
-#pragma unroll
-        for (int t = 0; t < half; ++t) {
-            const float send_h = upper ? hi[t] : hi[t + half], send_l = upper ? lo[t] : lo[t + half];
-            const float keep_h = upper ? hi[t + half] : hi[t], keep_l = upper ? lo[t + half] : lo[t];
-            const float rh = __shfl_xor_sync(FULL, send_h, half), rl = __shfl_xor_sync(FULL, send_l, half);
-            float s, e;
-            two_sum(keep_h, rh, s, e);
-            hi[t] = s;
-            lo[t] = keep_l + rl + e;
-        }
-    }
+    rs_level<8, K1>(hi, lo, lane, base, cnt);
+    rs_level<4, K2>(hi, lo, lane, base, cnt);
+    rs_level<2, K3>(hi, lo, lane, base, cnt);
+    rs_level<1, K4>(hi, lo, lane, base, cnt);
+    slot = cnt > 0 ? base : -1;
     return make_float2(hi[0], lo[0]);
 }
 

@@ -1135,8 +1135,9 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 }
             }
             if (rec && lane == 0) rec[3] = (unsigned short)done;
-            // lane partials: compensated reduce-scatter, lane t gets accumulator 32c + t;
-            // prefactor 2^(1 - zeta), zeta = 2^k
+            // lane partials: compensated reduce-scatter of the NA accumulators, 32 at a
+            // time (a lane gets one accumulator, or none); prefactor 2^(1 - zeta), zeta = 2^k
+            static_assert(NA <= 64, "at most two rounds of 32 accumulators");
 #pragma unroll
             for (int c0 = 0; c0 < NA; c0 += 32) {
                 float v[32];
@@ -1151,9 +1152,11 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                     }
                     v[t] = a;
                 }
-                const float2 tot = warp_reduce_scatter32_ff(v, lane);
-                const int idx = c0 + lane;
-                if (idx < NA) {
+                int slot;
+                const float2 tot = (c0 == 0) ? warp_reduce_scatter_n<(NA < 32 ? NA : 32)>(v, lane, slot)
+                                             : warp_reduce_scatter_n<(NA > 32 ? NA - 32 : 1)>(v, lane, slot);
+                const int idx = c0 + slot;
+                if (slot >= 0 && idx < NA) {
                     const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
                     const int o = (q < E.n_eta) ? E.ang_out[cls][q][l][kk] : -1;
                     const float sc = exp2f((float)(1 - (1 << kk)));   // a power of two: exact
