@@ -923,7 +923,6 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         const int ncls = RES ? E.n_cls : 1;
         for (int cls = 0; NETA > 0 && cls < ncls; ++cls) {
             constexpr int NQ = NETA > 0 ? NETA : 1, NP = (NQ + 1) / 2;
-            constexpr int NA = NQ * 2 * (NNP_KMAX + 1);   // dense accumulators, index (q*2 + l)*(KMAX+1) + k
             // accumulators per eta: (lambda = +1, lambda = -1) as packed f32x2 for
             // k <= KLO, where both powers come out of one packed chain; beyond, the
             // one lambda that goes on (TX: lambda = +1) as floats
@@ -1135,29 +1134,32 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
                 }
             }
             if (rec && lane == 0) rec[3] = (unsigned short)done;
-            // lane partials: compensated reduce-scatter of the NA accumulators, 32 at a
-            // time (a lane gets one accumulator, or none); prefactor 2^(1 - zeta), zeta = 2^k
-            static_assert(NA <= 64, "at most two rounds of 32 accumulators");
+            // lane partials: compensated reduce-scatter of the accumulators in use, per eta
+            // the KP + 1 of lambda = +1 then the KN + 1 of lambda = -1, 32 at a time (a lane
+            // gets one accumulator, or none); prefactor 2^(1 - zeta), zeta = 2^k
+            constexpr int PER = KP + KN + 2, NAC = NQ * PER;
+            static_assert(NAC <= 64, "at most two rounds of 32 accumulators");
 #pragma unroll
-            for (int c0 = 0; c0 < NA; c0 += 32) {
+            for (int c0 = 0; c0 < NAC; c0 += 32) {
                 float v[32];
 #pragma unroll
                 for (int t = 0; t < 32; ++t) {
-                    const int idx = c0 + t;
-                    const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
+                    const int idx = c0 + t, q = idx / PER, r = idx % PER;
+                    const int l = (r <= KP) ? 0 : 1, kk = (r <= KP) ? r : r - (KP + 1);
                     float a = 0.f;
-                    if (idx < NA) {
+                    if (idx < NAC) {
                         if (kk <= KLO) a = (l == 0) ? accL[q][kk].x : accL[q][kk].y;
-                        else if (kk <= KM && (l == 0) == TX) a = accT[q][kk - KLO - 1];
+                        else a = accT[q][kk - KLO - 1];   // the one lambda that goes on beyond KLO
                     }
                     v[t] = a;
                 }
                 int slot;
-                const float2 tot = (c0 == 0) ? warp_reduce_scatter_n<(NA < 32 ? NA : 32)>(v, lane, slot)
-                                             : warp_reduce_scatter_n<(NA > 32 ? NA - 32 : 1)>(v, lane, slot);
+                const float2 tot = (c0 == 0) ? warp_reduce_scatter_n<(NAC < 32 ? NAC : 32)>(v, lane, slot)
+                                             : warp_reduce_scatter_n<(NAC > 32 ? NAC - 32 : 1)>(v, lane, slot);
                 const int idx = c0 + slot;
-                if (slot >= 0 && idx < NA) {
-                    const int q = idx / (2 * (NNP_KMAX + 1)), l = (idx / (NNP_KMAX + 1)) % 2, kk = idx % (NNP_KMAX + 1);
+                if (slot >= 0 && idx < NAC) {
+                    const int q = idx / PER, r = idx % PER;
+                    const int l = (r <= KP) ? 0 : 1, kk = (r <= KP) ? r : r - (KP + 1);
                     const int o = (q < E.n_eta) ? E.ang_out[cls][q][l][kk] : -1;
                     const float sc = exp2f((float)(1 - (1 << kk)));   // a power of two: exact
                     if (o >= 0) sG[o] = make_float2(tot.x * sc, tot.y * sc);
