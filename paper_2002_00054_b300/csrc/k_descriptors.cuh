@@ -871,18 +871,26 @@ k_sf(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* __re
         //   loop over neighbours with broadcast reads; Kahan-compensated sums (they
         //   feed G~ = (G - mu)/s with |mu/s| up to ~20).
         if (rad_tab) {
+            // both half-warps on the 16 columns: rows 0..15 and 16..31 (the upper half
+            // one row ahead, so that the two rows of a step sit in opposite bank halves),
+            // each a compensated sum, then the two halves' (sum, -comp) pairs added
             const float* tab = reinterpret_cast<const float*>(w.queue);
-            if (lane < E.n_rad) {
-                float sum = 0.f, comp = 0.f;
+            const int col = lane & 15, hf = lane >> 4;
+            float sum = 0.f, comp = 0.f;
+            if (col < E.n_rad) {
 #pragma unroll 8
-                for (int l = 0; l < 32; ++l) {
-                    const float y = tab[16 * l + (lane ^ (l & 15))] - comp;
+                for (int u = 0; u < 16; ++u) {
+                    const int l = 16 * hf + ((u + hf) & 15);
+                    const float y = tab[16 * l + (col ^ (l & 15))] - comp;
                     const float t = sum + y;
                     comp = (t - sum) - y;
                     sum = t;
                 }
-                sG[E.rad_out[lane]] = make_float2(sum, -comp);
             }
+            const float oh = __shfl_xor_sync(FULL, sum, 16), ol = __shfl_xor_sync(FULL, -comp, 16);
+            float sh, el;
+            two_sum(sum, oh, sh, el);
+            if (hf == 0 && col < E.n_rad) sG[E.rad_out[col]] = make_float2(sh, (-comp + ol) + el);
             __syncwarp();
         } else {
             const int halves = (E.n_rad <= 16) ? 2 : 1;
