@@ -62,14 +62,14 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # profiles/ (a 2M-atom launch moves the same bytes per atom: list rows,
 # positions, pair-queue and staged-neighbour records all scale with atoms).
 # Valid only for the kernel sources with this hash; otherwise traffic is null.
-TRAFFIC = {"force": (915.480832e6 + 6.215168e6) / 110592, "descriptors": (91.616256e6 + 781.42848e6) / 110592}
-TRAFFIC_SRC_SHA = "392a25eeae05"
+TRAFFIC = {"force": (916.454656e6 + 6.298112e6) / 110592, "descriptors": (91.076864e6 + 781.018368e6) / 110592}
+TRAFFIC_SRC_SHA = "5ca50ae96948"
 # Warp instructions per atom-evaluation of the same launches (ncu
 # smsp__inst_executed.sum over the atoms; the 2M-atom launches run the same
 # instruction streams, their chunked atom walk adds a few per atom), under the same
 # source hash.  Both big kernels are bound by instruction issue: 148 SMs x 4
 # schedulers x 2032 MHz, one warp instruction per scheduler per clock.
-INST_PER_ATOM = {"force": 982335969 / 110592, "descriptors": 1058140535 / 110592}
+INST_PER_ATOM = {"force": 974924989 / 110592, "descriptors": 1058140535 / 110592}
 ISSUE_PEAK_WINST = 148 * 4 * 2032e6
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 

@@ -1409,7 +1409,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                 for (int kk = 0; kk <= KM; ++kk) {
                     const int op = (q < E.n_eta && kk <= KP) ? E.ang_out[cls][q][0][kk] : -1;
                     const int om = (q < E.n_eta && kk <= KN) ? E.ang_out[cls][q][1][kk] : -1;
-                    const float sc = exp2f((float)(1 - (1 << kk)));
+                    // 2^(1 - zeta) as its bit pattern (kk is a constant here: the factor folds)
+                    const float sc = __int_as_float((127 + 1 - (1 << kk)) << 23);
                     const float wp = (op >= 0) ? sW[op] * sc : 0.f, wm = (om >= 0) ? sW[om] * sc : 0.f;
                     if (kk <= KLO) WL[q][kk] = f2(wp, wm);
                     else WT[q][kk - KLO - 1] = TX ? wp : wm;
@@ -1719,12 +1720,21 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         // floats (order-dependent); otherwise g is written per list slot for the
         // gather.  Then the own force and the virial.
         const int cnt = n_list;
-        if (HOT || (Fq && staged)) {
+        // own force sums (64-bit fixed point): taken in the assembly loop where it
+        // reads every slot anyway (one read and conversion per slot, not two)
+        long long qx = 0, qy = 0, qz = 0;
+        const bool q_done = HOT || (Fq && staged);
+        if (q_done) {
             for (int m = lane; m < M; m += 32) {
+                const long long gx = fx_get64<NARROW>(w, 3 * m), gy = fx_get64<NARROW>(w, 3 * m + 1),
+                                gz = fx_get64<NARROW>(w, 3 * m + 2);
                 unsigned long long* fj = Fq + 3 * (size_t)w.jidx[m];
-                atomicAdd(fj + 0, (unsigned long long)(-fx_get64<NARROW>(w, 3 * m)));
-                atomicAdd(fj + 1, (unsigned long long)(-fx_get64<NARROW>(w, 3 * m + 1)));
-                atomicAdd(fj + 2, (unsigned long long)(-fx_get64<NARROW>(w, 3 * m + 2)));
+                atomicAdd(fj + 0, (unsigned long long)(-gx));
+                atomicAdd(fj + 1, (unsigned long long)(-gy));
+                atomicAdd(fj + 2, (unsigned long long)(-gz));
+                qx += gx;
+                qy += gy;
+                qz += gz;
             }
         } else if (!HOT && Fq) {
             const uint32_t* row = nv.nbr + (size_t)i * nv.stride;
@@ -1757,7 +1767,6 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
             }
         }
         float fx = 0.f, fy = 0.f, fz = 0.f, v[9];
-        long long qx = 0, qy = 0, qz = 0;
 #pragma unroll
         for (int q = 0; q < 9; ++q) v[q] = 0.f;
         // the virial only when the caller asked for it (vir_part != nullptr), and
@@ -1765,7 +1774,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
         const bool vir_i = !HOT && vir_part && i < n_vir;
         const bool fq = HOT || Fq;
         for (int m = lane; m < M; m += 32) {
-            if (fq) {
+            if (fq && !q_done) {
                 qx += fx_get64<NARROW>(w, 3 * m);
                 qy += fx_get64<NARROW>(w, 3 * m + 1);
                 qz += fx_get64<NARROW>(w, 3 * m + 2);
