@@ -1495,8 +1495,8 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                     }
                     // stored queues come from global memory: load one round ahead
                     int ent_next = (STORED && lane < total) ? qsrc[lane] : 0;
-                    auto batch = [&](auto tail, int e0) {
-                        constexpr bool TAIL = decltype(tail)::value;
+                    auto batch = [&](auto tail, auto exact_t, int e0) {
+                        constexpr bool TAIL = decltype(tail)::value, EXACT = decltype(exact_t)::value;
                         const int e = e0 + lane;
                         int ent;
                         if (STORED) {
@@ -1655,7 +1655,7 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                             const float cd = NARROW ? phid * ird : 0.f;
                             // every component of g_a is at most |u_a| + |phic / ra| + |phid| (|a| = ra,
                             // |e| = rd); likewise for g_b
-                            if (exact)
+                            if (EXACT)
                                 fx_bad |= !(fabsf(ua) + fabsf(ta) + fabsf(phid) < FX_LIMIT &&
                                             fabsf(ub) + fabsf(tb) + fabsf(phid) < FX_LIMIT);
                             // with e = b - a: g_a = (ca + cd) a + (cab - cd) b, g_b = (cab - cd) a +
@@ -1697,8 +1697,14 @@ k_force(int n, const float4* __restrict__ pos4, Box bx, NbView nv, const Plan* _
                     // full batches without the lane guard (no divergent region, the vote
                     // over the full warp), then the partial one: -1.3 % on water
                     int e0 = 0;
-                    for (; e0 + 32 <= total; e0 += 32) batch(BTag<false>{}, e0);
-                    if (e0 < total) batch(BTag<true>{}, e0);
+                    // the atom's range test compiled in only where its bound does not hold
+                    if (exact) {
+                        for (; e0 + 32 <= total; e0 += 32) batch(BTag<false>{}, BTag<true>{}, e0);
+                        if (e0 < total) batch(BTag<true>{}, BTag<true>{}, e0);
+                    } else {
+                        for (; e0 + 32 <= total; e0 += 32) batch(BTag<false>{}, BTag<false>{}, e0);
+                        if (e0 < total) batch(BTag<true>{}, BTag<false>{}, e0);
+                    }
                     __syncwarp();
                     if (!STORED && FxU<NARROW>::CARRY && 32 * nb + 1 > FX_MAXADDS) {
                         // the slots of blocks A and B took at most 32 adds each: carry.
