@@ -62,14 +62,14 @@ MUFU_PEAK_GOPS = 148 * 16 * 2032e6 / 1e9
 # profiles/ (a 2M-atom launch moves the same bytes per atom: list rows,
 # positions, pair-queue and staged-neighbour records all scale with atoms).
 # Valid only for the kernel sources with this hash; otherwise traffic is null.
-TRAFFIC = {"force": (915.65056e6 + 6.571264e6) / 110592, "descriptors": (91.122176e6 + 781.284096e6) / 110592}
-TRAFFIC_SRC_SHA = "3d5fc7106f7d"
+TRAFFIC = {"force": (915.176704e6 + 6.241536e6) / 110592, "descriptors": (91.117312e6 + 780.914432e6) / 110592}
+TRAFFIC_SRC_SHA = "407f630bec03"
 # Warp instructions per atom-evaluation of the same launches (ncu
 # smsp__inst_executed.sum over the atoms; the 2M-atom launches run the same
 # instruction streams, their chunked atom walk adds a few per atom), under the same
 # source hash.  Both big kernels are bound by instruction issue: 148 SMs x 4
 # schedulers x 2032 MHz, one warp instruction per scheduler per clock.
-INST_PER_ATOM = {"force": 958243225 / 110592, "descriptors": 1058140535 / 110592}
+INST_PER_ATOM = {"force": 955708559 / 110592, "descriptors": 1058140535 / 110592}
 ISSUE_PEAK_WINST = 148 * 4 * 2032e6
 MEASURED_PEAKS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
 
